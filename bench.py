@@ -1,0 +1,464 @@
+#!/usr/bin/env python3
+"""Benchmark of the sub-band de-dispersion + boxcar matched-filter path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload meerkat_l|small] [--output cands|plane|cube]
+
+A step is one execute of the whole path on one block of a beam (ingest and
+transpose of a time-major uint8 block, stage 1, stage 2, statistics, boxcar
+S/N, output) with the beam's overlap tail resident on the device. The metric
+is DM-trial x samples per second (ndm * T per block). Inputs are synthetic,
+seeded, shaped like the workload, and resident in HBM before timing; each
+block is larger than L2 and two distinct blocks alternate.
+
+Rank 0 prints one JSON line. With --gpus N > 1 (launched by torchrun) every
+rank runs an independent beam replica on its own GPU (the path has no
+exchange step); value is the total over ranks divided by the slowest rank's
+time.
+
+--impl reference times the CPU oracle (test infrastructure, plain numpy) on
+bounded samples of the same workload: each step is one coarse DM group
+(stage 1 for its sub-bands, stage 2, statistics and boxcar for its fine DMs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "DM-trial*samples/s (dedisp+boxcar)"
+UNIT = "DM-trial*samples/s"
+SMS = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS), default="meerkat_l")
+    ap.add_argument("--output", choices=["cands", "plane", "cube"], default="cands")
+    ap.add_argument("--layout", choices=["tf", "ft"], default="tf")
+    ap.add_argument("--interm", choices=["u16", "i32"], default="u16")
+    ap.add_argument("--gamma", type=float, default=7.0)
+    ap.add_argument("--max-cands", type=int, default=1 << 22)
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# inputs
+# ----------------------------------------------------------------------------
+def workload_pulses(wl, nblocks, overlap):
+    """Pulses for each block of the stream (arrival times are stream positions)."""
+    out = []
+    for b in range(nblocks):
+        if wl.name.startswith("small"):
+            ps = synth.small_pulses(wl)
+        else:
+            ps = synth.meerkat_pulses(wl, seed=1 + b)
+        for p in ps:
+            p.t_arr += b * wl.nsamp
+        out += ps
+    return out
+
+
+def make_stream(wl, overlap, nblocks, seed=0):
+    return synth.make_stream(wl, overlap + nblocks * wl.nsamp, workload_pulses(wl, nblocks, overlap), seed=seed)
+
+
+# ----------------------------------------------------------------------------
+# peaks, clocks, traffic
+# ----------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ_NOMINAL}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if re.match(r"^[\d.]+$", r[1])]
+        smax = [float(r[2]) for r in rows if re.match(r"^[\d.]+$", r[2])]
+        pw = [float(r[3]) for r in rows if re.match(r"^[\d.]+$", r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        # samples taken under load: the upper half by power
+        if pw and len(pw) == len(sm):
+            cut = statistics.median(pw)
+            loaded = [s for s, p in zip(sm, pw) if p >= cut] or sm
+        else:
+            loaded = sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+def kernels_sha():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2401_13834_gb300", "csrc", "kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this kernels.cu."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([\d.eE+]+)", txt)
+    s = re.search(r"kernels_cu_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernels_sha():
+        return None
+    return float(m.group(1))
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work per launch (for the roofline)
+# ----------------------------------------------------------------------------
+def algorithmic_work(plan, ncand_avg):
+    """Per-launch algorithmic units of each phase.
+
+    stage1: sample-adds = sum_{k,s} m * (T + W_max - 1 + spread_ks), spread_ks the
+            stage-2 delay range of group k in sub-band s (the stage-1 sums stage 2 needs)
+    stage2: sample-adds = ndm * nsub * (T + W_max - 1)
+    ingest: bytes = block read + ring write + carried tail read + write
+    boxcar: bytes = series read (ndm * (T + W_max - 1) * 4) + output written
+    """
+    t = plan.tables()
+    d2, kof = t["d2"], t["coarse_of_fine"]
+    G = plan.group
+    Td = plan.series_len
+    m = plan.nchan // plan.nsub
+    adds1 = 0
+    for k in range(plan.ncoarse):
+        blk = d2[k * G:min((k + 1) * G, plan.ndm)]
+        spread = (blk.max(axis=0) - blk.min(axis=0)).astype(np.int64)
+        adds1 += int(m * (Td + spread).sum())
+    adds2 = plan.ndm * plan.nsub * Td
+    ingest = plan.block_bytes * 2 + plan.nchan * plan.overlap * 2
+    outb = {"cands": 8 + 16 * ncand_avg, "plane": plan.ndm * plan.nsamp * 5,
+            "cube": plan.ndm * plan.nwidth * plan.nsamp * 4}[plan.output]
+    box = plan.ndm * Td * 4 + outb
+    return {"ingest": ("hbm", ingest), "stage1": ("alu", adds1), "stage2": ("alu", adds2),
+            "stats": ("hbm", plan.ndm * plan.ntile2 * 16 if hasattr(plan, "ntile2") else plan.ndm * 16),
+            "boxcar": ("hbm", box)}
+
+
+def alu_peak(phase, sm_mhz):
+    """Derived on-chip peak in sample-adds/s.
+
+    Both de-dispersion stages stream their shifted operands through shared
+    memory, whose port moves 128 B per clock per SM. Stage 1 reads one byte per
+    sample-add (uint8 samples, four per 32-bit word), stage 2 two bytes (uint16
+    sums, two per word): 128 and 64 sample-adds per clock per SM.
+    """
+    per_clk = {"stage1": 128.0, "stage2": 64.0}[phase]
+    return SMS * per_clk * sm_mhz * 1e6
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing
+# ----------------------------------------------------------------------------
+def oracle_group_step(O, X, op, T, k, gamma):
+    ds = list(op.fine_dms_of(k))
+    D = O.subband_dedisperse(X, op, T + op.wmax - 1, ds)
+    _, _, mu, sg = O.block_stats(D, T)
+    snr = O.boxcar_snr(D, op.widths, T, mu, sg)
+    best, bw = O.dm_time_plane(snr)
+    O.candidates(best, bw, gamma, ds)
+    return len(ds)
+
+
+def cpu_baseline(wl, X, gamma, budget_s):
+    from oracle import dedisp as O
+    op = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, 0, wl.widths)
+    T = wl.nsamp
+    ks = np.linspace(0, op.nk - 1, min(op.nk, 64)).astype(int)
+    t0 = time.perf_counter()
+    ndone = 0
+    groups = 0
+    for k in ks:
+        ndone += oracle_group_step(O, X, op, T, int(k), gamma)
+        groups += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": ndone * T / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{groups} coarse DM groups ({ndone} of {wl.ndm} DM trials, spread over the DM range) "
+                      f"of one {wl.nchan}-channel x {T}-sample block: stage 1, stage 2, block statistics, "
+                      f"boxcar S/N, best width and candidates; numpy, single thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import dedisp as O
+    wl = synth.WORKLOADS[args.workload]()
+    op = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, 0, wl.widths)
+    X = make_stream(wl, op.overlap, 1)
+    T = wl.nsamp
+    ks = np.linspace(0, op.nk - 1, op.nk).astype(int)
+    for i in range(args.warmup):
+        oracle_group_step(O, X, op, T, int(ks[(i * 37) % len(ks)]), args.gamma)
+    t0 = time.perf_counter()
+    ndone = 0
+    for i in range(args.steps):
+        ndone += oracle_group_step(O, X, op, T, int(ks[(i * 37 + 11) % len(ks)]), args.gamma)
+    el = time.perf_counter() - t0
+    value = ndone * T / el
+    sample = (f"each step: one coarse DM group ({op.group} DM trials) of one {wl.nchan}-channel x {T}-sample "
+              f"block through the oracle (stage 1, stage 2, statistics, boxcar, candidates)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(wl, op.group, op.overlap, args, kind="reference"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, group, overlap, args, kind="ours"):
+    return {
+        "workload": wl.name, "nchan": wl.nchan, "band_mhz": [float(wl.freqs_mhz.min()), float(wl.freqs_mhz.max())],
+        "tsamp_us": wl.tsamp_s * 1e6, "ndm": wl.ndm, "dm_max": float(wl.dms.max()), "nsub": wl.nsub,
+        "group": group, "nsamp_per_block": wl.nsamp, "overlap": overlap,
+        "widths": [int(w) for w in wl.widths], "output": args.output, "layout": args.layout,
+        "interm": args.interm, "snr_threshold": args.gamma,
+        "l2": "inputs larger than L2: each block is nchan*T bytes (268 MB for 4096x65536), two distinct blocks alternate",
+        "beams_per_gpu": 1,
+    }
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2401_13834_gb300 import build as _build
+    _build.build()
+    import paper_2401_13834_gb300 as tx
+
+    wl = synth.WORKLOADS[args.workload]()
+    plan = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, layout=args.layout,
+                   interm=args.interm, output=args.output, snr_threshold=args.gamma, max_cands=args.max_cands)
+    L, T = plan.overlap, plan.nsamp
+    nb = 2
+    X = make_stream(wl, L, nb, seed=rank)
+
+    def lay(a):
+        return np.ascontiguousarray(a.T if args.layout == "tf" else a)
+
+    tail_h = lay(X[:, :L])
+    blocks_h = [lay(X[:, L + b * T:L + (b + 1) * T]) for b in range(nb)]
+    blocks = [torch.from_numpy(b).to(dev) for b in blocks_h]
+    beam = tx.Beam(plan)
+    beam.prime(torch.from_numpy(tail_h).to(dev))
+    ws = plan.alloc_workspace(dev)
+    out, ncand = plan.alloc_out(dev)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        tx.execute(plan, beam, blocks[i % nb], out=out, ncand=ncand, workspace=ws)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    timer = tx.Timer(args.steps)
+    clocks = None
+    for attempt in range(2):
+        timer.clear()
+        sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(args.steps):
+            tx.execute_timed(plan, beam, blocks[i % nb], out, ncand, ws, timer)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        elapsed_ms = ev0.elapsed_time(ev1)
+        if sampler:
+            clocks = sampler.stop()
+        bad = clocks and any(r in clocks["reasons"] for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"))
+        if not bad:
+            break
+    ncand_last = int(ncand.item()) if ncand is not None else 0
+    phase_ms, nsteps, step_ms = timer.read()
+
+    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t_max.item())
+    units = wl.ndm * T
+    value = world * units * args.steps / (elapsed_ms / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----------------
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = []
+        for b in blocks_h:
+            t = torch.empty(b.shape, dtype=torch.uint8, pin_memory=True)
+            t.numpy()[...] = b
+            pinned.append(t)
+        staging = torch.empty(plan.block_bytes, dtype=torch.uint8, device=dev)
+        if plan.output == "cands":
+            h_out = torch.empty((args.max_cands, 4), dtype=torch.int32, pin_memory=True).numpy()
+        else:
+            h_out = torch.empty(plan.out_bytes, dtype=torch.uint8, pin_memory=True).numpy()
+        for i in range(2):
+            tx.execute_host(plan, beam, pinned[i % nb].numpy(), h_out, staging, out, ncand, ws)
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for i in range(args.e2e_steps):
+            n = tx.execute_host(plan, beam, pinned[i % nb].numpy(), h_out, staging, out, ncand, ws)
+            d2h += (8 + 16 * min(n, args.max_cands)) if plan.output == "cands" else plan.out_bytes
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        tmax = torch.tensor([el], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * units * args.e2e_steps / float(tmax.item()), "unit": UNIT,
+               "h2d_bytes_per_step": plan.block_bytes, "d2h_bytes_per_step": int(d2h / args.e2e_steps),
+               "steps": args.e2e_steps, "api": "tx_execute_host (pinned host block in, results out, synchronous)"}
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        work = algorithmic_work(plan, ncand_last)
+        phases = {}
+        for name, ms in phase_ms.items():
+            avg = ms / max(nsteps, 1)
+            bound, amount = work[name]
+            entry = {"ms_per_launch": avg, "share": ms / max(sum(phase_ms.values()), 1e-12), "bound": bound}
+            if bound == "hbm":
+                ach = amount / (avg / 1e3) / 1e9 if avg > 0 else 0.0
+                entry.update({"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": ach / peaks["hbm_gbs"], "algorithmic": amount})
+            else:
+                pk = alu_peak(name, SM_MAX_MHZ_NOMINAL) / 1e12
+                ach = amount / (avg / 1e3) / 1e12 if avg > 0 else 0.0
+                entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": amount})
+            phases[name] = entry
+        dom = max(phase_ms, key=phase_ms.get)
+        kernel_of = {"ingest": "k_ingest_tf", "stage1": "k_stage1", "stage2": "k_stage2_u16", "stats": "k_stats",
+                     "boxcar": "k_boxcar"}
+        d = phases[dom]
+        roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": profiled_traffic(kernel_of[dom], wl.name), "kernel": kernel_of[dom],
+                "peak_source": (f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
+                                "derived: 152 SMs x shared-memory port 128 B/clk x 2.07 GHz, "
+                                f"{'1' if dom == 'stage1' else '2'} B per sample-add")}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(wl, X[:, :L + T], args.gamma, args.cpu_seconds)
+        launches_per_step = 6 if plan.output != "series" else 4
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32 sums, f32 S/N", "data": "synthetic",
+            "config": dict(workload_config(wl, plan.group, L, args), parallelism=f"replicas{world}"),
+            "p50_block_ms": float(np.percentile(step_ms, 50)), "p99_block_ms": float(np.percentile(step_ms, 99)),
+            "real_time_factor": (T * wl.tsamp_s) / (elapsed_ms / args.steps / 1e3),
+            "candidates_per_block": ncand_last if plan.output == "cands" else None,
+            "roofline": roof, "phases": phases, "clocks": clocks, "e2e": e2e,
+            "cpu_baseline": cpu, "gpu_launches": launches_per_step * args.steps,
+            "paper_context": "TransientX de-dispersion runs in real time on one i7-10750H core for 4096 channels x "
+                             "4096 DM trials at 153 us (>= 2.68e7 DM-trial*samples/s); CPU, other hardware",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * transientx.h -- C ABI of a GB300 (sm_103a) implementation of TransientX's
+ * de-dispersion + matched-filter hot path (Men & Barr, "TransientX: A high
+ * performance single pulse search package").
+ *
+ * What the library computes, per block of T new samples of a beam:
+ *
+ *   1. Sub-band de-dispersion (Sec. 2.3, Fig. 3), with the cold-plasma delay
+ *      of Eq. 1, tau = K DM (f^-2 - f_ref^-2), K = 4.148808e3 s MHz^2 pc^-1 cm^3:
+ *        stage 1:  P[k][s][t] = sum_{c in s} X[c][t + d1[k][c]]
+ *        stage 2:  D[d][t]    = sum_s     P[k(d)][s][t + d2[d][s]]
+ *      d1 = rnd(K DM_k (f_c^-2 - f_ref,s^-2) / t_samp) at the coarse DM k of the
+ *      trial's group, d2 = rnd(K DM_d (f_ref,s^-2 - f_ref^-2) / t_samp) at the fine
+ *      DM; rnd rounds half away from zero; f_ref = highest channel centre,
+ *      f_ref,s = highest centre in sub-band s; sub-band s = channels
+ *      [s m, (s+1) m); fine DMs are grouped G at a time in order and a group's
+ *      coarse DM is the midpoint of its first and last fine DM.
+ *   2. Block statistics of each series over t in [0, T): exact integer sums,
+ *      mean and population standard deviation ("sigma is the standard
+ *      deviation of the noise", Sec. 2.4), or their running (exponential)
+ *      update across blocks.
+ *   3. The boxcar matched filter of Eq. 5 computed by prefix sums (Sec. 2.4):
+ *        S/N[d][w][t] = (sum_{i=t}^{t+W_w-1} D[d][i] - W_w mu_d) / (sigma_d sqrt(W_w))
+ *      (window reported at its start t; sigma = 0 gives S/N = 0).
+ *   4. Output: the S/N cube, the DM-time plane of the best width (Sec. 2.5;
+ *      ties go to the smaller width), or the plane's points with
+ *      S/N >= threshold as candidate records.
+ *
+ * Blocking (Sec. 2.3 data flow, steps 1-4): each beam keeps the last L samples
+ * of every channel on the device (L = overlap = max over (d, c) of
+ * d1 + d2 + W_max - 1). An execute appends the T new samples behind that tail,
+ * computes outputs for buffer positions t in [0, T), and keeps the last L
+ * samples as the next tail. Output t of block b therefore refers to stream
+ * time b T - L + t at f_ref. A fresh beam's tail is zero; tx_beam_prime sets it.
+ *
+ * Conventions:
+ *  - Every function returns an int status: TX_OK (0) or a negative TX_ERR_*.
+ *    tx_last_error() gives a message for the calling thread's last failure.
+ *  - Pointers named d_* are device pointers (cudaMalloc / PyTorch CUDA
+ *    tensors); h_* are host pointers. The caller owns every buffer it passes.
+ *    The library owns what a plan or beam allocates and frees it in
+ *    tx_plan_destroy / tx_beam_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Device calls only enqueue work; nothing synchronises unless a
+ *    function says so.
+ *  - Distinct beams may be used from distinct threads concurrently. One beam
+ *    must not be used by two calls at once.
+ */
+#ifndef TRANSIENTX_H
+#define TRANSIENTX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TX_OK                  0
+#define TX_ERR_INVALID_ARG    -1  /* a pointer, size or enum out of range            */
+#define TX_ERR_NOT_DIVISIBLE  -2  /* nchan is not a multiple of nsub                  */
+#define TX_ERR_OOM            -3  /* a device or host allocation failed               */
+#define TX_ERR_CUDA           -4  /* a CUDA call failed (message in tx_last_error)    */
+#define TX_ERR_TIMEOUT        -5  /* a bounded wait ran out                           */
+#define TX_ERR_CAND_OVERFLOW  -6  /* more candidates than max_cands (results kept)    */
+#define TX_ERR_BUDGET         -7  /* an allocation would exceed a caller's budget     */
+#define TX_ERR_UNSUPPORTED    -8  /* valid but not supported by this build            */
+
+/* ---- enums ---- */
+enum tx_layout { TX_LAYOUT_FT = 0,   /* block is channel-major  uint8 [nchan][T]      */
+                 TX_LAYOUT_TF = 1 }; /* block is time-major     uint8 [T][nchan]
+                                        (filterbank order; transposed on ingest,
+                                        Sec. 2.3 data-flow step 2)                   */
+enum tx_interm { TX_INTERM_U16 = 0,  /* stage-1 sums stored as uint16 (exact for
+                                        nchan/nsub <= 257)                          */
+                 TX_INTERM_I32 = 1 };/* stored as int32                              */
+enum tx_output { TX_OUT_CANDS  = 0,  /* tx_cand records, S/N >= snr_threshold        */
+                 TX_OUT_PLANE  = 1,  /* float32 [ndm][T] best S/N, then uint8 [ndm][T]
+                                        index of the best width                      */
+                 TX_OUT_CUBE   = 2,  /* float32 [ndm][nwidth][T]                     */
+                 TX_OUT_SERIES = 3 };/* int32 [ndm][T + W_max - 1] de-dispersed series
+                                        (no matched filter)                          */
+enum tx_stats  { TX_STATS_BLOCK   = 0,  /* mu, sigma of this block                   */
+                 TX_STATS_RUNNING = 1 };/* mu, var <- (1-l) prev + l block; the first
+                                          block after create/reset initialises      */
+
+/* ---- plan description (all host pointers; copied by tx_plan_create) ---- */
+typedef struct tx_plan_desc {
+  int32_t        nchan;          /* channels, >= 1                                  */
+  const double*  freq_mhz;       /* [nchan] channel centre frequencies, MHz, > 0,
+                                    any order (sub-bands are index ranges)          */
+  double         tsamp_s;        /* sampling time, s, > 0                           */
+  int32_t        ndm;            /* fine DM trials, >= 1                            */
+  const double*  dm;             /* [ndm] ascending (non-decreasing), >= 0          */
+  int32_t        nsub;           /* sub-bands, divides nchan; nchan/nsub <= 257     */
+  int32_t        group;          /* fine DMs per coarse DM, 0 = automatic rule      */
+  int32_t        nwidth;         /* boxcar widths, 1..32                            */
+  const int32_t* widths;         /* [nwidth] strictly ascending, 1..4096 samples    */
+  int64_t        nsamp;          /* T, new samples per block, >= 1                  */
+  int32_t        layout;         /* enum tx_layout of blocks passed to execute      */
+  int32_t        interm;         /* enum tx_interm                                  */
+  int32_t        output;         /* enum tx_output                                  */
+  float          snr_threshold;  /* gamma for TX_OUT_CANDS (inclusive)              */
+  int64_t        max_cands;      /* capacity of the candidate buffer, >= 1          */
+  int32_t        stats;          /* enum tx_stats                                   */
+  double         stats_lambda;   /* weight of a new block in TX_STATS_RUNNING, (0,1]*/
+} tx_plan_desc;
+
+typedef struct tx_plan_info {
+  int32_t nchan, nsub, ndm, ncoarse, group, nwidth, wmax, reserved0;
+  int64_t nsamp;            /* T                                                    */
+  int64_t overlap;          /* L: carried samples per channel                       */
+  int64_t max_delay;        /* max over (d, c) of d1 + d2                           */
+  int64_t series_len;       /* T + W_max - 1                                        */
+  int64_t workspace_bytes;  /* device scratch an execute needs (d_workspace)        */
+  int64_t beam_state_bytes; /* device memory one beam holds                         */
+  int64_t out_bytes;        /* size of d_out for the plan's output mode             */
+  int64_t export_bytes;     /* host bytes for tx_beam_export / import               */
+  int64_t block_bytes;      /* nchan * T, bytes of one input block                  */
+} tx_plan_info;
+
+/* One candidate of TX_OUT_CANDS: a DM-time plane point with S/N >= threshold. */
+typedef struct tx_cand {
+  int32_t dm_index;   /* fine DM trial                                              */
+  int32_t t;          /* output position in [0, T) (window start)                   */
+  int32_t w_index;    /* index into widths of the best width                        */
+  float   snr;        /* its S/N                                                    */
+} tx_cand;
+
+typedef struct tx_plan tx_plan;
+typedef struct tx_beam tx_beam;
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t tx_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to
+   `size`) into `buf`; returns the message length. */
+int32_t tx_last_error(char* buf, size_t size);
+
+/* Builds a plan on the host: delay tables (Eq. 1 in double, rounded half away
+   from zero), coarse grouping, overlap, kernel work lists. No GPU is touched.
+   Errors: INVALID_ARG, NOT_DIVISIBLE, OOM. */
+int32_t tx_plan_create(const tx_plan_desc* desc, tx_plan** out);
+
+/* Sizes and shape of a plan. */
+int32_t tx_plan_get_info(const tx_plan* plan, tx_plan_info* info);
+
+/* Host copies of the plan's tables (any pointer may be NULL to skip it):
+     d1             int32 [ncoarse][nchan]  stage-1 delays (samples)
+     d2             int32 [ndm][nsub]       stage-2 delays (samples)
+     coarse_of_fine int32 [ndm]             group index k(d)
+     coarse_dm      double [ncoarse]        coarse DMs
+   These follow Eq. 1 and the sub-band scheme of Sec. 2.3. */
+int32_t tx_plan_tables(const tx_plan* plan, int32_t* d1, int32_t* d2,
+                       int32_t* coarse_of_fine, double* coarse_dm);
+
+/* Geometric boxcar ladder (Sec. 2.4: widths in a geometric sequence with a
+   tunable ratio): w_i = floor(ratio^i + 0.5), duplicates dropped, w_i <= wmax.
+   Writes at most `cap` widths to h_widths; returns the count (or an error). */
+int32_t tx_geometric_widths(double ratio, int32_t wmax, int32_t* h_widths, int32_t cap);
+
+/* Layout of the stage-1 intermediate inside d_workspace (for parity checks):
+     *p_offset  byte offset of P in the workspace
+     *p_pitch   elements per (k, s) row
+     h_base     int32 [ncoarse][nsub] (may be NULL): row (k, s) holds the stage-1
+                sum at times h_base[k][s] + j, j in [0, p_pitch)
+   P rows are uint16 or int32 per the plan's interm, row index k * nsub + s. */
+int32_t tx_plan_stage1_layout(const tx_plan* plan, int64_t* p_offset, int64_t* p_pitch,
+                              int32_t* h_base);
+
+void tx_plan_destroy(tx_plan* plan);
+
+/* Allocates a beam's device state (two channel-major rings of L + T samples per
+   channel, running statistics) on the current CUDA device and zeroes it.
+   Synchronous. Errors: INVALID_ARG, OOM, CUDA. */
+int32_t tx_beam_create(const tx_plan* plan, tx_beam** out);
+
+/* Zeroes the carried tail and the running statistics (enqueued on `stream`). */
+int32_t tx_beam_reset(const tx_plan* plan, tx_beam* beam, void* stream);
+
+/* Sets the carried tail to L given samples, d_tail in the plan's layout:
+   uint8 [nchan][L] (FT) or [L][nchan] (TF). Enqueued on `stream`. */
+int32_t tx_beam_prime(const tx_plan* plan, tx_beam* beam, const uint8_t* d_tail, void* stream);
+
+/* Checkpoint: copies the carried tail, running statistics and block counter to
+   host memory of info.export_bytes bytes (synchronous), and back. Resuming from
+   an export reproduces the uninterrupted outputs exactly. */
+int32_t tx_beam_export(const tx_plan* plan, const tx_beam* beam, void* h_dst, int64_t bytes);
+int32_t tx_beam_import(const tx_plan* plan, tx_beam* beam, const void* h_src, int64_t bytes);
+
+/* Blocks processed since create/reset/import. */
+int32_t tx_beam_blocks(const tx_beam* beam, int64_t* nblocks);
+
+void tx_beam_destroy(tx_beam* beam);
+
+/* Processes one block (Sec. 2.3 data flow, then Sec. 2.4 and 2.5):
+     d_block     uint8, nchan * T bytes in the plan's layout
+     d_out       info.out_bytes bytes; format set by the plan's output mode
+     d_ncand     int64 [1], TX_OUT_CANDS only (else may be NULL): set to the number
+                 of candidates found; records beyond max_cands are dropped, so a
+                 value above max_cands means the buffer overflowed
+     d_workspace info.workspace_bytes bytes of device scratch (not kept)
+   All kernels go on `stream`; the call returns once they are enqueued. */
+int32_t tx_execute(const tx_plan* plan, tx_beam* beam, const uint8_t* d_block, void* d_out,
+                   int64_t* d_ncand, void* d_workspace, void* stream);
+
+/* tx_execute from and to host memory: copies h_block (nchan * T bytes, the
+   plan's layout; pinned memory for full speed) to d_block_staging, executes,
+   and copies the result back, then synchronises `stream`:
+     TX_OUT_CANDS: *h_ncand and min(*h_ncand, max_cands) records to h_out
+     other modes:  info.out_bytes bytes to h_out
+   d_block_staging / d_out / d_ncand / d_workspace are device scratch as in
+   tx_execute. Returns TX_ERR_CAND_OVERFLOW (results kept) if candidates were
+   dropped. */
+int32_t tx_execute_host(const tx_plan* plan, tx_beam* beam, const uint8_t* h_block,
+                        void* h_out, int64_t* h_ncand, uint8_t* d_block_staging, void* d_out,
+                        int64_t* d_ncand, void* d_workspace, void* stream);
+
+/* ---- phase timing (CUDA events recorded on the execute's stream) ----
+   Phases of one execute, in order:
+     TX_PHASE_INGEST  carried tail + new block into the ring (Sec. 2.3 steps 1, 2, 4)
+     TX_PHASE_STAGE1  sub-bands at the coarse DMs (Sec. 2.3 sub-band step 1)
+     TX_PHASE_STAGE2  fine DMs from the sub-bands + exact sums (sub-band step 3)
+     TX_PHASE_STATS   mean / sigma per DM (Eq. 5's sigma)
+     TX_PHASE_BOXCAR  boxcar S/N and outputs (Eq. 5, Sec. 2.5)
+   A timer owns (TX_NPHASES + 1) * max_steps events created on the current
+   device; each tx_execute_timed call records one step's boundaries. */
+#define TX_PHASE_INGEST 0
+#define TX_PHASE_STAGE1 1
+#define TX_PHASE_STAGE2 2
+#define TX_PHASE_STATS  3
+#define TX_PHASE_BOXCAR 4
+#define TX_NPHASES      5
+
+typedef struct tx_timer tx_timer;
+
+int32_t tx_timer_create(int32_t max_steps, tx_timer** out);
+
+/* Forgets recorded steps (the events are reused). */
+int32_t tx_timer_clear(tx_timer* timer);
+
+/* tx_execute, recording the phase boundaries of the timer's next step on
+   `stream`. Errors as tx_execute, plus INVALID_ARG when the timer is full. */
+int32_t tx_execute_timed(const tx_plan* plan, tx_beam* beam, const uint8_t* d_block, void* d_out,
+                         int64_t* d_ncand, void* d_workspace, void* stream, tx_timer* timer);
+
+/* Waits for the last recorded event, then writes the summed milliseconds per
+   phase over all recorded steps to h_ms[TX_NPHASES], the step count, and (if
+   h_step_ms is not NULL) each step's total milliseconds to h_step_ms[nsteps]. */
+int32_t tx_timer_read(tx_timer* timer, double* h_ms, int32_t* nsteps, double* h_step_ms);
+
+void tx_timer_destroy(tx_timer* timer);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRANSIENTX_H */

@@ -1,0 +1,337 @@
+"""ctypes marshalling for libtransientx_gb300.so (argument conversion only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libtransientx_gb300.so")
+
+LAYOUTS = {"ft": 0, "tf": 1}
+INTERMS = {"u16": 0, "i32": 1}
+OUTPUTS = {"cands": 0, "plane": 1, "cube": 2, "series": 3}
+STATS = {"block": 0, "running": 1}
+
+TX_ERR_CAND_OVERFLOW = -6
+
+CAND_DTYPE = np.dtype([("dm_index", np.int32), ("t", np.int32), ("w_index", np.int32), ("snr", np.float32)])
+
+
+class TxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"transientx error {code}: {msg}")
+        self.code = code
+
+
+class _Desc(C.Structure):
+    _fields_ = [
+        ("nchan", C.c_int32), ("freq_mhz", C.POINTER(C.c_double)), ("tsamp_s", C.c_double),
+        ("ndm", C.c_int32), ("dm", C.POINTER(C.c_double)), ("nsub", C.c_int32), ("group", C.c_int32),
+        ("nwidth", C.c_int32), ("widths", C.POINTER(C.c_int32)), ("nsamp", C.c_int64),
+        ("layout", C.c_int32), ("interm", C.c_int32), ("output", C.c_int32),
+        ("snr_threshold", C.c_float), ("max_cands", C.c_int64), ("stats", C.c_int32),
+        ("stats_lambda", C.c_double),
+    ]
+
+
+class _Info(C.Structure):
+    _fields_ = [
+        ("nchan", C.c_int32), ("nsub", C.c_int32), ("ndm", C.c_int32), ("ncoarse", C.c_int32),
+        ("group", C.c_int32), ("nwidth", C.c_int32), ("wmax", C.c_int32), ("reserved0", C.c_int32),
+        ("nsamp", C.c_int64), ("overlap", C.c_int64), ("max_delay", C.c_int64), ("series_len", C.c_int64),
+        ("workspace_bytes", C.c_int64), ("beam_state_bytes", C.c_int64), ("out_bytes", C.c_int64),
+        ("export_bytes", C.c_int64), ("block_bytes", C.c_int64),
+    ]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(
+            f"{_LIB_PATH} is missing: build it with `python -m paper_2401_13834_gb300.build` "
+            "(there is no CPU fallback)")
+    L = C.CDLL(_LIB_PATH)
+    P, I32, I64, VP = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p
+    sig = {
+        "tx_version": (I32, []),
+        "tx_last_error": (I32, [C.c_char_p, C.c_size_t]),
+        "tx_plan_create": (I32, [C.POINTER(_Desc), C.POINTER(P)]),
+        "tx_plan_get_info": (I32, [P, C.POINTER(_Info)]),
+        "tx_plan_tables": (I32, [P, VP, VP, VP, VP]),
+        "tx_geometric_widths": (I32, [C.c_double, I32, VP, I32]),
+        "tx_plan_stage1_layout": (I32, [P, C.POINTER(I64), C.POINTER(I64), VP]),
+        "tx_plan_destroy": (None, [P]),
+        "tx_beam_create": (I32, [P, C.POINTER(P)]),
+        "tx_beam_reset": (I32, [P, P, VP]),
+        "tx_beam_prime": (I32, [P, P, VP, VP]),
+        "tx_beam_export": (I32, [P, P, VP, I64]),
+        "tx_beam_import": (I32, [P, P, VP, I64]),
+        "tx_beam_blocks": (I32, [P, C.POINTER(I64)]),
+        "tx_beam_destroy": (None, [P]),
+        "tx_execute": (I32, [P, P, VP, VP, VP, VP, VP]),
+        "tx_execute_host": (I32, [P, P, VP, VP, VP, VP, VP, VP, VP, VP]),
+        "tx_timer_create": (I32, [I32, C.POINTER(P)]),
+        "tx_timer_clear": (I32, [P]),
+        "tx_execute_timed": (I32, [P, P, VP, VP, VP, VP, VP, P]),
+        "tx_timer_read": (I32, [P, VP, C.POINTER(I32), VP]),
+        "tx_timer_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def version() -> int:
+    return int(lib.tx_version())
+
+
+def _check(rc):
+    if rc != 0:
+        buf = C.create_string_buffer(1024)
+        lib.tx_last_error(buf, 1024)
+        raise TxError(rc, buf.value.decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def geometric_widths(ratio: float, wmax: int) -> np.ndarray:
+    """Geometric boxcar ladder from the library (Sec. 2.4)."""
+    n = lib.tx_geometric_widths(float(ratio), int(wmax), None, 0)
+    if n < 0:
+        _check(n)
+    out = np.zeros(n, dtype=np.int32)
+    lib.tx_geometric_widths(float(ratio), int(wmax), out.ctypes.data_as(C.c_void_p), n)
+    return out
+
+
+class Plan:
+    """A de-dispersion + matched-filter plan (tables on the host until first use)."""
+
+    def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group=0, layout="ft", interm="u16",
+                 output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25):
+        self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+        self.dms = np.ascontiguousarray(dms, dtype=np.float64)
+        self.widths = np.ascontiguousarray(widths, dtype=np.int32)
+        d = _Desc()
+        d.nchan = self.freqs.size
+        d.freq_mhz = self.freqs.ctypes.data_as(C.POINTER(C.c_double))
+        d.tsamp_s = float(tsamp_s)
+        d.ndm = self.dms.size
+        d.dm = self.dms.ctypes.data_as(C.POINTER(C.c_double))
+        d.nsub = int(nsub)
+        d.group = int(group)
+        d.nwidth = self.widths.size
+        d.widths = self.widths.ctypes.data_as(C.POINTER(C.c_int32))
+        d.nsamp = int(nsamp)
+        d.layout = LAYOUTS[layout]
+        d.interm = INTERMS[interm]
+        d.output = OUTPUTS[output]
+        d.snr_threshold = float(snr_threshold)
+        d.max_cands = int(max_cands)
+        d.stats = STATS[stats]
+        d.stats_lambda = float(stats_lambda)
+        self.layout, self.interm, self.output, self.stats = layout, interm, output, stats
+        self.snr_threshold = float(snr_threshold)
+        self.max_cands = int(max_cands)
+        h = C.c_void_p()
+        _check(lib.tx_plan_create(C.byref(d), C.byref(h)))
+        self._h = h
+        inf = _Info()
+        _check(lib.tx_plan_get_info(h, C.byref(inf)))
+        self.info = {k: int(getattr(inf, k)) for k, _ in _Info._fields_ if k != "reserved0"}
+        for k, v in self.info.items():
+            setattr(self, k, v)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tables(self):
+        nk, nc, nd, ns = self.ncoarse, self.nchan, self.ndm, self.nsub
+        d1 = np.zeros((nk, nc), dtype=np.int32)
+        d2 = np.zeros((nd, ns), dtype=np.int32)
+        kof = np.zeros(nd, dtype=np.int32)
+        cdm = np.zeros(nk, dtype=np.float64)
+        _check(lib.tx_plan_tables(self._h, d1.ctypes.data_as(C.c_void_p), d2.ctypes.data_as(C.c_void_p),
+                                  kof.ctypes.data_as(C.c_void_p), cdm.ctypes.data_as(C.c_void_p)))
+        return {"d1": d1, "d2": d2, "coarse_of_fine": kof, "coarse_dm": cdm}
+
+    def stage1_layout(self):
+        off, pitch = C.c_int64(), C.c_int64()
+        base = np.zeros((self.ncoarse, self.nsub), dtype=np.int32)
+        _check(lib.tx_plan_stage1_layout(self._h, C.byref(off), C.byref(pitch), base.ctypes.data_as(C.c_void_p)))
+        return int(off.value), int(pitch.value), base
+
+    def alloc_workspace(self, device=None):
+        import torch
+        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device or "cuda")
+
+    def alloc_out(self, device=None):
+        import torch
+        dev = device or "cuda"
+        if self.output == "cands":
+            return (torch.empty((self.max_cands, 4), dtype=torch.int32, device=dev),
+                    torch.zeros(1, dtype=torch.int64, device=dev))
+        return torch.empty(self.out_bytes, dtype=torch.uint8, device=dev), None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and lib is not None:
+            lib.tx_plan_destroy(h)
+            self._h = None
+
+
+class Beam:
+    """Per-beam device state: the carried tail (two rings) and running statistics."""
+
+    def __init__(self, plan: Plan):
+        self.plan = plan
+        h = C.c_void_p()
+        _check(lib.tx_beam_create(plan.handle, C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reset(self, stream=None):
+        _check(lib.tx_beam_reset(self.plan.handle, self._h, _stream_ptr(stream)))
+
+    def prime(self, tail, stream=None):
+        """Set the carried tail from L samples (uint8 CUDA tensor in the plan's layout)."""
+        assert tail.is_cuda and tail.dtype.is_floating_point is False and tail.numel() == self.plan.nchan * self.plan.overlap
+        _check(lib.tx_beam_prime(self.plan.handle, self._h, _ptr(tail.contiguous()), _stream_ptr(stream)))
+
+    def export(self) -> bytes:
+        buf = (C.c_uint8 * self.plan.export_bytes)()
+        _check(lib.tx_beam_export(self.plan.handle, self._h, buf, self.plan.export_bytes))
+        return bytes(buf)
+
+    def import_(self, state: bytes):
+        buf = (C.c_uint8 * len(state)).from_buffer_copy(state)
+        _check(lib.tx_beam_import(self.plan.handle, self._h, buf, len(state)))
+
+    @property
+    def nblocks(self) -> int:
+        n = C.c_int64()
+        _check(lib.tx_beam_blocks(self._h, C.byref(n)))
+        return int(n.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and lib is not None:
+            lib.tx_beam_destroy(h)
+            self._h = None
+
+
+def execute(plan: Plan, beam: Beam, block, out=None, ncand=None, workspace=None, stream=None):
+    """Run one block (uint8 CUDA tensor, nchan*T bytes in the plan's layout).
+
+    Returns the raw output tensor(s) without synchronising: (out, ncand) for
+    candidates, else out (uint8 bytes of the plan's output mode).
+    """
+    if out is None:
+        out, ncand = plan.alloc_out(block.device)
+    if workspace is None:
+        workspace = plan.alloc_workspace(block.device)
+    assert block.is_cuda and block.numel() == plan.nchan * plan.nsamp and block.is_contiguous()
+    _check(lib.tx_execute(plan.handle, beam.handle, _ptr(block), _ptr(out), _ptr(ncand), _ptr(workspace),
+                          _stream_ptr(stream)))
+    return (out, ncand) if plan.output == "cands" else out
+
+
+PHASES = ("ingest", "stage1", "stage2", "stats", "boxcar")
+
+
+class Timer:
+    """CUDA events recorded between the phases of timed executes (on their stream)."""
+
+    def clear(self):
+        _check(lib.tx_timer_clear(self._h))
+
+    def __init__(self, max_steps: int):
+        h = C.c_void_p()
+        _check(lib.tx_timer_create(int(max_steps), C.byref(h)))
+        self._h = h
+        self.max_steps = int(max_steps)
+
+    def read(self):
+        """(summed ms per phase, step count, per-step total ms) over the recorded steps."""
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        steps = np.zeros(self.max_steps, dtype=np.float64)
+        n = C.c_int32()
+        _check(lib.tx_timer_read(self._h, ms.ctypes.data_as(C.c_void_p), C.byref(n), steps.ctypes.data_as(C.c_void_p)))
+        return dict(zip(PHASES, ms.tolist())), int(n.value), steps[:n.value]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and lib is not None:
+            lib.tx_timer_destroy(h)
+            self._h = None
+
+
+def execute_timed(plan: Plan, beam: Beam, block, out, ncand, workspace, timer: Timer, stream=None):
+    """``execute`` that also records the phase boundaries into ``timer``."""
+    _check(lib.tx_execute_timed(plan.handle, beam.handle, _ptr(block), _ptr(out), _ptr(ncand), _ptr(workspace),
+                                _stream_ptr(stream), timer._h))
+
+
+def execute_host(plan: Plan, beam: Beam, h_block: np.ndarray, h_out: np.ndarray, staging, out, ncand,
+                 workspace, stream=None):
+    """Host-to-host execute through the C ABI (copies inside; synchronises).
+
+    Returns the number of candidates (cands mode) or None.
+    """
+    h_block = np.ascontiguousarray(h_block)
+    hn = np.zeros(1, dtype=np.int64)
+    rc = lib.tx_execute_host(plan.handle, beam.handle, h_block.ctypes.data_as(C.c_void_p),
+                             h_out.ctypes.data_as(C.c_void_p), hn.ctypes.data_as(C.c_void_p), _ptr(staging),
+                             _ptr(out), _ptr(ncand), _ptr(workspace), _stream_ptr(stream))
+    if rc not in (0, TX_ERR_CAND_OVERFLOW):
+        _check(rc)
+    return int(hn[0]) if plan.output == "cands" else None
+
+
+# ---- decoding helpers (views of the raw output, no arithmetic) -------------
+def cands_view(plan: Plan, out, ncand):
+    import torch
+    n = min(int(ncand.item()), plan.max_cands)
+    raw = out[:n].contiguous().cpu().numpy()
+    return raw.view(CAND_DTYPE).reshape(-1), int(ncand.item())
+
+
+def plane_view(plan: Plan, out):
+    import torch
+    nd, T = plan.ndm, plan.nsamp
+    snr = out[: nd * T * 4].view(torch.float32).view(nd, T)
+    w = out[nd * T * 4: nd * T * 5].view(nd, T)
+    return snr, w
+
+
+def cube_view(plan: Plan, out):
+    import torch
+    return out.view(torch.float32).view(plan.ndm, plan.nwidth, plan.nsamp)
+
+
+def series_view(plan: Plan, out):
+    import torch
+    return out.view(torch.int32).view(plan.ndm, plan.series_len)

@@ -1,0 +1,336 @@
+// Host side of the plan: Eq. 1 delay tables, the sub-band grouping of Sec. 2.3,
+// the overlap carried between blocks, and the kernels' work lists and layouts.
+//
+// Compiled with -ffp-contract=off so that every delay is evaluated as
+// K * DM * (1/f^2 - 1/f_ref^2) / t_samp with separately rounded IEEE double
+// operations on every host architecture, then rounded half away from zero
+// (llround).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "tx_internal.h"
+
+namespace tx {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Eq. 1 in samples: rnd(K DM (1/f^2 - 1/f_ref^2) / t_samp), rnd = llround.
+static int64_t delay_samples(double dm, double f, double f_ref, double tsamp) {
+  const double v = kDispersion * dm * (1.0 / (f * f) - 1.0 / (f_ref * f_ref)) / tsamp;
+  return std::llround(v);
+}
+
+// Automatic coarse-grid rule (the paper leaves the coarse DM grid open): the
+// largest power of two G with G <= 1 + S_full / S_sub, where S_full is the
+// delay per unit DM across the whole band and S_sub the largest one inside a
+// sub-band, capped by the largest power of two <= ndm. Then a coarse DM's
+// residual smear inside any sub-band stays below the fine grid's half-step
+// smear across the band.
+static int auto_group(const std::vector<double>& f, double tsamp, int nsub, int ndm) {
+  const int nchan = (int)f.size();
+  const int m = nchan / nsub;
+  const double f_ref = *std::max_element(f.begin(), f.end());
+  const double f_min = *std::min_element(f.begin(), f.end());
+  const double s_full = kDispersion * (1.0 / (f_min * f_min) - 1.0 / (f_ref * f_ref)) / tsamp;
+  double s_sub = 0.0;
+  for (int s = 0; s < nsub; ++s) {
+    const double lo = *std::min_element(f.begin() + s * m, f.begin() + (s + 1) * m);
+    const double hi = *std::max_element(f.begin() + s * m, f.begin() + (s + 1) * m);
+    const double v = kDispersion * (1.0 / (lo * lo) - 1.0 / (hi * hi)) / tsamp;
+    s_sub = std::max(s_sub, v);
+  }
+  int cap = 1;
+  while ((int64_t)cap * 2 <= ndm) cap *= 2;
+  if (s_sub <= 0.0) return cap;
+  const double ratio = 1.0 + s_full / s_sub;
+  int g = 1;
+  while ((double)(g * 2) <= ratio && g * 2 <= cap) g *= 2;
+  return g;
+}
+
+static int build(tx_plan* p, const tx_plan_desc* d) {
+  // ---- validation ----------------------------------------------------------
+  if (!d->freq_mhz || !d->dm || !d->widths) { set_error("null table pointer in plan description"); return TX_ERR_INVALID_ARG; }
+  if (d->nchan < 1 || d->nsub < 1 || d->ndm < 1) { set_error("nchan, nsub and ndm must be >= 1"); return TX_ERR_INVALID_ARG; }
+  if (d->nchan % d->nsub) { set_error("nchan (%d) is not a multiple of nsub (%d)", d->nchan, d->nsub); return TX_ERR_NOT_DIVISIBLE; }
+  const int m = d->nchan / d->nsub;
+  if (m > 257) { set_error("at most 257 channels per sub-band (uint16 stage-1 sums); got %d", m); return TX_ERR_UNSUPPORTED; }
+  if (!(d->tsamp_s > 0.0) || !std::isfinite(d->tsamp_s)) { set_error("tsamp_s must be > 0"); return TX_ERR_INVALID_ARG; }
+  for (int c = 0; c < d->nchan; ++c)
+    if (!(d->freq_mhz[c] > 0.0) || !std::isfinite(d->freq_mhz[c])) { set_error("freq_mhz[%d] must be finite and > 0", c); return TX_ERR_INVALID_ARG; }
+  for (int i = 0; i < d->ndm; ++i) {
+    if (!(d->dm[i] >= 0.0) || !std::isfinite(d->dm[i])) { set_error("dm[%d] must be finite and >= 0", i); return TX_ERR_INVALID_ARG; }
+    if (i && d->dm[i] < d->dm[i - 1]) { set_error("dm must be ascending (dm[%d] < dm[%d])", i, i - 1); return TX_ERR_INVALID_ARG; }
+  }
+  if (d->nwidth < 1 || d->nwidth > kMaxWidths) { set_error("nwidth must be in [1, %d]", kMaxWidths); return TX_ERR_INVALID_ARG; }
+  for (int i = 0; i < d->nwidth; ++i) {
+    if (d->widths[i] < 1 || d->widths[i] > kMaxWidth) { set_error("widths[%d] must be in [1, %d]", i, kMaxWidth); return TX_ERR_INVALID_ARG; }
+    if (i && d->widths[i] <= d->widths[i - 1]) { set_error("widths must be strictly ascending"); return TX_ERR_INVALID_ARG; }
+  }
+  if (d->nsamp < 1) { set_error("nsamp must be >= 1"); return TX_ERR_INVALID_ARG; }
+  if (d->group < 0) { set_error("group must be >= 0"); return TX_ERR_INVALID_ARG; }
+  if (d->layout != TX_LAYOUT_FT && d->layout != TX_LAYOUT_TF) { set_error("bad layout"); return TX_ERR_INVALID_ARG; }
+  if (d->interm != TX_INTERM_U16 && d->interm != TX_INTERM_I32) { set_error("bad interm"); return TX_ERR_INVALID_ARG; }
+  if (d->output < TX_OUT_CANDS || d->output > TX_OUT_SERIES) { set_error("bad output mode"); return TX_ERR_INVALID_ARG; }
+  if (d->stats != TX_STATS_BLOCK && d->stats != TX_STATS_RUNNING) { set_error("bad stats mode"); return TX_ERR_INVALID_ARG; }
+  if (d->stats == TX_STATS_RUNNING && !(d->stats_lambda > 0.0 && d->stats_lambda <= 1.0)) { set_error("stats_lambda must be in (0, 1]"); return TX_ERR_INVALID_ARG; }
+  if (d->output == TX_OUT_CANDS && d->max_cands < 1) { set_error("max_cands must be >= 1"); return TX_ERR_INVALID_ARG; }
+  if (!std::isfinite(d->snr_threshold)) { set_error("snr_threshold must be finite"); return TX_ERR_INVALID_ARG; }
+
+  p->nchan = d->nchan; p->nsub = d->nsub; p->m = m; p->ndm = d->ndm; p->nw = d->nwidth;
+  p->T = d->nsamp; p->layout = d->layout; p->interm = d->interm; p->output = d->output;
+  p->stats = d->stats; p->gamma = d->snr_threshold; p->max_cands = d->max_cands;
+  p->lambda = d->stats == TX_STATS_RUNNING ? d->stats_lambda : 1.0;
+  p->tsamp = d->tsamp_s;
+  p->freq.assign(d->freq_mhz, d->freq_mhz + d->nchan);
+  p->dm.assign(d->dm, d->dm + d->ndm);
+  p->widths.assign(d->widths, d->widths + d->nwidth);
+  p->wmax = p->widths.back();
+  // window sums (<= wmax * nchan * 255) and W * mu must fit int32
+  if ((double)p->wmax * p->nchan * 255.0 >= 2147483647.0) { set_error("wmax * nchan * 255 must be < 2^31"); return TX_ERR_UNSUPPORTED; }
+  // exact S2 = sum D^2 in uint64
+  if ((double)p->T * std::pow((double)p->nchan * 255.0, 2) >= 9.2e18) { set_error("nsamp * (nchan*255)^2 must be < 2^63"); return TX_ERR_UNSUPPORTED; }
+
+  // ---- Eq. 1 tables, sub-band scheme of Sec. 2.3 ----------------------------
+  const int nchan = p->nchan, nsub = p->nsub, ndm = p->ndm;
+  p->group = d->group ? d->group : auto_group(p->freq, p->tsamp, nsub, ndm);
+  const int G = p->group;
+  if (G > kStage2MaxGroup) { set_error("group (%d) must be <= %d", G, kStage2MaxGroup); return TX_ERR_UNSUPPORTED; }
+  p->nk = (ndm + G - 1) / G;
+  const int nk = p->nk;
+  p->f_ref = *std::max_element(p->freq.begin(), p->freq.end());
+  p->f_ref_s.resize(nsub);
+  for (int s = 0; s < nsub; ++s) p->f_ref_s[s] = *std::max_element(p->freq.begin() + s * m, p->freq.begin() + (s + 1) * m);
+  p->kof.resize(ndm);
+  for (int i = 0; i < ndm; ++i) p->kof[i] = i / G;
+  p->coarse_dm.resize(nk);
+  for (int k = 0; k < nk; ++k) p->coarse_dm[k] = (p->dm[k * G] + p->dm[std::min((k + 1) * G, ndm) - 1]) / 2.0;
+  p->d1.resize((size_t)nk * nchan);
+  for (int k = 0; k < nk; ++k)
+    for (int c = 0; c < nchan; ++c) {
+      const int64_t v = delay_samples(p->coarse_dm[k], p->freq[c], p->f_ref_s[c / m], p->tsamp);
+      if (v < 0 || v > (1LL << 30)) { set_error("stage-1 delay out of range"); return TX_ERR_UNSUPPORTED; }
+      p->d1[(size_t)k * nchan + c] = (int32_t)v;
+    }
+  p->d2.resize((size_t)ndm * nsub);
+  for (int i = 0; i < ndm; ++i)
+    for (int s = 0; s < nsub; ++s) {
+      const int64_t v = delay_samples(p->dm[i], p->f_ref_s[s], p->f_ref, p->tsamp);
+      if (v < 0 || v > (1LL << 30)) { set_error("stage-2 delay out of range"); return TX_ERR_UNSUPPORTED; }
+      p->d2[(size_t)i * nsub + s] = (int32_t)v;
+    }
+  // overlap L = max over (d, c) of d1[k(d)][c] + d2[d][s(c)] + W_max - 1
+  int64_t best = 0;
+  std::vector<int32_t> d2max((size_t)nk * nsub, 0), d2min((size_t)nk * nsub, 0);
+  for (int k = 0; k < nk; ++k)
+    for (int s = 0; s < nsub; ++s) {
+      int32_t hi = 0, lo = INT32_MAX;
+      for (int i = k * G; i < std::min((k + 1) * G, ndm); ++i) {
+        hi = std::max(hi, p->d2[(size_t)i * nsub + s]);
+        lo = std::min(lo, p->d2[(size_t)i * nsub + s]);
+      }
+      d2max[(size_t)k * nsub + s] = hi;
+      d2min[(size_t)k * nsub + s] = lo;
+      for (int c = s * m; c < (s + 1) * m; ++c) best = std::max<int64_t>(best, (int64_t)p->d1[(size_t)k * nchan + c] + hi);
+    }
+  p->max_delay = best;
+  p->L = best + p->wmax - 1;
+  if (p->T + p->L >= (1LL << 30)) { set_error("nsamp + overlap must be < 2^30"); return TX_ERR_UNSUPPORTED; }
+
+  // ---- stage-2 layout -------------------------------------------------------
+  // P row (k, s) starts at absolute time abase = min_d d2 rounded down to 16 so
+  // stage-1 tiles and stage-2 reads stay aligned; e2 = d2 - abase >= 0.
+  p->Td = p->T + p->wmax - 1;
+  p->abase.resize((size_t)nk * nsub);
+  p->e2.resize((size_t)ndm * nsub);
+  int32_t span2 = 0, e2max = 0;
+  for (int k = 0; k < nk; ++k)
+    for (int s = 0; s < nsub; ++s) {
+      const int32_t lo = d2min[(size_t)k * nsub + s];
+      p->abase[(size_t)k * nsub + s] = lo & ~15;
+      span2 = std::max(span2, d2max[(size_t)k * nsub + s] - lo);
+    }
+  for (int i = 0; i < ndm; ++i)
+    for (int s = 0; s < nsub; ++s) {
+      const int32_t v = p->d2[(size_t)i * nsub + s] - p->abase[(size_t)p->kof[i] * nsub + s];
+      p->e2[(size_t)i * nsub + s] = v;
+      e2max = std::max(e2max, v);
+    }
+  p->span2_max = span2;
+  const int64_t tt2 = 2 * (int64_t)kStage2Q;
+  p->ntile2 = (int32_t)((p->Td + tt2 - 1) / tt2);
+  // stage 2 reads u16 indices up to the last tile's end + max(e2) + 19
+  // (staged spread plus aligned triple-word loads)
+  p->Pp = round_up(p->ntile2 * tt2 + e2max + 32, 64);
+  {
+    const int64_t words = round_up(kStage2Q + span2 + 4, 4);
+    const int64_t per_sub = words * 4;
+    const int64_t fixed = (int64_t)kStage2MaxGroup * nsub * 4 + nsub * 4 + 64;
+    int64_t sc = (kSmemBudget - fixed) / per_sub;
+    if (p->interm == TX_INTERM_I32) sc = (kSmemBudget - fixed) / (round_up(2 * kStage2Q + span2 + 4, 4) * 4);
+    if (sc < 1) { set_error("stage-2 delay spread within a DM group (%d samples) too large; use a smaller group", span2); return TX_ERR_UNSUPPORTED; }
+    p->nsub_chunk2 = (int32_t)std::min<int64_t>(sc, nsub);
+  }
+  p->Dp = round_up(p->Td + 8, 8);
+  p->ntile3 = (int32_t)((p->T + kBoxTile - 1) / kBoxTile);
+
+  // ---- stage-1 work list ----------------------------------------------------
+  // quarter length q1: the largest of 256/128/64/32 whose staged tile fits
+  int q1 = 256;
+  while (q1 > 32 && (int64_t)m * (2 * q1 + 4) * 4 + (int64_t)kStage1MaxCoarse * m * 4 > kSmemBudget) q1 /= 2;
+  p->q1 = q1;
+  p->span1_max = q1;
+  const int64_t tt1 = 4 * (int64_t)q1;
+  int64_t max_phys = 0;
+  for (int s = 0; s < nsub; ++s) {
+    int kb = 0;
+    while (kb < nk) {
+      auto spread = [&](int k0, int k1) {  // max_c d1[k1-1][c] - d1[k0][c]
+        int32_t v = 0;
+        for (int c = s * m; c < (s + 1) * m; ++c)
+          v = std::max(v, p->d1[(size_t)(k1 - 1) * nchan + c] - p->d1[(size_t)k0 * nchan + c]);
+        return v;
+      };
+      int ke = kb + 1;
+      while (ke < nk && ke - kb < kStage1MaxCoarse && spread(kb, ke + 1) <= p->span1_max) ++ke;
+      if (ke - kb >= 16) ke = kb + (ke - kb) / 16 * 16;  // whole rounds of the 16 warps
+      const int32_t span = spread(kb, ke);
+      int64_t lo = INT64_MAX, hi = 0;
+      for (int k = kb; k < ke; ++k) {
+        lo = std::min<int64_t>(lo, p->abase[(size_t)k * nsub + s]);
+        hi = std::max<int64_t>(hi, (int64_t)p->abase[(size_t)k * nsub + s] + p->Pp);
+      }
+      for (int64_t t0 = floor_div(lo, tt1) * tt1; t0 < hi; t0 += tt1) {
+        p->items1.push_back(Stage1Item{s, kb, ke, (int32_t)t0});
+        p->span1.push_back(span);
+        for (int c = s * m; c < (s + 1) * m; ++c)
+          max_phys = std::max<int64_t>(max_phys, t0 + p->d1[(size_t)kb * nchan + c] + tt1 + span + 16);
+      }
+      kb = ke;
+    }
+  }
+
+  // ---- ring rows ---------------------------------------------------------------
+  // Row layout: [pad | carried tail L | new block T | zeros]; pad puts the
+  // block at a 64-byte boundary. Stage 1 may read past L + T (tile rounding):
+  // those bytes stay zero and only feed sums that stage 2 never reads.
+  p->ring_pad = (64 - p->L % 64) % 64;
+  p->Rp = round_up(std::max<int64_t>(p->ring_pad + p->L + p->T + 16, p->ring_pad + max_phys + 16), 64);
+
+  // ---- sizes ---------------------------------------------------------------------
+  const int64_t psz = p->interm == TX_INTERM_U16 ? 2 : 4;
+  int64_t off = 0;
+  p->ws_P = off; off = round_up(off + (int64_t)nk * nsub * p->Pp * psz, 256);
+  p->ws_D = off; off = round_up(off + (p->output == TX_OUT_SERIES ? 0 : (int64_t)ndm * p->Dp * 4), 256);
+  p->ws_part = off; off = round_up(off + (int64_t)ndm * p->ntile2 * 16, 256);
+  p->ws_const = off; off = round_up(off + (int64_t)ndm * p->nw * (int64_t)sizeof(SnrConst), 256);
+  p->ws_bytes = off;
+  switch (p->output) {
+    case TX_OUT_CANDS: p->out_bytes = p->max_cands * (int64_t)sizeof(tx_cand); break;
+    case TX_OUT_PLANE: p->out_bytes = (int64_t)ndm * p->T * 5; break;
+    case TX_OUT_CUBE: p->out_bytes = (int64_t)ndm * p->nw * p->T * 4; break;
+    default: p->out_bytes = (int64_t)ndm * p->Td * 4; break;
+  }
+  p->beam_bytes = 2 * (int64_t)nchan * p->Rp + (int64_t)ndm * 16 + 16;
+  p->export_bytes = 64 + (int64_t)nchan * p->L + (int64_t)ndm * 16;
+  return TX_OK;
+}
+
+}  // namespace tx
+
+using namespace tx;
+
+extern "C" {
+
+int32_t tx_version(void) { return 100; }
+
+int32_t tx_last_error(char* buf, size_t size) {
+  const std::string& e = g_last_error;
+  if (buf && size) {
+    const size_t n = std::min(size - 1, e.size());
+    std::memcpy(buf, e.data(), n);
+    buf[n] = 0;
+  }
+  return (int32_t)e.size();
+}
+
+int32_t tx_plan_create(const tx_plan_desc* desc, tx_plan** out) {
+  if (!desc || !out) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  *out = nullptr;
+  tx_plan* p = new (std::nothrow) tx_plan();
+  if (!p) { set_error("out of host memory"); return TX_ERR_OOM; }
+  int rc;
+  try {
+    rc = build(p, desc);
+  } catch (const std::bad_alloc&) {
+    set_error("out of host memory");
+    rc = TX_ERR_OOM;
+  }
+  if (rc != TX_OK) { delete p; return rc; }
+  *out = p;
+  return TX_OK;
+}
+
+int32_t tx_plan_get_info(const tx_plan* p, tx_plan_info* info) {
+  if (!p || !info) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  std::memset(info, 0, sizeof(*info));
+  info->nchan = p->nchan; info->nsub = p->nsub; info->ndm = p->ndm; info->ncoarse = p->nk;
+  info->group = p->group; info->nwidth = p->nw; info->wmax = p->wmax;
+  info->nsamp = p->T; info->overlap = p->L; info->max_delay = p->max_delay; info->series_len = p->Td;
+  info->workspace_bytes = p->ws_bytes; info->beam_state_bytes = p->beam_bytes;
+  info->out_bytes = p->out_bytes; info->export_bytes = p->export_bytes;
+  info->block_bytes = (int64_t)p->nchan * p->T;
+  return TX_OK;
+}
+
+int32_t tx_plan_tables(const tx_plan* p, int32_t* d1, int32_t* d2, int32_t* coarse_of_fine, double* coarse_dm) {
+  if (!p) { set_error("null plan"); return TX_ERR_INVALID_ARG; }
+  if (d1) std::memcpy(d1, p->d1.data(), p->d1.size() * 4);
+  if (d2) std::memcpy(d2, p->d2.data(), p->d2.size() * 4);
+  if (coarse_of_fine) std::memcpy(coarse_of_fine, p->kof.data(), p->kof.size() * 4);
+  if (coarse_dm) std::memcpy(coarse_dm, p->coarse_dm.data(), p->coarse_dm.size() * 8);
+  return TX_OK;
+}
+
+int32_t tx_geometric_widths(double ratio, int32_t wmax, int32_t* h_widths, int32_t cap) {
+  if (!(ratio > 1.0) || wmax < 1 || cap < 0 || (cap > 0 && !h_widths)) { set_error("need ratio > 1, wmax >= 1"); return TX_ERR_INVALID_ARG; }
+  int32_t n = 0, last = 0;
+  double w = 1.0;
+  while (true) {
+    const int32_t iw = (int32_t)std::floor(w + 0.5);
+    if (iw > wmax) break;
+    if (iw != last) {
+      if (n < cap) h_widths[n] = iw;
+      ++n;
+      last = iw;
+    }
+    w *= ratio;
+  }
+  return n;
+}
+
+int32_t tx_plan_stage1_layout(const tx_plan* p, int64_t* p_offset, int64_t* p_pitch, int32_t* h_base) {
+  if (!p) { set_error("null plan"); return TX_ERR_INVALID_ARG; }
+  if (p_offset) *p_offset = p->ws_P;
+  if (p_pitch) *p_pitch = p->Pp;
+  if (h_base) std::memcpy(h_base, p->abase.data(), p->abase.size() * 4);
+  return TX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the host plan (plan.cpp) and the CUDA side
+// (kernels.cu). Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "transientx.h"
+
+namespace tx {
+
+// Eq. 1 constant e^2 / (2 pi m_e c) in s MHz^2 pc^-1 cm^3.
+constexpr double kDispersion = 4.148808e3;
+
+// ---- stage 1 (channels -> sub-bands at coarse DMs) tiling -------------------
+// A stage-1 tile covers 4*q consecutive times: a shared-memory word holds the
+// samples of times j, j+q, j+2q, j+3q of one channel, so one 32-bit load feeds
+// four outputs whatever the per-channel delay.
+constexpr int kStage1MaxCoarse = 32;   // coarse DMs that share one staged tile
+constexpr int kStage1Warps = 16;
+constexpr int kSmemBudget = 200 * 1024;
+
+// ---- stage 2 (sub-bands -> fine DMs) tiling ---------------------------------
+// Stage-2 words pair the uint16 sums of times j and j+q2 (q2 = kStage2Q).
+constexpr int kStage2Q = 256;
+constexpr int kStage2MaxGroup = 32;    // one warp per fine DM of a group
+
+// ---- matched filter ---------------------------------------------------------
+constexpr int kBoxTile = 2048;         // outputs per block of the boxcar kernel
+constexpr int kBoxThreads = 256;
+constexpr int kMaxWidths = 32;
+constexpr int kMaxWidth = 4096;
+
+// Stage-1 work item: sub-band s, coarse DMs [kb, ke), first time tau0.
+struct Stage1Item {
+  int32_t s, kb, ke, tau0;
+};
+
+// Per (fine DM, width) constants of the S/N normalisation (Eq. 5):
+// S/N = (float(B - hi) - lo) * inv with hi + lo = W * mu and inv = 1 / (sigma sqrt W).
+struct SnrConst {
+  int32_t hi;
+  float lo;
+  float inv;
+  float pad;
+};
+
+struct DevicePlan {
+  int device = -1;
+  int32_t* d1 = nullptr;         // [nk][nchan]
+  int32_t* abase = nullptr;      // [nk][nsub]
+  int32_t* e2 = nullptr;         // [ndm][nsub]
+  int32_t* widths = nullptr;     // [nw]
+  Stage1Item* items1 = nullptr;  // [n_items1]
+  int32_t* span1 = nullptr;      // [n_items1] staged delay spread per item
+};
+
+void set_error(const char* fmt, ...);
+
+}  // namespace tx
+
+struct tx_plan {
+  // ---- description -------------------------------------------------------
+  int32_t nchan = 0, nsub = 0, m = 0, ndm = 0, nk = 0, group = 0, nw = 0, wmax = 0;
+  int64_t T = 0;
+  int32_t layout = 0, interm = 0, output = 0, stats = 0;
+  float gamma = 0.f;
+  int64_t max_cands = 0;
+  double lambda = 1.0;
+  double tsamp = 0.0, f_ref = 0.0;
+  std::vector<double> freq, dm, coarse_dm, f_ref_s;
+  std::vector<int32_t> widths;
+
+  // ---- tables (Eq. 1, Sec. 2.3) -------------------------------------------
+  std::vector<int32_t> d1;        // [nk][nchan]
+  std::vector<int32_t> d2;        // [ndm][nsub]
+  std::vector<int32_t> kof;       // [ndm]
+  int64_t max_delay = 0, L = 0;
+
+  // ---- derived layout -----------------------------------------------------
+  std::vector<int32_t> abase;     // [nk][nsub] absolute time of P row start
+  std::vector<int32_t> e2;        // [ndm][nsub] = d2 - abase
+  int64_t Td = 0;                 // series length T + wmax - 1
+  int64_t Pp = 0;                 // P row pitch (elements)
+  int64_t Dp = 0;                 // D row pitch (int32 elements)
+  int64_t ring_pad = 0;           // ring row: [pad | tail L | block T | zeros]
+  int64_t Rp = 0;                 // ring row pitch (bytes)
+  int32_t q1 = 256;               // stage-1 quarter length (words)
+  int32_t span1_max = 256;        // staged delay spread limit of stage 1
+  int32_t span2_max = 0;          // max stage-2 delay spread within a group
+  int32_t ntile2 = 0;             // stage-2 tiles over the series
+  int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
+  int32_t ntile3 = 0;             // boxcar tiles over [0, T)
+  std::vector<tx::Stage1Item> items1;
+  std::vector<int32_t> span1;
+
+  // ---- workspace carve-up (bytes) -------------------------------------------
+  int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_bytes = 0;
+  int64_t out_bytes = 0, beam_bytes = 0, export_bytes = 0;
+
+  // ---- device copy, uploaded once ------------------------------------------
+  std::once_flag dev_once;
+  int dev_status = 0;
+  tx::DevicePlan dev;
+};
+
+struct tx_beam {
+  const tx_plan* plan = nullptr;
+  int device = -1;
+  uint8_t* ring[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* run = nullptr;          // [ndm][2] running (mu, var)
+  int32_t* run_init = nullptr;    // [1]
+  int64_t nblocks = 0;
+};
+
+// Implemented in kernels.cu.
+int tx_upload_plan(const tx_plan* plan);

@@ -190,11 +190,15 @@ def _pulse_half_span(p: Pulse) -> int:
     return int(math.ceil(2.0 * p.fwhm + 14.0 * p.tau_s + 4))
 
 
-def add_pulse(x: np.ndarray, p: Pulse, freqs: np.ndarray, tsamp: float) -> None:
-    """Add one dispersed pulse, in place, to a float dynamic spectrum x[nchan, nsamp]."""
+def add_pulse(x: np.ndarray, p: Pulse, freqs: np.ndarray, tsamp: float, f_top=None, f_mid=None) -> None:
+    """Add one dispersed pulse, in place, to a float dynamic spectrum x[nchan, nsamp].
+
+    f_top (arrival reference) and f_mid (spectral pivot) default to the band of
+    ``freqs``; pass the full band's values when ``freqs`` is a slice of it.
+    """
     nsamp = x.shape[1]
-    f_top = float(freqs.max())
-    f_mid = 0.5 * (float(freqs.min()) + f_top)
+    f_top = float(freqs.max()) if f_top is None else f_top
+    f_mid = 0.5 * (float(freqs.min()) + f_top) if f_mid is None else f_mid
     centres = p.t_arr + sky_delay_samples(p.dm, freqs, f_top, tsamp)
     spec = (freqs / f_mid) ** (-p.alpha)
     half = _pulse_half_span(p)
@@ -224,6 +228,27 @@ def make_spectrum(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0,
     for p in pulses:
         add_pulse(x, p, wl.freqs_mhz, wl.tsamp_s)
     return quantise(x)
+
+
+def make_stream(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0, chunk: int = 256) -> np.ndarray:
+    """Like ``make_spectrum`` but drawn in channel chunks to bound host memory.
+
+    Chunk i uses the generator seeded with (seed, i), so the result depends
+    only on (seed, chunk), not on the machine.
+    """
+    out = np.empty((wl.nchan, nsamp_total), dtype=np.uint8)
+    f32 = np.float32
+    for c0 in range(0, wl.nchan, chunk):
+        c1 = min(c0 + chunk, wl.nchan)
+        rng = np.random.default_rng([seed, c0 // chunk])
+        x = rng.standard_normal((c1 - c0, nsamp_total), dtype=f32)
+        x *= f32(wl.noise_std)
+        x += f32(wl.noise_mean)
+        for p in pulses:
+            add_pulse(x, p, wl.freqs_mhz[c0:c1], wl.tsamp_s, f_top=float(wl.freqs_mhz.max()),
+                      f_mid=0.5 * (float(wl.freqs_mhz.min()) + float(wl.freqs_mhz.max())))
+        out[c0:c1] = quantise(x)
+    return out
 
 
 def amplitude_for_snr(snr_g: float, wl: Workload, p: Pulse) -> float:

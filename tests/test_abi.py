@@ -1,0 +1,117 @@
+"""The C-ABI library on the CPU: it loads, exports what include/*.h declares,
+and its host-side plan (Eq. 1 tables, grouping, overlap) equals the oracle's.
+
+No compute call is made here; these tests need no GPU.
+"""
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dedisp as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tx():
+    from paper_2401_13834_gb300 import build
+    build.build()
+    import paper_2401_13834_gb300 as tx
+    return tx
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tx_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(tx):
+    declared = _declared()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", tx.library_path()], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = declared - exported
+    assert not missing, missing
+    for n in declared:
+        assert hasattr(tx.lib, n)
+
+
+def _plan(tx, wl, **kw):
+    return tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, group=wl.group, **kw)
+
+
+@pytest.mark.parametrize("mk", [
+    lambda: synth.small_workload(),
+    lambda: synth.meerkat_l_workload(),
+    lambda: synth.tiny_workload(descending=True),
+    lambda: synth.tiny_workload(nchan=48, nsub=48, ndm=9, group=4),
+    lambda: synth.tiny_workload(nchan=40, nsub=1, ndm=7, group=1),
+    lambda: synth.tiny_workload(nchan=64, nsub=8, ndm=13, group=5),
+])
+def test_plan_tables_equal_oracle(tx, mk):
+    wl = mk()
+    p = _plan(tx, wl)
+    o = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.group, wl.widths)
+    t = p.tables()
+    assert p.group == o.group and p.ncoarse == o.nk
+    assert np.array_equal(t["coarse_of_fine"], o.coarse_of_fine)
+    assert np.array_equal(t["coarse_dm"], o.coarse_dm)
+    assert np.array_equal(t["d1"], o.d1)
+    assert np.array_equal(t["d2"], o.d2)
+    assert p.overlap == o.overlap and p.max_delay == o.max_delay
+    assert p.series_len == wl.nsamp + o.wmax - 1
+
+
+def test_meerkat_plan_sizes(tx):
+    wl = synth.meerkat_l_workload()
+    p = _plan(tx, wl, output="plane")
+    assert p.group == 16 and p.ncoarse == 256
+    assert p.overlap == p.max_delay + 255 and 55000 < p.max_delay < 55500
+    assert p.out_bytes == 4096 * 65536 * 5
+    assert p.block_bytes == 4096 * 65536
+    off, pitch, base = p.stage1_layout()
+    assert off == 0 and pitch >= 65536 + 255 and np.all(base % 16 == 0)
+
+
+def test_geometric_widths_match_ladder(tx):
+    for r, w in [(2.0, 256), (1.5, 100), (1.1, 40), (3.0, 1)]:
+        assert np.array_equal(tx.geometric_widths(r, w), synth.geometric_widths(w, r))
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nsub=7), -2),
+    (dict(widths=[4, 2]), -1),
+    (dict(dms=[5.0, 1.0]), -1),
+    (dict(tsamp=0.0), -1),
+    (dict(nsamp=0), -1),
+    (dict(output="cands", max_cands=0), -1),
+])
+def test_invalid_plans_rejected(tx, kw, code):
+    wl = synth.tiny_workload(nchan=32, nsub=4)
+    args = dict(freqs=wl.freqs_mhz, tsamp=wl.tsamp_s, dms=wl.dms, nsub=4, widths=wl.widths, nsamp=wl.nsamp)
+    extra = {}
+    for k, v in kw.items():
+        if k in args:
+            args[k] = v
+        else:
+            extra[k] = v
+    with pytest.raises(tx.TxError) as e:
+        tx.Plan(args["freqs"], args["tsamp"], args["dms"], args["nsub"], args["widths"], args["nsamp"], **extra)
+    assert e.value.code == code
+
+
+def test_too_many_channels_per_subband_unsupported(tx):
+    wl = synth.tiny_workload(nchan=520, nsub=2)
+    with pytest.raises(tx.TxError) as e:
+        _plan(tx, wl)
+    assert e.value.code == -8

@@ -118,6 +118,9 @@ typedef struct tx_plan_info {
   int64_t out_bytes;        /* size of d_out for the plan's output mode             */
   int64_t export_bytes;     /* host bytes for tx_beam_export / import               */
   int64_t block_bytes;      /* nchan * T, bytes of one input block                  */
+  int64_t ring_len;         /* samples per channel of a beam's circular buffer (>= L + T);
+                               a block that wraps its end is ingested in two launches */
+  int64_t ring_head0;       /* where a fresh beam's first block lands in it        */
 } tx_plan_info;
 
 /* One candidate of TX_OUT_CANDS: a DM-time plane point with S/N >= threshold. */

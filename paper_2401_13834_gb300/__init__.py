@@ -2,8 +2,9 @@
 
 A thin ctypes binding over the C ABI declared in include/transientx.h; every
 step of the computation runs in the library's CUDA kernels. PyTorch provides
-device memory and streams only. There is no CPU fallback: if the shared
-library is missing the import of the native layer raises.
+device memory and streams only. There is no CPU fallback: the first use of any
+name below loads libtransientx_gb300.so and raises ImportError if it is
+missing (build it with ``python -m paper_2401_13834_gb300.build``).
 
     plan = Plan(freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, output="cands")
     beam = Beam(plan)
@@ -12,8 +13,16 @@ library is missing the import of the native layer raises.
 """
 from __future__ import annotations
 
-from ._native import (  # noqa: F401
-    LAYOUTS, INTERMS, OUTPUTS, STATS, CAND_DTYPE, TxError, Plan, Beam, execute, execute_host,
-    geometric_widths, lib, library_path, version, cands_view, plane_view, cube_view, series_view,
-    PHASES, Timer, execute_timed,
+_EXPORTS = (
+    "LAYOUTS", "INTERMS", "OUTPUTS", "STATS", "CAND_DTYPE", "PHASES", "TxError", "Plan", "Beam", "Timer",
+    "execute", "execute_timed", "execute_host", "geometric_widths", "lib", "library_path", "version",
+    "cands_view", "plane_view", "cube_view", "series_view",
 )
+__all__ = list(_EXPORTS)
+
+
+def __getattr__(name):
+    if name in _EXPORTS:
+        from . import _native
+        return getattr(_native, name)
+    raise AttributeError(name)

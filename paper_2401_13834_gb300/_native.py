@@ -42,7 +42,8 @@ class _Info(C.Structure):
         ("group", C.c_int32), ("nwidth", C.c_int32), ("wmax", C.c_int32), ("reserved0", C.c_int32),
         ("nsamp", C.c_int64), ("overlap", C.c_int64), ("max_delay", C.c_int64), ("series_len", C.c_int64),
         ("workspace_bytes", C.c_int64), ("beam_state_bytes", C.c_int64), ("out_bytes", C.c_int64),
-        ("export_bytes", C.c_int64), ("block_bytes", C.c_int64),
+        ("export_bytes", C.c_int64), ("block_bytes", C.c_int64), ("ring_len", C.c_int64),
+        ("ring_head0", C.c_int64),
     ]
 
 

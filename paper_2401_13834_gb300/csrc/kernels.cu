@@ -4,17 +4,17 @@
 // them.
 //
 // Kernel map (one execute):
-//   k_tail / k_ingest_*   Sec. 2.3 data-flow steps 1, 2 and 4: the carried
-//                         tail and the new block land channel-major in the
-//                         beam's next ring buffer (time-major input is
-//                         transposed on the way).
-//   k_stage1              stage 1: P[k][s][t] = sum_{c in s} X[c][t + d1[k][c]]
-//   k_stage2_*            stage 2: D[d][t] = sum_s P[k(d)][s][t + d2[d][s]],
-//                         plus exact per-tile sums of D and D^2
-//   k_stats               mean / sigma per DM (block or running), and the
-//                         per-width constants of Eq. 5
-//   k_boxcar              prefix sums, window sums for every width, S/N
-//                         (Eq. 5), best width, and cube / plane / candidates
+//   k_ingest_*   Sec. 2.3 data-flow steps 1, 2 and 4: the new block lands
+//                channel-major in the beam's circular buffer behind the carried
+//                tail (time-major input is transposed on the way); nothing is
+//                shifted, the buffer start advances by T instead.
+//   k_stage1     stage 1: P[k][s][t] = sum_{c in s} X[c][t + d1[k][c]]
+//   k_stage2_*   stage 2: D[d][t] = sum_s P[k(d)][s][t + d2[d][s]], plus exact
+//                per-tile sums of D and D^2
+//   k_stats      mean / sigma per DM (block or running) and the per-width
+//                constants of Eq. 5
+//   k_boxcar     prefix sums, window sums for every width, S/N (Eq. 5), best
+//                width, and cube / plane / candidates
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,161 +39,259 @@ using namespace tx;
 namespace {
 
 // ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+// a * one + c with `one` a runtime value (always 1): the add is issued as an
+// integer multiply-add on the FMA pipe, leaving the ALU pipe to the byte
+// permutes and the other adds.
+__device__ __forceinline__ void madd(uint32_t& acc, uint32_t a, uint32_t one) {
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(a), "r"(one));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // ingest (Sec. 2.3 data flow)
 // ---------------------------------------------------------------------------
-// Channel-major block [nchan][n] -> ring rows at byte offset `off`.
-__global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t n, uint8_t* __restrict__ ring,
-                            int64_t Rp, int64_t off) {
+// Channel-major rows: ring[c][dst_off + i] = src[c][src_off + i], i < n.
+__global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t src_pitch, int64_t src_off, int64_t n,
+                            uint8_t* __restrict__ ring, int64_t R, int64_t dst_off, int vec) {
   const int c = blockIdx.y;
-  const uint8_t* s = src + (int64_t)c * n;
-  uint8_t* d = ring + (int64_t)c * Rp + off;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = s[i];
+  const uint8_t* s = src + (int64_t)c * src_pitch + src_off;
+  uint8_t* d = ring + (int64_t)c * R + dst_off;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(s);
+    uint4* d4 = reinterpret_cast<uint4*>(d);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 16; i += stride) d4[i] = s4[i];
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) d[i] = s[i];
+  }
 }
 
-// Same with 16-byte vectors (n, off, the source rows and the ring rows all 16-byte aligned).
-__global__ void k_ingest_ft16(const uint4* __restrict__ src, int64_t n16, uint8_t* __restrict__ ring,
-                              int64_t Rp, int64_t off) {
-  const int c = blockIdx.y;
-  const uint4* s = src + (int64_t)c * n16;
-  uint4* d = reinterpret_cast<uint4*>(ring + (int64_t)c * Rp + off);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = s[i];
-}
-
-// Time-major block [n][nchan] -> ring[c][off + t], through a 64 x 64 byte tile.
-__global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ src, int64_t n, int nchan,
-                                                   uint8_t* __restrict__ ring, int64_t Rp, int64_t off) {
-  __shared__ uint8_t tile[64][68];
+// Time-major block rows [t][nchan], t in [t_off, t_off + n) -> ring[c][dst_off + t - t_off],
+// through a 64-time x 64-channel byte tile. vec: 16-byte loads and stores
+// (nchan, dst_off and the source all 16-byte aligned).
+__global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ src, int64_t t_off, int64_t n,
+                                                   int nchan, uint8_t* __restrict__ ring, int64_t R,
+                                                   int64_t dst_off, int vec) {
+  __shared__ __align__(16) uint8_t tile[64][80];
   const int64_t t0 = (int64_t)blockIdx.x * 64;
   const int c0 = blockIdx.y * 64;
-  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-    const int tt = i >> 6, cc = i & 63;
-    if (t0 + tt < n && c0 + cc < nchan) tile[tt][cc] = src[(t0 + tt) * nchan + c0 + cc];
+  {
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const int64_t t = t0 + r;
+    const int c = c0 + 16 * q;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (t < n) {
+      const uint8_t* sp = src + (t_off + t) * nchan + c;
+      if (vec && c + 16 <= nchan) {
+        v = __ldg(reinterpret_cast<const uint4*>(sp));
+      } else {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        for (int i = 0; i < 16; ++i)
+          if (c + i < nchan) w[i >> 2] |= (uint32_t)sp[i] << (8 * (i & 3));
+        v = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    *reinterpret_cast<uint4*>(&tile[r][16 * q]) = v;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-    const int cc = i >> 6, tt = i & 63;
-    if (t0 + tt < n && c0 + cc < nchan) ring[(int64_t)(c0 + cc) * Rp + off + t0 + tt] = tile[tt][cc];
+  {
+    const int cc = threadIdx.x & 63, pq = threadIdx.x >> 6;
+    const int c = c0 + cc;
+    if (c < nchan) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        w[i] = (uint32_t)tile[16 * pq + 4 * i][cc] | ((uint32_t)tile[16 * pq + 4 * i + 1][cc] << 8) |
+               ((uint32_t)tile[16 * pq + 4 * i + 2][cc] << 16) | ((uint32_t)tile[16 * pq + 4 * i + 3][cc] << 24);
+      const int64_t t = t0 + 16 * pq;
+      uint8_t* dp = ring + (int64_t)c * R + dst_off + t;
+      if (vec && t + 16 <= n) {
+        *reinterpret_cast<uint4*>(dp) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        for (int i = 0; i < 16; ++i)
+          if (t + i < n) dp[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+      }
+    }
   }
-}
-
-// Carried tail: next[c][pad + i] = cur[c][pad + T + i], i in [0, L).
-__global__ void k_tail(const uint8_t* __restrict__ cur, uint8_t* __restrict__ nxt, int64_t Rp, int64_t src_off,
-                       int64_t dst_off, int64_t L) {
-  const int c = blockIdx.y;
-  const uint8_t* s = cur + (int64_t)c * Rp + src_off;
-  uint8_t* d = nxt + (int64_t)c * Rp + dst_off;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = s[i];
 }
 
 // ---------------------------------------------------------------------------
 // stage 1 (Sec. 2.3: de-disperse each sub-band on the coarse DM grid)
 // ---------------------------------------------------------------------------
-// One block = one work item: sub-band s, coarse DMs [kb, ke), absolute times
-// [tau0, tau0 + 4Q). Shared word S[c][j] holds channel c's samples at times
-// tau0 + d1[kb][c] + j + qQ in byte q (q = 0..3). For coarse DM k the output
-// word j is sum_c S[c][j + d1[k][c] - d1[kb][c]], four outputs per 32-bit
-// load whatever the delays. Sums use the byte-lane identity
+// Persistent blocks walk the work items (sub-band s, coarse DMs [kb, ke),
+// absolute times [tau0, tau0 + 4Q)). For each item the channels' input
+// windows are copied (cp.async) into a raw buffer while the previous item is
+// being summed, then rearranged so that shared word S[c][j] holds channel c's
+// samples at times tau0 + d1[kb][c] + j + qQ in byte q (q = 0..3). For coarse
+// DM k the output word j is sum_c S[c][j + d1[k][c] - d1[kb][c]]: four outputs
+// per 32-bit load whatever the delays. Sums use the byte-lane identity
 //   sum w = sum(lo lanes) + 256 * sum(hi lanes)  (mod 2^32)
 // with the hi lanes (bytes 1, 3) accumulated separately as 16-bit lanes,
 // exact for up to 257 channels per sub-band.
 template <int Q, typename PT>
-__global__ void __launch_bounds__(kStage1Warps * 32)
-k_stage1(const uint8_t* __restrict__ ring, int64_t Rp, int64_t pad, const Stage1Item* __restrict__ items,
-         const int32_t* __restrict__ spans, const int32_t* __restrict__ d1, int nchan, int m, int nsub,
-         const int32_t* __restrict__ abase, PT* __restrict__ P, int64_t Pp) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  constexpr int SW = 2 * Q + 4;  // words per staged channel: Q + span (span <= Q), 16-byte rows
+__global__ void __launch_bounds__(kStage1Warps * 32, 1)
+k_stage1(const uint8_t* __restrict__ ring, int R, int start, const Stage1Item* __restrict__ items,
+         int nitems, const int32_t* __restrict__ d1, int nchan, int m, int nsub, const int32_t* __restrict__ abase,
+         PT* __restrict__ P, int64_t Pp, uint32_t one) {
+  extern __shared__ __align__(16) uint8_t smem1[];
+  constexpr int SW = 2 * Q + 32;                 // staged words per channel (>= Q + span + 30, span <= Q)
+  constexpr int RB = (5 * Q + 48 + 15) / 16 * 16;  // raw bytes per channel (>= 3Q + SW bytes)
+  constexpr int NCH = RB / 16;
   constexpr int V = Q / 32;
-  uint32_t* S = smem;
-  int32_t* off = reinterpret_cast<int32_t*>(smem + (size_t)m * SW);
-  const Stage1Item it = items[blockIdx.x];
-  const int span = spans[blockIdx.x];
-  const int nkk = it.ke - it.kb;
-  const int c0 = it.s * m;
-  const int32_t* d1kb = d1 + (size_t)it.kb * nchan + c0;
-
-  for (int i = threadIdx.x; i < nkk * m; i += blockDim.x) {
-    const int kk = i / m, c = i - kk * m;
-    off[i] = d1[(size_t)(it.kb + kk) * nchan + c0 + c] - d1kb[c];
-  }
-  const int nw4 = (Q + span + 3) >> 2;
-  for (int i = threadIdx.x; i < m * nw4; i += blockDim.x) {
-    const int c = i / nw4, j = (i - c * nw4) << 2;
-    const uint8_t* row = ring + (size_t)(c0 + c) * Rp;
-    const int64_t b = pad + (int64_t)it.tau0 + d1kb[c] + j;
-    uint32_t r[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t p = b + (int64_t)q * Q;
-      const uint32_t* wp = reinterpret_cast<const uint32_t*>(row + (p & ~(int64_t)3));
-      r[q] = __funnelshift_r(__ldg(wp), __ldg(wp + 1), (unsigned)(p & 3) * 8u);
-    }
-    // 4 x 4 byte transpose: word j+i collects byte i of each quarter
-    const uint32_t t0 = __byte_perm(r[0], r[1], 0x5140), t1 = __byte_perm(r[0], r[1], 0x7362);
-    const uint32_t t2 = __byte_perm(r[2], r[3], 0x5140), t3 = __byte_perm(r[2], r[3], 0x7362);
-    uint4 w;
-    w.x = __byte_perm(t0, t2, 0x5410);
-    w.y = __byte_perm(t0, t2, 0x7632);
-    w.z = __byte_perm(t1, t3, 0x5410);
-    w.w = __byte_perm(t1, t3, 0x7632);
-    *reinterpret_cast<uint4*>(S + (size_t)c * SW + j) = w;
-  }
-  __syncthreads();
-
+  const int TS = (m + 1) & ~1;                   // offset-table row stride (8-byte aligned pairs)
+  uint32_t* S = reinterpret_cast<uint32_t*>(smem1);
+  uint8_t* raw = smem1 + (size_t)m * SW * 4;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(raw + (size_t)m * RB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int kk = warp; kk < nkk; kk += kStage1Warps) {
-    const int k = it.kb + kk;
-    const int64_t ab = abase[(size_t)k * nsub + it.s];
-    if ((int64_t)it.tau0 + 4 * Q <= ab || (int64_t)it.tau0 >= ab + Pp) continue;
-    uint32_t aw[V], ah[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
-    const int32_t* o = off + kk * m;
-    const uint32_t* base = S + lane;
-#pragma unroll 4
-    for (int c = 0; c < m; ++c) {
-      const uint32_t* rw = base + (size_t)c * SW + o[c];
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const uint32_t w = rw[32 * v];
-        aw[v] += w;
-        ah[v] += __byte_perm(w, 0u, 0x4341);
+
+  // physical ring position of channel c's first staged sample for item idx
+  auto window_start = [&](const Stage1Item& it, int c) -> int {
+    const int64_t p = (int64_t)start + it.tau0 + d1[(size_t)it.kb * nchan + it.s * m + c];
+    return (int)(p % R);
+  };
+  auto issue = [&](int idx) {
+    const Stage1Item it = items[idx];
+    for (int c = warp; c < m; c += kStage1Warps) {
+      const int pa = window_start(it, c) & ~15;
+      const uint8_t* row = ring + (size_t)(it.s * m + c) * R;
+      uint8_t* dst = raw + (size_t)c * RB;
+      for (int ch = lane; ch < NCH; ch += 32) {
+        int q = pa + 16 * ch;  // R is a multiple of 64: a chunk never straddles the wrap
+        while (q >= R) q -= R;
+        cp_async16(dst + 16 * ch, row + q);
       }
     }
-    PT* prow = P + ((size_t)k * nsub + it.s) * Pp;
-    const int64_t rel0 = (int64_t)it.tau0 - ab;
+    cp_async_commit();
+  };
+
+  int idx = blockIdx.x;
+  if (idx < nitems) issue(idx);
+  while (idx < nitems) {
+    const Stage1Item it = items[idx];
+    const int c0 = it.s * m;
+    const int nkk = it.ke - it.kb;
+    const int32_t* d1kb = d1 + (size_t)it.kb * nchan + c0;
+    cp_async_wait_all();
+    __syncthreads();
+    // Raw windows (16-byte aligned starts) -> four-quarter words: S[c][j] byte q
+    // = raw[c][j + qQ]. The window's misalignment a_c goes into the offsets.
+    // Lane g builds words 16g .. 16g + 15 from four aligned 16-byte loads.
+    const int n16 = (Q + it.span + 15 + 15) >> 4;
+    for (int c = warp; c < m; c += kStage1Warps) {
+      const uint8_t* rw = raw + (size_t)c * RB;
+      uint32_t* srow = S + (size_t)c * SW;
+      for (int g = lane; g < n16; g += 32) {
+        const int j = g << 4;
+        uint4 x[4];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int j = lane + 32 * v;
-      const uint32_t lo = aw[v] - (ah[v] << 8);
-      const uint32_t val[4] = {lo & 0xFFFFu, ah[v] & 0xFFFFu, lo >> 16, ah[v] >> 16};
+        for (int q = 0; q < 4; ++q) x[q] = *reinterpret_cast<const uint4*>(rw + j + q * Q);
+        uint32_t xs[4][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t u = rel0 + j + (int64_t)q * Q;
-        if (u >= 0 && u < Pp) prow[u] = (PT)val[q];
+        for (int q = 0; q < 4; ++q) {
+          xs[q][0] = x[q].x; xs[q][1] = x[q].y; xs[q][2] = x[q].z; xs[q][3] = x[q].w;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          // 4 x 4 byte transpose: word 4e+i collects byte i of each quarter's word e
+          const uint32_t t0 = __byte_perm(xs[0][e], xs[1][e], 0x5140), t1 = __byte_perm(xs[0][e], xs[1][e], 0x7362);
+          const uint32_t t2 = __byte_perm(xs[2][e], xs[3][e], 0x5140), t3 = __byte_perm(xs[2][e], xs[3][e], 0x7362);
+          uint4 w;
+          w.x = __byte_perm(t0, t2, 0x5410);
+          w.y = __byte_perm(t0, t2, 0x7632);
+          w.z = __byte_perm(t1, t3, 0x5410);
+          w.w = __byte_perm(t1, t3, 0x7632);
+          *reinterpret_cast<uint4*>(srow + j + 4 * e) = w;
+        }
       }
     }
+    // word offset of S[c][a_c + d1[k][c] - d1[kb][c]] for every (k, c)
+    for (int kk = warp; kk < nkk; kk += kStage1Warps) {
+      const int32_t* d1k = d1 + (size_t)(it.kb + kk) * nchan + c0;
+      for (int c = lane; c < m; c += 32)
+        tab[kk * TS + c] = (uint32_t)(c * SW + (window_start(it, c) & 15) + d1k[c] - d1kb[c]);
+    }
+    __syncthreads();
+    const int next = idx + gridDim.x;
+    if (next < nitems) issue(next);
+
+    const uint32_t* Sl = S + lane;
+    for (int kk = warp; kk < nkk; kk += kStage1Warps) {
+      const int k = it.kb + kk;
+      const int64_t ab = abase[(size_t)k * nsub + it.s];
+      if ((int64_t)it.tau0 + 4 * Q <= ab || (int64_t)it.tau0 >= ab + Pp) continue;
+      uint32_t aw[V], ah[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
+      const uint32_t* t = tab + kk * TS;
+      int c = 0;
+#pragma unroll 2
+      for (; c + 1 < m; c += 2) {
+        const uint2 oo = *reinterpret_cast<const uint2*>(t + c);
+        const uint32_t* r0 = Sl + oo.x;
+        const uint32_t* r1 = Sl + oo.y;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+          madd(aw[v], w0, one);
+          madd(aw[v], w1, one);
+          ah[v] += __byte_perm(w0, 0u, 0x4341) + __byte_perm(w1, 0u, 0x4341);
+        }
+      }
+      if (c < m) {
+        const uint32_t* r0 = Sl + t[c];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const uint32_t w0 = r0[32 * v];
+          madd(aw[v], w0, one);
+          ah[v] += __byte_perm(w0, 0u, 0x4341);
+        }
+      }
+      PT* prow = P + ((size_t)k * nsub + it.s) * Pp;
+      const int rel0 = (int)((int64_t)it.tau0 - ab);  // |rel0| < 2^30
+      if (rel0 >= 0 && (int64_t)rel0 + 4 * Q <= Pp) {
+        // tile inside the row: unguarded stores at fixed offsets
+        PT* o = prow + rel0 + lane;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const uint32_t lo = aw[v] - (ah[v] << 8);
+          o[32 * v] = (PT)(lo & 0xFFFFu);
+          o[32 * v + Q] = (PT)(ah[v] & 0xFFFFu);
+          o[32 * v + 2 * Q] = (PT)(lo >> 16);
+          o[32 * v + 3 * Q] = (PT)(ah[v] >> 16);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int j = lane + 32 * v;
+          const uint32_t lo = aw[v] - (ah[v] << 8);
+          const uint32_t val[4] = {lo & 0xFFFFu, ah[v] & 0xFFFFu, lo >> 16, ah[v] >> 16};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t u = (uint32_t)(rel0 + j + q * Q);
+            if (u < (uint64_t)Pp) prow[u] = (PT)val[q];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    idx = next;
   }
 }
 
 // ---------------------------------------------------------------------------
 // stage 2 (Sec. 2.3: de-disperse the sub-bands on the fine DM grid)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load4_u16(const uint16_t* __restrict__ row, int64_t a, uint32_t& x0, uint32_t& x1) {
-  const uint32_t* wp = reinterpret_cast<const uint32_t*>(row + (a & ~(int64_t)1));
-  const uint32_t w0 = __ldg(wp), w1 = __ldg(wp + 1), w2 = __ldg(wp + 2);
-  if (a & 1) {
-    x0 = __funnelshift_r(w0, w1, 16);
-    x1 = __funnelshift_r(w1, w2, 16);
-  } else {
-    x0 = w0;
-    x1 = w1;
-  }
-}
-
 __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long& s2) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -202,128 +300,176 @@ __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long
   }
 }
 
-// One block = (time tile, coarse group k); warp g handles fine DM kG + g.
-// Shared word S[s][j] pairs the uint16 sums P[k][s] at times t0 + emin_s + j
-// and t0 + emin_s + j + Q, so a 32-bit load feeds two outputs. Sums use
+// Persistent blocks walk units (coarse group k, tile of 2 NW outputs) in
+// sub-band chunks; warp g sums fine DM kG + g. A chunk's uint16 stage-1 rows
+// are copied (cp.async, double-buffered) into shared memory as 32-bit words
+// of consecutive pairs (even copy) and re-paired one element later (odd copy),
+// so every delay, even or odd, is a 32-bit load feeding two outputs. Sums use
 //   sum w = sum(lo) + 65536 * sum(hi) (mod 2^32), sum(hi) = sum(w >> 16),
 // exact because every stage-2 sum is below 2^32.
-template <int Q>
-__global__ void __launch_bounds__(kStage2MaxGroup * 32)
+template <int NW, int MAXWARPS>
+__global__ void __launch_bounds__(MAXWARPS * 32, 1)
 k_stage2_u16(const uint16_t* __restrict__ P, int64_t Pp, const int32_t* __restrict__ e2, int ndm, int nsub,
-             int G, int sc, int SW, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
-             longlong2* __restrict__ part, int ntile) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  constexpr int V = Q / 32;
-  const int tile = blockIdx.x, k = blockIdx.y;
-  const int64_t t0 = (int64_t)tile * 2 * Q;
-  const int dfirst = k * G;
-  const int nd = min(G, ndm - dfirst);
-  int32_t* emin = reinterpret_cast<int32_t*>(smem);
-  int32_t* off = emin + nsub;
-  uint32_t* S = smem + (((size_t)nsub * (1 + kStage2MaxGroup) + 3) & ~(size_t)3);
-  for (int s = threadIdx.x; s < nsub; s += blockDim.x) emin[s] = e2[(size_t)dfirst * nsub + s];
-  for (int i = threadIdx.x; i < nd * nsub; i += blockDim.x) {
-    const int g = i / nsub, s = i - g * nsub;
-    off[i] = e2[(size_t)(dfirst + g) * nsub + s] - e2[(size_t)dfirst * nsub + s];
-  }
-  __syncthreads();
+             int G, int nk, int SC, int SWW, int ntile, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
+             longlong2* __restrict__ part, uint32_t one) {
+  extern __shared__ __align__(16) uint32_t smem2[];
+  constexpr int V = NW / 32;
+  uint32_t* Se = smem2;                                  // [2][SC][SWW]
+  uint32_t* So = Se + 2 * (size_t)SC * SWW;              // [SC][SWW]
+  uint32_t* tab = So + (size_t)SC * SWW;                 // [MAXWARPS][SC] word offsets from smem2
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int nchunk = (nsub + SC - 1) / SC;
+  const int nunits = nk * ntile;
+  // steps (unit, chunk) of this block: unit = blockIdx.x + r * gridDim.x
+  const int my_units = (int)blockIdx.x < nunits ? (nunits - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nsteps = my_units * nchunk;
+  const int nq = SWW >> 2;
+
+  auto issue = [&](int step, int buf) {
+    const int unit = blockIdx.x + (step / nchunk) * gridDim.x;
+    const int ch = step % nchunk;
+    const int k = unit / ntile, tile = unit - k * ntile;
+    const int64_t t0 = (int64_t)tile * 2 * NW;
+    const int s0 = ch * SC, ns = min(SC, nsub - s0);
+    uint32_t* dst = Se + (size_t)buf * SC * SWW;
+    for (int ss = warp; ss < ns; ss += nwarps) {
+      const int s = s0 + ss;
+      const int64_t b = (t0 + e2[(size_t)k * G * nsub + s]) & ~(int64_t)7;
+      const uint16_t* src = P + ((size_t)k * nsub + s) * Pp + b;
+      uint32_t* d = dst + (size_t)ss * SWW;
+      for (int q = lane; q < nq; q += 32) cp_async16(d + 4 * q, src + 8 * q);
+    }
+    cp_async_commit();
+  };
+
   uint32_t aw[V], ah[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
-  const int nwq = (SW - 4) >> 2;  // staged words / 4
-  for (int sb = 0; sb < nsub; sb += sc) {
-    const int ns = min(sc, nsub - sb);
-    for (int i = threadIdx.x; i < ns * nwq; i += blockDim.x) {
-      const int ss = i / nwq, j = (i - ss * nwq) << 2;
-      const int s = sb + ss;
-      const uint16_t* prow = P + ((size_t)k * nsub + s) * Pp;
-      const int64_t a = t0 + emin[s] + j;
-      uint32_t x0, x1, y0, y1;
-      load4_u16(prow, a, x0, x1);
-      load4_u16(prow, a + Q, y0, y1);
-      uint4 w;
-      w.x = __byte_perm(x0, y0, 0x5410);
-      w.y = __byte_perm(x0, y0, 0x7632);
-      w.z = __byte_perm(x1, y1, 0x5410);
-      w.w = __byte_perm(x1, y1, 0x7632);
-      *reinterpret_cast<uint4*>(S + (size_t)ss * SW + j) = w;
-    }
+  if (nsteps > 0) issue(0, 0);
+  for (int step = 0; step < nsteps; ++step) {
+    const int buf = step & 1;
+    const int unit = blockIdx.x + (step / nchunk) * gridDim.x;
+    const int ch = step % nchunk;
+    const int k = unit / ntile, tile = unit - k * ntile;
+    const int64_t t0 = (int64_t)tile * 2 * NW;
+    const int dfirst = k * G;
+    const int nd = min(G, ndm - dfirst);
+    const int s0 = ch * SC, ns = min(SC, nsub - s0);
+    uint32_t* cur = Se + (size_t)buf * SC * SWW;
+    cp_async_wait_all();
     __syncthreads();
-    if (warp < nd) {
-      const int32_t* o = off + warp * nsub + sb;
-      const uint32_t* base = S + lane;
-#pragma unroll 4
-      for (int ss = 0; ss < ns; ++ss) {
-        const uint32_t* rw = base + (size_t)ss * SW + o[ss];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const uint32_t w = rw[32 * v];
-          aw[v] += w;
-          ah[v] += w >> 16;
-        }
+    // odd copy: So[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged base
+    for (int ss = warp; ss < ns; ss += nwarps) {
+      const uint32_t* r = cur + (size_t)ss * SWW;
+      uint32_t* o = So + (size_t)ss * SWW;
+      for (int j = 4 * lane; j < SWW - 4; j += 128) {
+        const uint4 a = *reinterpret_cast<const uint4*>(r + j);
+        const uint32_t b = r[j + 4];
+        *reinterpret_cast<uint4*>(o + j) =
+            make_uint4(__funnelshift_r(a.x, a.y, 16), __funnelshift_r(a.y, a.z, 16), __funnelshift_r(a.z, a.w, 16),
+                       __funnelshift_r(a.w, b, 16));
+      }
+    }
+    for (int g = warp; g < nd; g += nwarps) {
+      for (int ss = lane; ss < ns; ss += 32) {
+        const int s = s0 + ss;
+        const int32_t emin = e2[(size_t)dfirst * nsub + s];
+        const int off = e2[(size_t)(dfirst + g) * nsub + s] - emin + (int)((t0 + emin) & 7);
+        const uint32_t* base = (off & 1) ? So : cur;
+        tab[g * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
       }
     }
     __syncthreads();
-  }
-  if (warp < nd) {
-    const int d = dfirst + warp;
-    int32_t* drow = D + (size_t)d * Dp;
-    long long s1 = 0;
-    unsigned long long s2 = 0;
+    if (step + 1 < nsteps) issue(step + 1, buf ^ 1);
+
+    if (warp < nd) {
+      const uint32_t* t = tab + warp * SC;
+      const uint32_t* Sl = smem2 + lane;
+      int ss = 0;
+#pragma unroll 2
+      for (; ss + 1 < ns; ss += 2) {
+        const uint32_t* r0 = Sl + t[ss];
+        const uint32_t* r1 = Sl + t[ss + 1];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int j = lane + 32 * v;
-      const uint32_t lo = aw[v] - (ah[v] << 16);
-      const int64_t ta = t0 + j, tb = t0 + Q + j;
-      if (ta < Td) drow[ta] = (int32_t)lo;
-      if (tb < Td) drow[tb] = (int32_t)ah[v];
-      if (ta < T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
-      if (tb < T) { s1 += ah[v]; s2 += (unsigned long long)ah[v] * ah[v]; }
+        for (int v = 0; v < V; ++v) {
+          const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+          madd(aw[v], w0, one);
+          madd(aw[v], w1, one);
+          ah[v] += (w0 >> 16) + (w1 >> 16);
+        }
+      }
+      if (ss < ns) {
+        const uint32_t* r0 = Sl + t[ss];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const uint32_t w0 = r0[32 * v];
+          madd(aw[v], w0, one);
+          ah[v] += w0 >> 16;
+        }
+      }
     }
-    warp_sum_stats(s1, s2);
-    if (lane == 0) part[(size_t)d * ntile + tile] = make_longlong2(s1, (long long)s2);
+    if (ch == nchunk - 1) {
+      if (warp < nd) {
+        const int d = dfirst + warp;
+        int32_t* drow = D + (size_t)d * Dp;
+        long long s1 = 0;
+        unsigned long long s2 = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int64_t ta = t0 + 2 * (lane + 32 * v);
+          const uint32_t lo = aw[v] - (ah[v] << 16), hi = ah[v];
+          if (ta + 1 < Td && (Dp & 1) == 0) {
+            *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
+          } else {
+            if (ta < Td) drow[ta] = (int32_t)lo;
+            if (ta + 1 < Td) drow[ta + 1] = (int32_t)hi;
+          }
+          if (ta < T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
+          if (ta + 1 < T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
+          aw[v] = ah[v] = 0u;
+        }
+        warp_sum_stats(s1, s2);
+        if (lane == 0) part[(size_t)d * ntile + tile] = make_longlong2(s1, (long long)s2);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
+      }
+    }
   }
 }
 
-// Stage 2 from int32 intermediates (plain layout, one output per load).
-template <int Q>
+// Stage 2 from int32 intermediates (plain layout, one output per load); one
+// block per (tile of 2 NW outputs, coarse group), sub-band chunks in turn.
+template <int NW>
 __global__ void __launch_bounds__(kStage2MaxGroup * 32)
 k_stage2_i32(const int32_t* __restrict__ P, int64_t Pp, const int32_t* __restrict__ e2, int ndm, int nsub,
-             int G, int sc, int SW, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
+             int G, int SC, int SW, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
              longlong2* __restrict__ part, int ntile) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  constexpr int V = 2 * Q / 32;
+  extern __shared__ __align__(16) uint32_t smem3[];
+  constexpr int V = 2 * NW / 32;
   const int tile = blockIdx.x, k = blockIdx.y;
-  const int64_t t0 = (int64_t)tile * 2 * Q;
+  const int64_t t0 = (int64_t)tile * 2 * NW;
   const int dfirst = k * G;
   const int nd = min(G, ndm - dfirst);
-  int32_t* emin = reinterpret_cast<int32_t*>(smem);
-  int32_t* off = emin + nsub;
-  int32_t* S = reinterpret_cast<int32_t*>(smem + (((size_t)nsub * (1 + kStage2MaxGroup) + 3) & ~(size_t)3));
-  for (int s = threadIdx.x; s < nsub; s += blockDim.x) emin[s] = e2[(size_t)dfirst * nsub + s];
-  for (int i = threadIdx.x; i < nd * nsub; i += blockDim.x) {
-    const int g = i / nsub, s = i - g * nsub;
-    off[i] = e2[(size_t)(dfirst + g) * nsub + s] - e2[(size_t)dfirst * nsub + s];
-  }
-  __syncthreads();
+  int32_t* S = reinterpret_cast<int32_t*>(smem3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = 0;
-  for (int sb = 0; sb < nsub; sb += sc) {
-    const int ns = min(sc, nsub - sb);
+  for (int sb = 0; sb < nsub; sb += SC) {
+    const int ns = min(SC, nsub - sb);
     for (int i = threadIdx.x; i < ns * SW; i += blockDim.x) {
       const int ss = i / SW, j = i - ss * SW;
       const int s = sb + ss;
-      S[(size_t)ss * SW + j] = __ldg(P + ((size_t)k * nsub + s) * Pp + t0 + emin[s] + j);
+      S[(size_t)ss * SW + j] = __ldg(P + ((size_t)k * nsub + s) * Pp + t0 + e2[(size_t)dfirst * nsub + s] + j);
     }
     __syncthreads();
     if (warp < nd) {
-      const int32_t* o = off + warp * nsub + sb;
-#pragma unroll 4
       for (int ss = 0; ss < ns; ++ss) {
-        const int32_t* rw = S + (size_t)ss * SW + o[ss] + lane;
+        const int s = sb + ss;
+        const int o = e2[(size_t)(dfirst + warp) * nsub + s] - e2[(size_t)dfirst * nsub + s];
+        const int32_t* rw = S + (size_t)ss * SW + o + lane;
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] += rw[32 * v];
       }
@@ -400,22 +546,41 @@ __global__ void k_stats(const longlong2* __restrict__ part, int ntile, int ndm, 
 // ---------------------------------------------------------------------------
 // boxcar matched filter (Eq. 5 via prefix sums, Sec. 2.4) and outputs (Sec. 2.5)
 // ---------------------------------------------------------------------------
+// One block per (fine DM, tile of kBoxTile outputs): the series with its
+// W_max - 1 look-ahead goes to shared memory, becomes an inclusive prefix sum
+// C, and each output t takes B_W = C[t + W] - C[t] for every width.
+// NWT > 0: exactly NWT widths, per-width constants in registers.
+// NWT = 0: any count up to kMaxWidths, constants in shared memory.
+template <int NWT>
 __global__ void __launch_bounds__(kBoxThreads)
-k_boxcar(const int32_t* __restrict__ D, int64_t Dp, int64_t T, int nw, const int32_t* __restrict__ widths,
+k_boxcar(const int32_t* __restrict__ D, int64_t Dp, int64_t T, int nw_rt, const int32_t* __restrict__ widths,
          int wmax, const SnrConst* __restrict__ cst, int mode, float gamma, float* __restrict__ outf,
          uint8_t* __restrict__ outw, tx_cand* __restrict__ cands, unsigned long long* __restrict__ ncand,
          long long max_cands) {
+  constexpr int NR = NWT > 0 ? NWT : 1;
   extern __shared__ __align__(16) uint32_t C[];
-  __shared__ int32_t sw[kMaxWidths];
-  __shared__ SnrConst sc[kMaxWidths];
   __shared__ uint32_t wsum[kBoxThreads / 32];
+  __shared__ int32_t sW[kMaxWidths];
+  __shared__ SnrConst sC[kMaxWidths];
+  const int nw = NWT > 0 ? NWT : nw_rt;
   const int d = blockIdx.y;
   const int64_t t0 = (int64_t)blockIdx.x * kBoxTile;
   const int n = (int)min((int64_t)kBoxTile, T - t0);
   const int N = n + wmax - 1;
-  if (threadIdx.x < nw) {
-    sw[threadIdx.x] = widths[threadIdx.x];
-    sc[threadIdx.x] = cst[(size_t)d * nw + threadIdx.x];
+  int32_t Wr[NR], hi[NR];
+  float lo[NR], inv[NR];
+  if (NWT > 0) {
+#pragma unroll
+    for (int w = 0; w < NR; ++w) {
+      const SnrConst c = cst[(size_t)d * nw + w];
+      Wr[w] = __ldg(widths + w);
+      hi[w] = c.hi;
+      lo[w] = c.lo;
+      inv[w] = c.inv;
+    }
+  } else if (threadIdx.x < nw) {
+    sW[threadIdx.x] = widths[threadIdx.x];
+    sC[threadIdx.x] = cst[(size_t)d * nw + threadIdx.x];
   }
   const int32_t* drow = D + (size_t)d * Dp + t0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) C[i + 1] = (uint32_t)__ldg(drow + i);
@@ -444,16 +609,41 @@ k_boxcar(const int32_t* __restrict__ D, int64_t Dp, int64_t T, int nw, const int
   __syncthreads();
 
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t cl = C[i];
+    const uint32_t* Ci = C + i;
+    const uint32_t cl = Ci[0];
     float best = -INFINITY;
     int bw = 0;
-    for (int w = 0; w < nw; ++w) {
-      const uint32_t B = C[i + sw[w]] - cl;
-      const float snr = ((float)((int32_t)B - sc[w].hi) - sc[w].lo) * sc[w].inv;
-      if (mode == TX_OUT_CUBE) outf[((size_t)d * nw + w) * T + t0 + i] = snr;
-      if (snr > best) {
-        best = snr;
-        bw = w;
+    if (NWT > 0) {
+      float sv[NR];
+#pragma unroll
+      for (int w = 0; w < NR; ++w) {
+        const uint32_t B = Ci[Wr[w]] - cl;
+        sv[w] = ((float)((int32_t)B - hi[w]) - lo[w]) * inv[w];
+      }
+      if (mode == TX_OUT_CUBE) {
+#pragma unroll
+        for (int w = 0; w < NR; ++w) outf[((size_t)d * nw + w) * T + t0 + i] = sv[w];
+      } else {
+#pragma unroll
+        for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
+        // best width, ties to the smaller width: needed for every point of the
+        // plane, only for the (rare) points above threshold of the candidates
+        if (mode == TX_OUT_PLANE || best >= gamma) {
+          bw = NR - 1;
+#pragma unroll
+          for (int w = NR - 1; w >= 0; --w)
+            if (sv[w] == best) bw = w;
+        }
+      }
+    } else {
+      for (int w = 0; w < nw; ++w) {
+        const uint32_t B = Ci[sW[w]] - cl;
+        const float snr = ((float)((int32_t)B - sC[w].hi) - sC[w].lo) * sC[w].inv;
+        if (mode == TX_OUT_CUBE) outf[((size_t)d * nw + w) * T + t0 + i] = snr;
+        if (snr > best) {
+          best = snr;
+          bw = w;
+        }
       }
     }
     if (mode == TX_OUT_PLANE) {
@@ -484,6 +674,36 @@ k_boxcar(const int32_t* __restrict__ D, int64_t Dp, int64_t T, int nw, const int
   }
 }
 
+// Launch helper: exact width counts 1..12 and 16 get their own instantiation.
+template <int NWT>
+void launch_boxcar_t(dim3 grid, int smem, cudaStream_t st, const int32_t* D, int64_t Dp, int64_t T, int nw,
+                     const int32_t* widths, int wmax, const SnrConst* cst, int mode, float gamma, float* outf,
+                     uint8_t* outw, tx_cand* cands, unsigned long long* nc, long long max_cands) {
+  k_boxcar<NWT><<<grid, kBoxThreads, smem, st>>>(D, Dp, T, nw, widths, wmax, cst, mode, gamma, outf, outw, cands, nc,
+                                                 max_cands);
+}
+
+using BoxLaunch = void (*)(dim3, int, cudaStream_t, const int32_t*, int64_t, int64_t, int, const int32_t*, int,
+                           const SnrConst*, int, float, float*, uint8_t*, tx_cand*, unsigned long long*, long long);
+using BoxKernel = void (*)(const int32_t*, int64_t, int64_t, int, const int32_t*, int, const SnrConst*, int, float,
+                           float*, uint8_t*, tx_cand*, unsigned long long*, long long);
+
+struct BoxEntry {
+  BoxLaunch launch;
+  BoxKernel kernel;
+};
+
+BoxEntry box_entry(int nw) {
+  switch (nw) {
+#define TX_BOX(N) \
+  case N: return {launch_boxcar_t<N>, k_boxcar<N>};
+    TX_BOX(1) TX_BOX(2) TX_BOX(3) TX_BOX(4) TX_BOX(5) TX_BOX(6) TX_BOX(7) TX_BOX(8) TX_BOX(9) TX_BOX(10)
+    TX_BOX(11) TX_BOX(12) TX_BOX(16)
+#undef TX_BOX
+    default: return {launch_boxcar_t<0>, k_boxcar<0>};
+  }
+}
+
 __global__ void k_fill_run(double* run, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) run[2 * i + 1] = -1.0;  // marks "not initialised"
@@ -499,17 +719,10 @@ int upload(T** dst, const std::vector<T>& v) {
   return TX_OK;
 }
 
-int stage1_smem(const tx_plan* p) { return p->m * (2 * p->q1 + 4) * 4 + kStage1MaxCoarse * p->m * 4; }
-
 int stage2_smem(const tx_plan* p) {
-  const int hdr = (int)(((size_t)p->nsub * (1 + kStage2MaxGroup) + 3) & ~(size_t)3) * 4;
-  const int sw = p->interm == TX_INTERM_U16 ? ((kStage2Q + p->span2_max + 3) / 4 * 4 + 4)
-                                            : (2 * kStage2Q + p->span2_max + 4);
-  return hdr + p->nsub_chunk2 * sw * 4;
-}
-
-int stage2_sw(const tx_plan* p) {
-  return p->interm == TX_INTERM_U16 ? ((kStage2Q + p->span2_max + 3) / 4 * 4 + 4) : (2 * kStage2Q + p->span2_max + 4);
+  if (p->interm == TX_INTERM_U16)
+    return (3 * p->nsub_chunk2 * p->sww2 + kStage2MaxGroup * p->nsub_chunk2) * 4;
+  return p->nsub_chunk2 * p->sw2_i32 * 4;
 }
 
 int box_smem(const tx_plan* p) { return (kBoxTile + p->wmax + 4) * 4; }
@@ -520,18 +733,24 @@ int set_stage1_attr(int bytes) {
   return TX_OK;
 }
 
+template <int NW, int MAXWARPS>
+int set_stage2_attr(int bytes) {
+  TX_CUDA(cudaFuncSetAttribute(k_stage2_u16<NW, MAXWARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return TX_OK;
+}
+
 int do_upload(tx_plan* p) {
   int dev = 0;
   TX_CUDA(cudaGetDevice(&dev));
   p->dev.device = dev;
+  TX_CUDA(cudaDeviceGetAttribute(&p->dev.num_sms, cudaDevAttrMultiProcessorCount, dev));
   int rc;
   if ((rc = upload(&p->dev.d1, p->d1))) return rc;
   if ((rc = upload(&p->dev.abase, p->abase))) return rc;
   if ((rc = upload(&p->dev.e2, p->e2))) return rc;
   if ((rc = upload(&p->dev.widths, p->widths))) return rc;
   if ((rc = upload(&p->dev.items1, p->items1))) return rc;
-  if ((rc = upload(&p->dev.span1, p->span1))) return rc;
-  const int s1 = stage1_smem(p);
+  const int s1 = (int)stage1_smem_bytes(p->m, p->q1);
   const bool u16 = p->interm == TX_INTERM_U16;
   switch (p->q1) {
     case 256: rc = u16 ? set_stage1_attr<256, uint16_t>(s1) : set_stage1_attr<256, int32_t>(s1); break;
@@ -541,17 +760,24 @@ int do_upload(tx_plan* p) {
   }
   if (rc) return rc;
   const int s2 = stage2_smem(p);
-  if (u16) TX_CUDA(cudaFuncSetAttribute(k_stage2_u16<kStage2Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
-  else TX_CUDA(cudaFuncSetAttribute(k_stage2_i32<kStage2Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
-  TX_CUDA(cudaFuncSetAttribute(k_boxcar, cudaFuncAttributeMaxDynamicSharedMemorySize, box_smem(p)));
+  if (u16) {
+    if ((rc = p->nw2 == 512 ? set_stage2_attr<512, 16>(s2) : set_stage2_attr<256, 32>(s2))) return rc;
+  } else if (p->nw2 == 512) {
+    TX_CUDA(cudaFuncSetAttribute(k_stage2_i32<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
+  } else {
+    TX_CUDA(cudaFuncSetAttribute(k_stage2_i32<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
+  }
+  TX_CUDA(cudaFuncSetAttribute(box_entry(p->nw).kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, box_smem(p)));
   return TX_OK;
 }
 
 template <int Q, typename PT>
-void launch_stage1(const tx_plan* p, const uint8_t* ring, void* P, cudaStream_t st) {
-  k_stage1<Q, PT><<<(unsigned)p->items1.size(), kStage1Warps * 32, stage1_smem(p), st>>>(
-      ring, p->Rp, p->ring_pad, p->dev.items1, p->dev.span1, p->dev.d1, p->nchan, p->m, p->nsub, p->dev.abase,
-      reinterpret_cast<PT*>(P), p->Pp);
+void launch_stage1(const tx_plan* p, const uint8_t* ring, int64_t start, void* P, cudaStream_t st) {
+  const int nitems = (int)p->items1.size();
+  const int grid = std::min(nitems, std::max(p->dev.num_sms, 1));
+  k_stage1<Q, PT><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
+      ring, (int)p->R, (int)start, p->dev.items1, nitems, p->dev.d1, p->nchan, p->m, p->nsub, p->dev.abase,
+      reinterpret_cast<PT*>(P), p->Pp, 1u);
 }
 
 int check_beam(const tx_plan* p, const tx_beam* b) {
@@ -563,21 +789,52 @@ int check_beam(const tx_plan* p, const tx_beam* b) {
   return TX_OK;
 }
 
-// Writes a block (plan layout) of n samples into ring rows at byte offset off.
-int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64_t off, cudaStream_t st) {
+int64_t mod(int64_t a, int64_t r) { return ((a % r) + r) % r; }
+
+// Writes n samples (plan layout, rows of n samples for FT) into the ring at
+// physical positions [pos, pos + n) mod R, splitting at the wrap.
+int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64_t pos, cudaStream_t st) {
   if (n <= 0) return TX_OK;
-  if (p->layout == TX_LAYOUT_TF) {
-    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((p->nchan + 63) / 64));
-    k_ingest_tf<<<grid, 256, 0, st>>>(src, n, p->nchan, ring, p->Rp, off);
-  } else if (n % 16 == 0 && off % 16 == 0 && ((uintptr_t)src & 15) == 0) {
-    const int64_t n16 = n / 16;
-    dim3 grid((unsigned)std::min<int64_t>((n16 + 255) / 256, 64), (unsigned)p->nchan);
-    k_ingest_ft16<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4*>(src), n16, ring, p->Rp, off);
-  } else {
-    dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 256), (unsigned)p->nchan);
-    k_ingest_ft<<<grid, 256, 0, st>>>(src, n, ring, p->Rp, off);
+  const int64_t R = p->R;
+  int64_t done = 0;
+  pos = mod(pos, R);
+  while (done < n) {
+    const int64_t len = std::min(n - done, R - pos);
+    if (p->layout == TX_LAYOUT_TF) {
+      const int vec = (p->nchan % 16 == 0) && (pos % 16 == 0) && (((uintptr_t)src & 15) == 0);
+      dim3 grid((unsigned)((len + 63) / 64), (unsigned)((p->nchan + 63) / 64));
+      k_ingest_tf<<<grid, 256, 0, st>>>(src, done, len, p->nchan, ring, R, pos, vec);
+    } else {
+      const int vec = (n % 16 == 0) && (done % 16 == 0) && (len % 16 == 0) && (pos % 16 == 0) &&
+                      (((uintptr_t)src & 15) == 0);
+      dim3 grid((unsigned)std::min<int64_t>((len + 4095) / 4096, 64), (unsigned)p->nchan);
+      k_ingest_ft<<<grid, 256, 0, st>>>(src, n, done, len, ring, R, pos, vec);
+    }
+    TX_CUDA(cudaGetLastError());
+    done += len;
+    pos = 0;
   }
-  TX_CUDA(cudaGetLastError());
+  return TX_OK;
+}
+
+// Copies the carried tail (the L samples before `head`, per channel) between
+// the ring and a host buffer [nchan][L].
+int copy_tail(const tx_plan* p, const tx_beam* b, uint8_t* host, bool to_host) {
+  const int64_t L = p->L, R = p->R;
+  if (L <= 0) return TX_OK;
+  const int64_t a = mod(b->head - L, R);
+  const int64_t first = std::min(L, R - a);
+  if (to_host) {
+    TX_CUDA(cudaMemcpy2D(host, (size_t)L, b->ring + a, (size_t)R, (size_t)first, (size_t)p->nchan, cudaMemcpyDeviceToHost));
+    if (first < L)
+      TX_CUDA(cudaMemcpy2D(host + first, (size_t)L, b->ring, (size_t)R, (size_t)(L - first), (size_t)p->nchan,
+                           cudaMemcpyDeviceToHost));
+  } else {
+    TX_CUDA(cudaMemcpy2D(b->ring + a, (size_t)R, host, (size_t)L, (size_t)first, (size_t)p->nchan, cudaMemcpyHostToDevice));
+    if (first < L)
+      TX_CUDA(cudaMemcpy2D(b->ring, (size_t)R, host + first, (size_t)L, (size_t)(L - first), (size_t)p->nchan,
+                           cudaMemcpyHostToDevice));
+  }
   return TX_OK;
 }
 
@@ -606,7 +863,6 @@ void tx_plan_destroy(tx_plan* p) {
     cudaFree(p->dev.e2);
     cudaFree(p->dev.widths);
     cudaFree(p->dev.items1);
-    cudaFree(p->dev.span1);
     cudaSetDevice(prev);
   }
   delete p;
@@ -621,9 +877,7 @@ int32_t tx_beam_create(const tx_plan* p, tx_beam** out) {
   if (!b) { set_error("out of host memory"); return TX_ERR_OOM; }
   b->plan = p;
   cudaGetDevice(&b->device);
-  const size_t rbytes = (size_t)p->nchan * p->Rp;
-  cudaError_t e = cudaMalloc((void**)&b->ring[0], rbytes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->ring[1], rbytes);
+  cudaError_t e = cudaMalloc((void**)&b->ring, (size_t)p->nchan * p->R);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->run, (size_t)p->ndm * 2 * sizeof(double));
   if (e != cudaSuccess) {
     set_error("beam allocation failed: %s", cudaGetErrorString(e));
@@ -644,13 +898,11 @@ int32_t tx_beam_reset(const tx_plan* p, tx_beam* b, void* stream) {
   int rc = check_beam(p, b);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t rbytes = (size_t)p->nchan * p->Rp;
-  TX_CUDA(cudaMemsetAsync(b->ring[0], 0, rbytes, st));
-  TX_CUDA(cudaMemsetAsync(b->ring[1], 0, rbytes, st));
+  TX_CUDA(cudaMemsetAsync(b->ring, 0, (size_t)p->nchan * p->R, st));
   TX_CUDA(cudaMemsetAsync(b->run, 0, (size_t)p->ndm * 2 * sizeof(double), st));
   k_fill_run<<<(p->ndm + 255) / 256, 256, 0, st>>>(b->run, p->ndm);
   TX_CUDA(cudaGetLastError());
-  b->cur = 0;
+  b->head = p->head0;
   b->nblocks = 0;
   return TX_OK;
 }
@@ -659,8 +911,8 @@ int32_t tx_beam_prime(const tx_plan* p, tx_beam* b, const uint8_t* d_tail, void*
   int rc = check_beam(p, b);
   if (rc) return rc;
   if (!d_tail && p->L > 0) { set_error("null tail"); return TX_ERR_INVALID_ARG; }
-  // the next execute copies logical [T, T + L) of the current ring
-  return ingest(p, d_tail, p->L, b->ring[b->cur], p->ring_pad + p->T, (cudaStream_t)stream);
+  // the tail sits in the L positions before the next block
+  return ingest(p, d_tail, p->L, b->ring, b->head - p->L, (cudaStream_t)stream);
 }
 
 int32_t tx_beam_blocks(const tx_beam* b, int64_t* n) {
@@ -675,12 +927,10 @@ int32_t tx_beam_export(const tx_plan* p, const tx_beam* b, void* h_dst, int64_t 
   if (!h_dst || bytes < p->export_bytes) { set_error("export buffer needs %lld bytes", (long long)p->export_bytes); return TX_ERR_INVALID_ARG; }
   uint8_t* h = static_cast<uint8_t*>(h_dst);
   std::memset(h, 0, 64);
-  const int64_t hdr[4] = {0x54584245414d31LL, p->nchan, p->L, b->nblocks};
+  const int64_t hdr[4] = {0x54584245414d32LL, p->nchan, p->L, b->nblocks};
   std::memcpy(h, hdr, sizeof(hdr));
   TX_CUDA(cudaDeviceSynchronize());
-  if (p->L > 0)
-    TX_CUDA(cudaMemcpy2D(h + 64, (size_t)p->L, b->ring[b->cur] + p->ring_pad + p->T, (size_t)p->Rp, (size_t)p->L,
-                         (size_t)p->nchan, cudaMemcpyDeviceToHost));
+  if ((rc = copy_tail(p, b, h + 64, true))) return rc;
   TX_CUDA(cudaMemcpy(h + 64 + (size_t)p->nchan * p->L, b->run, (size_t)p->ndm * 16, cudaMemcpyDeviceToHost));
   return TX_OK;
 }
@@ -692,11 +942,9 @@ int32_t tx_beam_import(const tx_plan* p, tx_beam* b, const void* h_src, int64_t 
   const uint8_t* h = static_cast<const uint8_t*>(h_src);
   int64_t hdr[4];
   std::memcpy(hdr, h, sizeof(hdr));
-  if (hdr[0] != 0x54584245414d31LL || hdr[1] != p->nchan || hdr[2] != p->L) { set_error("export does not match this plan"); return TX_ERR_INVALID_ARG; }
+  if (hdr[0] != 0x54584245414d32LL || hdr[1] != p->nchan || hdr[2] != p->L) { set_error("export does not match this plan"); return TX_ERR_INVALID_ARG; }
   TX_CUDA(cudaDeviceSynchronize());
-  if (p->L > 0)
-    TX_CUDA(cudaMemcpy2D(b->ring[b->cur] + p->ring_pad + p->T, (size_t)p->Rp, h + 64, (size_t)p->L, (size_t)p->L,
-                         (size_t)p->nchan, cudaMemcpyHostToDevice));
+  if ((rc = copy_tail(p, b, const_cast<uint8_t*>(h + 64), false))) return rc;
   TX_CUDA(cudaMemcpy(b->run, h + 64 + (size_t)p->nchan * p->L, (size_t)p->ndm * 16, cudaMemcpyHostToDevice));
   b->nblocks = hdr[3];
   return TX_OK;
@@ -707,8 +955,7 @@ void tx_beam_destroy(tx_beam* b) {
   int prev = 0;
   cudaGetDevice(&prev);
   if (b->device >= 0) cudaSetDevice(b->device);
-  cudaFree(b->ring[0]);
-  cudaFree(b->ring[1]);
+  cudaFree(b->ring);
   cudaFree(b->run);
   cudaSetDevice(prev);
   delete b;
@@ -740,26 +987,20 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   uint8_t* ws = static_cast<uint8_t*>(d_workspace);
   TX_MARK(0);
 
-  // Sec. 2.3 data flow: carried tail + new block -> next ring (steps 1, 2, 4)
-  uint8_t* cur = b->ring[b->cur];
-  uint8_t* nxt = b->ring[b->cur ^ 1];
-  if (p->L > 0) {
-    dim3 grid((unsigned)std::min<int64_t>((p->L + 255) / 256, 128), (unsigned)p->nchan);
-    k_tail<<<grid, 256, 0, st>>>(cur, nxt, p->Rp, p->ring_pad + p->T, p->ring_pad, p->L);
-    TX_CUDA(cudaGetLastError());
-  }
-  if ((rc = ingest(p, d_block, p->T, nxt, p->ring_pad + p->L, st))) return rc;
-  b->cur ^= 1;
+  // Sec. 2.3 data flow: the block lands behind the carried tail (steps 1, 2, 4)
+  if ((rc = ingest(p, d_block, p->T, b->ring, b->head, st))) return rc;
+  const int64_t start = mod(b->head - p->L, p->R);
+  b->head = mod(b->head + p->T, p->R);
   TX_MARK(1);
 
   // stage 1
   void* P = ws + p->ws_P;
   const bool u16 = p->interm == TX_INTERM_U16;
   switch (p->q1) {
-    case 256: u16 ? launch_stage1<256, uint16_t>(p, nxt, P, st) : launch_stage1<256, int32_t>(p, nxt, P, st); break;
-    case 128: u16 ? launch_stage1<128, uint16_t>(p, nxt, P, st) : launch_stage1<128, int32_t>(p, nxt, P, st); break;
-    case 64: u16 ? launch_stage1<64, uint16_t>(p, nxt, P, st) : launch_stage1<64, int32_t>(p, nxt, P, st); break;
-    default: u16 ? launch_stage1<32, uint16_t>(p, nxt, P, st) : launch_stage1<32, int32_t>(p, nxt, P, st); break;
+    case 256: u16 ? launch_stage1<256, uint16_t>(p, b->ring, start, P, st) : launch_stage1<256, int32_t>(p, b->ring, start, P, st); break;
+    case 128: u16 ? launch_stage1<128, uint16_t>(p, b->ring, start, P, st) : launch_stage1<128, int32_t>(p, b->ring, start, P, st); break;
+    case 64: u16 ? launch_stage1<64, uint16_t>(p, b->ring, start, P, st) : launch_stage1<64, int32_t>(p, b->ring, start, P, st); break;
+    default: u16 ? launch_stage1<32, uint16_t>(p, b->ring, start, P, st) : launch_stage1<32, int32_t>(p, b->ring, start, P, st); break;
   }
   TX_CUDA(cudaGetLastError());
   TX_MARK(2);
@@ -770,16 +1011,29 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   const int64_t Dp = series ? p->Td : p->Dp;
   longlong2* part = reinterpret_cast<longlong2*>(ws + p->ws_part);
   {
-    dim3 grid((unsigned)p->ntile2, (unsigned)p->nk);
     const int threads = std::min(p->group, kStage2MaxGroup) * 32;
-    if (u16)
-      k_stage2_u16<kStage2Q><<<grid, threads, stage2_smem(p), st>>>(
-          static_cast<const uint16_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nsub_chunk2, stage2_sw(p),
-          D, Dp, p->Td, p->T, part, p->ntile2);
-    else
-      k_stage2_i32<kStage2Q><<<grid, threads, stage2_smem(p), st>>>(
-          static_cast<const int32_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nsub_chunk2, stage2_sw(p),
-          D, Dp, p->Td, p->T, part, p->ntile2);
+    if (u16) {
+      const int nunits = p->nk * p->ntile2;
+      const int grid = std::min(nunits, std::max(p->dev.num_sms, 1));
+      if (p->nw2 == 512)
+        k_stage2_u16<512, 16><<<grid, threads, stage2_smem(p), st>>>(
+            static_cast<const uint16_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nk, p->nsub_chunk2,
+            p->sww2, p->ntile2, D, Dp, p->Td, p->T, part, 1u);
+      else
+        k_stage2_u16<256, 32><<<grid, threads, stage2_smem(p), st>>>(
+            static_cast<const uint16_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nk, p->nsub_chunk2,
+            p->sww2, p->ntile2, D, Dp, p->Td, p->T, part, 1u);
+    } else {
+      dim3 grid((unsigned)p->ntile2, (unsigned)p->nk);
+      if (p->nw2 == 512)
+        k_stage2_i32<512><<<grid, threads, stage2_smem(p), st>>>(
+            static_cast<const int32_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nsub_chunk2, p->sw2_i32,
+            D, Dp, p->Td, p->T, part, p->ntile2);
+      else
+        k_stage2_i32<256><<<grid, threads, stage2_smem(p), st>>>(
+            static_cast<const int32_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nsub_chunk2, p->sw2_i32,
+            D, Dp, p->Td, p->T, part, p->ntile2);
+    }
     TX_CUDA(cudaGetLastError());
   }
   TX_MARK(3);
@@ -794,9 +1048,10 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
     float* outf = static_cast<float*>(d_out);
     uint8_t* outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(d_out) + (size_t)p->ndm * p->T * 4 : nullptr;
     dim3 grid((unsigned)p->ntile3, (unsigned)p->ndm);
-    k_boxcar<<<grid, kBoxThreads, box_smem(p), st>>>(
-        D, p->Dp, p->T, p->nw, p->dev.widths, p->wmax, cst, p->output, p->gamma, outf, outw,
-        static_cast<tx_cand*>(d_out), reinterpret_cast<unsigned long long*>(d_ncand), (long long)p->max_cands);
+    auto* cands = static_cast<tx_cand*>(d_out);
+    auto* nc = reinterpret_cast<unsigned long long*>(d_ncand);
+    box_entry(p->nw).launch(grid, box_smem(p), st, D, p->Dp, p->T, p->nw, p->dev.widths, p->wmax, cst, p->output,
+                            p->gamma, outf, outw, cands, nc, (long long)p->max_cands);
     TX_CUDA(cudaGetLastError());
   } else {
     TX_MARK(4);

@@ -28,6 +28,18 @@ void set_error(const char* fmt, ...) {
 }
 
 static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Raw window per channel: quarters reach byte 3q + (staged words) with staged
+// words <= q + span + 30 (span <= q, 15 for the misalignment, 15 to whole 16-byte
+// groups), rounded to 16-byte chunks.
+int64_t stage1_raw_bytes(int q) { return (5 * (int64_t)q + 48 + 15) / 16 * 16; }
+int64_t stage1_staged_words(int q) { return 2 * (int64_t)q + 32; }
+
+int64_t stage1_smem_bytes(int m, int q) {
+  // staged words, raw prefetch buffer, address table (rows padded to even length)
+  return (int64_t)m * stage1_staged_words(q) * 4 + (int64_t)m * stage1_raw_bytes(q) +
+         (int64_t)kStage1MaxCoarse * ((m + 1) & ~1) * 4;
+}
 static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Eq. 1 in samples: rnd(K DM (1/f^2 - 1/f_ref^2) / t_samp), rnd = llround.
@@ -155,7 +167,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
 
   // ---- stage-2 layout -------------------------------------------------------
   // P row (k, s) starts at absolute time abase = min_d d2 rounded down to 16 so
-  // stage-1 tiles and stage-2 reads stay aligned; e2 = d2 - abase >= 0.
+  // stage-1 tiles stay aligned; e2 = d2 - abase >= 0.
   p->Td = p->T + p->wmax - 1;
   p->abase.resize((size_t)nk * nsub);
   p->e2.resize((size_t)ndm * nsub);
@@ -173,31 +185,40 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
       e2max = std::max(e2max, v);
     }
   p->span2_max = span2;
-  const int64_t tt2 = 2 * (int64_t)kStage2Q;
+  // Stage-2 tiles hold nw2 uint16 pairs (2 * nw2 outputs).
+  // A sub-band's staged window starts at the tile start + emin rounded down to
+  // 8 elements (16 bytes) and spans the tile, the group's delay spread and
+  // that alignment: sww2 32-bit words.
+  p->nw2 = G <= 16 ? 512 : 256;
+  const int64_t tt2 = 2 * (int64_t)p->nw2;
   p->ntile2 = (int32_t)((p->Td + tt2 - 1) / tt2);
-  // stage 2 reads u16 indices up to the last tile's end + max(e2) + 19
-  // (staged spread plus aligned triple-word loads)
-  p->Pp = round_up(p->ntile2 * tt2 + e2max + 32, 64);
-  {
-    const int64_t words = round_up(kStage2Q + span2 + 4, 4);
-    const int64_t per_sub = words * 4;
-    const int64_t fixed = (int64_t)kStage2MaxGroup * nsub * 4 + nsub * 4 + 64;
-    int64_t sc = (kSmemBudget - fixed) / per_sub;
-    if (p->interm == TX_INTERM_I32) sc = (kSmemBudget - fixed) / (round_up(2 * kStage2Q + span2 + 4, 4) * 4);
-    if (sc < 1) { set_error("stage-2 delay spread within a DM group (%d samples) too large; use a smaller group", span2); return TX_ERR_UNSUPPORTED; }
-    p->nsub_chunk2 = (int32_t)std::min<int64_t>(sc, nsub);
+  p->sww2 = (int32_t)round_up(p->nw2 + (span2 + 7 + 2) / 2 + 6, 4);
+  const int64_t last_t0 = (int64_t)(p->ntile2 - 1) * tt2;
+  // uint16 path reads [base, base + 2 sww2) with base <= t0 + 15; int32 path
+  // reads [t0 + emin, + tt2 + span2 + 16)
+  p->Pp = round_up(std::max<int64_t>(last_t0 + 16 + 2 * (int64_t)p->sww2, last_t0 + 16 + tt2 + span2 + 16) + 16, 64);
+  if (p->interm == TX_INTERM_U16) {
+    // double-buffered even copy + odd copy + address table
+    const int64_t per_sub = 3 * (int64_t)p->sww2 * 4 + (int64_t)kStage2MaxGroup * 4 + 8;
+    p->nsub_chunk2 = (int32_t)std::min<int64_t>(nsub, (kSmemMax - 1024) / per_sub);
+  } else {
+    p->sw2_i32 = (int32_t)(tt2 + span2 + 16);
+    const int64_t per_sub = (int64_t)p->sw2_i32 * 4 + (int64_t)kStage2MaxGroup * 4 + 8;
+    p->nsub_chunk2 = (int32_t)std::min<int64_t>(nsub, (kSmemMax - 1024) / per_sub);
   }
+  if (p->nsub_chunk2 < 1) { set_error("stage-2 delay spread within a DM group (%d samples) too large; use a smaller group", span2); return TX_ERR_UNSUPPORTED; }
   p->Dp = round_up(p->Td + 8, 8);
   p->ntile3 = (int32_t)((p->T + kBoxTile - 1) / kBoxTile);
 
   // ---- stage-1 work list ----------------------------------------------------
-  // quarter length q1: the largest of 256/128/64/32 whose staged tile fits
+  // quarter length q1: the largest of 256/128/64/32 whose staged words, raw
+  // prefetch buffer and address table fit in shared memory
   int q1 = 256;
-  while (q1 > 32 && (int64_t)m * (2 * q1 + 4) * 4 + (int64_t)kStage1MaxCoarse * m * 4 > kSmemBudget) q1 /= 2;
+  while (q1 > 32 && stage1_smem_bytes(m, q1) > kSmemMax) q1 /= 2;
+  if (stage1_smem_bytes(m, q1) > kSmemMax) { set_error("too many channels per sub-band for stage 1 (%d)", m); return TX_ERR_UNSUPPORTED; }
   p->q1 = q1;
   p->span1_max = q1;
   const int64_t tt1 = 4 * (int64_t)q1;
-  int64_t max_phys = 0;
   for (int s = 0; s < nsub; ++s) {
     int kb = 0;
     while (kb < nk) {
@@ -216,22 +237,26 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
         lo = std::min<int64_t>(lo, p->abase[(size_t)k * nsub + s]);
         hi = std::max<int64_t>(hi, (int64_t)p->abase[(size_t)k * nsub + s] + p->Pp);
       }
-      for (int64_t t0 = floor_div(lo, tt1) * tt1; t0 < hi; t0 += tt1) {
-        p->items1.push_back(Stage1Item{s, kb, ke, (int32_t)t0});
-        p->span1.push_back(span);
-        for (int c = s * m; c < (s + 1) * m; ++c)
-          max_phys = std::max<int64_t>(max_phys, t0 + p->d1[(size_t)kb * nchan + c] + tt1 + span + 16);
-      }
+      for (int64_t t0 = floor_div(lo, tt1) * tt1; t0 < hi; t0 += tt1)
+        p->items1.push_back(Stage1Item{s, kb, ke, (int32_t)t0, span, 0, 0, 0});
       kb = ke;
     }
   }
+  // Time-major order: blocks working at the same time read overlapping input
+  // windows of every sub-band, which keeps the ring's working set in L2.
+  std::stable_sort(p->items1.begin(), p->items1.end(), [](const Stage1Item& a, const Stage1Item& b) {
+    return a.tau0 != b.tau0 ? a.tau0 < b.tau0 : (a.s != b.s ? a.s < b.s : a.kb < b.kb);
+  });
 
-  // ---- ring rows ---------------------------------------------------------------
-  // Row layout: [pad | carried tail L | new block T | zeros]; pad puts the
-  // block at a 64-byte boundary. Stage 1 may read past L + T (tile rounding):
-  // those bytes stay zero and only feed sums that stage 2 never reads.
-  p->ring_pad = (64 - p->L % 64) % 64;
-  p->Rp = round_up(std::max<int64_t>(p->ring_pad + p->L + p->T + 16, p->ring_pad + max_phys + 16), 64);
+  // ---- ring ----------------------------------------------------------------------
+  // Each channel is a circular buffer of R bytes; the next block lands at
+  // `head` and the samples of an execute's buffer are the L before it and the
+  // T of the block. R and the first head are multiples of 64 so a block of a
+  // multiple of 64 samples always lands 64-byte aligned. Stage 1's reads past
+  // the buffer (tile rounding) wrap onto older samples and only feed sums that
+  // stage 2 never reads.
+  p->R = round_up(p->L + p->T + 64, 64);
+  p->head0 = round_up(p->L, 64) % p->R;
 
   // ---- sizes ---------------------------------------------------------------------
   const int64_t psz = p->interm == TX_INTERM_U16 ? 2 : 4;
@@ -247,7 +272,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
     case TX_OUT_CUBE: p->out_bytes = (int64_t)ndm * p->nw * p->T * 4; break;
     default: p->out_bytes = (int64_t)ndm * p->Td * 4; break;
   }
-  p->beam_bytes = 2 * (int64_t)nchan * p->Rp + (int64_t)ndm * 16 + 16;
+  p->beam_bytes = (int64_t)nchan * p->R + (int64_t)ndm * 16 + 16;
   p->export_bytes = 64 + (int64_t)nchan * p->L + (int64_t)ndm * 16;
   return TX_OK;
 }
@@ -296,6 +321,8 @@ int32_t tx_plan_get_info(const tx_plan* p, tx_plan_info* info) {
   info->workspace_bytes = p->ws_bytes; info->beam_state_bytes = p->beam_bytes;
   info->out_bytes = p->out_bytes; info->export_bytes = p->export_bytes;
   info->block_bytes = (int64_t)p->nchan * p->T;
+  info->ring_len = p->R;
+  info->ring_head0 = p->head0;
   return TX_OK;
 }
 

@@ -20,11 +20,11 @@ constexpr double kDispersion = 4.148808e3;
 // four outputs whatever the per-channel delay.
 constexpr int kStage1MaxCoarse = 32;   // coarse DMs that share one staged tile
 constexpr int kStage1Warps = 16;
-constexpr int kSmemBudget = 200 * 1024;
+constexpr int kSmemMax = 232448;       // opt-in dynamic shared memory per block (227 KB)
 
 // ---- stage 2 (sub-bands -> fine DMs) tiling ---------------------------------
-// Stage-2 words pair the uint16 sums of times j and j+q2 (q2 = kStage2Q).
-constexpr int kStage2Q = 256;
+// A stage-2 tile is nw2 32-bit words of uint16 pairs (two outputs each):
+// 512 words for groups of up to 16 fine DMs (16 warps), 256 beyond.
 constexpr int kStage2MaxGroup = 32;    // one warp per fine DM of a group
 
 // ---- matched filter ---------------------------------------------------------
@@ -33,9 +33,10 @@ constexpr int kBoxThreads = 256;
 constexpr int kMaxWidths = 32;
 constexpr int kMaxWidth = 4096;
 
-// Stage-1 work item: sub-band s, coarse DMs [kb, ke), first time tau0.
+// Stage-1 work item: sub-band s, coarse DMs [kb, ke), times [tau0, tau0 + 4 q1),
+// span = max over the sub-band's channels of d1[ke-1][c] - d1[kb][c].
 struct Stage1Item {
-  int32_t s, kb, ke, tau0;
+  int32_t s, kb, ke, tau0, span, pad0, pad1, pad2;
 };
 
 // Per (fine DM, width) constants of the S/N normalisation (Eq. 5):
@@ -49,15 +50,18 @@ struct SnrConst {
 
 struct DevicePlan {
   int device = -1;
+  int num_sms = 0;
   int32_t* d1 = nullptr;         // [nk][nchan]
   int32_t* abase = nullptr;      // [nk][nsub]
   int32_t* e2 = nullptr;         // [ndm][nsub]
   int32_t* widths = nullptr;     // [nw]
   Stage1Item* items1 = nullptr;  // [n_items1]
-  int32_t* span1 = nullptr;      // [n_items1] staged delay spread per item
 };
 
 void set_error(const char* fmt, ...);
+int64_t stage1_raw_bytes(int q);
+int64_t stage1_staged_words(int q);
+int64_t stage1_smem_bytes(int m, int q);
 
 }  // namespace tx
 
@@ -85,16 +89,18 @@ struct tx_plan {
   int64_t Td = 0;                 // series length T + wmax - 1
   int64_t Pp = 0;                 // P row pitch (elements)
   int64_t Dp = 0;                 // D row pitch (int32 elements)
-  int64_t ring_pad = 0;           // ring row: [pad | tail L | block T | zeros]
-  int64_t Rp = 0;                 // ring row pitch (bytes)
+  int64_t R = 0;                  // ring bytes per channel (circular)
+  int64_t head0 = 0;              // where a fresh beam's first block lands
   int32_t q1 = 256;               // stage-1 quarter length (words)
   int32_t span1_max = 256;        // staged delay spread limit of stage 1
   int32_t span2_max = 0;          // max stage-2 delay spread within a group
+  int32_t nw2 = 512;              // stage-2 tile words (2 * nw2 outputs)
   int32_t ntile2 = 0;             // stage-2 tiles over the series
+  int32_t sww2 = 0;               // stage-2 staged words per sub-band (uint16 path)
+  int32_t sw2_i32 = 0;            // stage-2 staged elements per sub-band (int32 path)
   int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
   int32_t ntile3 = 0;             // boxcar tiles over [0, T)
   std::vector<tx::Stage1Item> items1;
-  std::vector<int32_t> span1;
 
   // ---- workspace carve-up (bytes) -------------------------------------------
   int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_bytes = 0;
@@ -109,10 +115,9 @@ struct tx_plan {
 struct tx_beam {
   const tx_plan* plan = nullptr;
   int device = -1;
-  uint8_t* ring[2] = {nullptr, nullptr};
-  int cur = 0;
-  double* run = nullptr;          // [ndm][2] running (mu, var)
-  int32_t* run_init = nullptr;    // [1]
+  uint8_t* ring = nullptr;        // [nchan][R] circular
+  int64_t head = 0;               // where the next block lands
+  double* run = nullptr;          // [ndm][2] running (mu, var); var < 0 = unset
   int64_t nblocks = 0;
 };
 

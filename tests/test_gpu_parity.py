@@ -313,9 +313,27 @@ def test_meerkat_full_size_sampled(tx, meerkat_case):
     _check_plane(s[sample].cpu().numpy(), w[sample].cpu().numpy(), snr)
     del out
     torch.cuda.empty_cache()
-    plan_c = make_plan(tx, wl, output="cands", snr_threshold=gamma, max_cands=1 << 22)
+    plan_c = make_plan(tx, wl, output="cands", snr_threshold=gamma, max_cands=1 << 24)
     (out, nc, _), = run_blocks(tx, plan_c, X)[0]
     got, n = tx.cands_view(plan_c, out, nc)
-    assert n < (1 << 22)
+    assert n < (1 << 24)
     sub = got[np.isin(got["dm_index"], sample)]
     _check_cands(sub, sub.size, snr, gamma, dm_indices=sample)
+
+
+@pytest.mark.parametrize("widths", [(1,), (3, 7), tuple(range(1, 17)), tuple(range(1, 21)), (1, 2, 4, 8, 16, 32, 64, 100, 200, 400, 800, 1000)])
+@pytest.mark.parametrize("output", ["cube", "plane"])
+def test_boxcar_width_sets(tx, widths, output):
+    """Every width-count code path (exact counts and the generic one) against the oracle."""
+    wl = synth.tiny_workload(nchan=32, nsub=4, ndm=6, nsamp=3000, widths=widths)
+    plan = make_plan(tx, wl, output=output)
+    op = oracle_plan(wl)
+    X = synth.make_spectrum(wl, plan.overlap + wl.nsamp,
+                            [synth.Pulse(dm=30.0, t_arr=1200.0, fwhm=12.0, amp=9.0)], seed=11)
+    (out, _, _), = run_blocks(tx, plan, X)[0]
+    snr, _ = _oracle_snr(X, op, wl.nsamp)
+    if output == "cube":
+        check_snr(tx.cube_view(plan, out).cpu().numpy(), snr)
+    else:
+        s, w = tx.plane_view(plan, out)
+        _check_plane(s.cpu().numpy(), w.cpu().numpy(), snr)

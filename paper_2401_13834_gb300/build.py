@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cxx = os.environ.get("CXX", "g++")
     cmd_plan = [cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-I", INCLUDE,
                 "-I", CSRC, "-c", os.path.join(CSRC, "plan.cpp"), "-o", obj_plan]
-    cmd_kern = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    cmd_kern = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
                 "-Xptxas", "-v" if verbose else "-O3",
                 "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, "kernels.cu"), "-o", obj_kern]
     with ThreadPoolExecutor(2) as ex:

@@ -48,6 +48,12 @@ __device__ __forceinline__ void madd(uint32_t& acc, uint32_t a, uint32_t one) {
   asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(a), "r"(one));
 }
 
+// acc += a >> 16 as one integer multiply-add on the FMA pipe: the high 32 bits
+// of a * 65536 are a >> 16.
+__device__ __forceinline__ void madd_hi16(uint32_t& acc, uint32_t a) {
+  asm("mad.hi.u32 %0, %1, 65536, %0;" : "+r"(acc) : "r"(a));
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -129,24 +135,86 @@ __global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ s
 // ---------------------------------------------------------------------------
 // stage 1 (Sec. 2.3: de-disperse each sub-band on the coarse DM grid)
 // ---------------------------------------------------------------------------
+// Sums one coarse DM over the sub-band's m channels for VW words per lane,
+// starting at word jbase of the tile, and stores the 4 * VW * 32 outputs.
+template <int Q, int VW, typename PT>
+__device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const uint32_t* __restrict__ t, int m,
+                                           uint32_t one, int lane, int jbase, PT* __restrict__ prow, int rel0,
+                                           int64_t Pp) {
+  uint32_t aw[VW], ah[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+  const uint32_t* base = S + jbase + lane;
+  int c = 0;
+#pragma unroll 2
+  for (; c + 1 < m; c += 2) {
+    const uint2 oo = *reinterpret_cast<const uint2*>(t + c);
+    const uint32_t* r0 = base + oo.x;
+    const uint32_t* r1 = base + oo.y;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+      madd(aw[v], w0, one);
+      madd(aw[v], w1, one);
+      ah[v] += __byte_perm(w0, 0u, 0x4341) + __byte_perm(w1, 0u, 0x4341);
+    }
+  }
+  if (c < m) {
+    const uint32_t* r0 = base + t[c];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const uint32_t w0 = r0[32 * v];
+      madd(aw[v], w0, one);
+      ah[v] += __byte_perm(w0, 0u, 0x4341);
+    }
+  }
+  const int r = rel0 + jbase;
+  if (r >= 0 && (int64_t)r + 4 * Q - jbase <= Pp) {
+    // every output inside the row: unguarded stores at fixed offsets
+    PT* o = prow + r + lane;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const uint32_t lo = aw[v] - (ah[v] << 8);
+      o[32 * v] = (PT)(lo & 0xFFFFu);
+      o[32 * v + Q] = (PT)(ah[v] & 0xFFFFu);
+      o[32 * v + 2 * Q] = (PT)(lo >> 16);
+      o[32 * v + 3 * Q] = (PT)(ah[v] >> 16);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const int j = lane + 32 * v;
+      const uint32_t lo = aw[v] - (ah[v] << 8);
+      const uint32_t val[4] = {lo & 0xFFFFu, ah[v] & 0xFFFFu, lo >> 16, ah[v] >> 16};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t u = (uint32_t)(r + j + q * Q);
+        if (u < (uint64_t)Pp) prow[u] = (PT)val[q];
+      }
+    }
+  }
+}
+
 // Persistent blocks walk the work items (sub-band s, coarse DMs [kb, ke),
 // absolute times [tau0, tau0 + 4Q)). For each item the channels' input
-// windows are copied (cp.async) into a raw buffer while the previous item is
-// being summed, then rearranged so that shared word S[c][j] holds channel c's
-// samples at times tau0 + d1[kb][c] + j + qQ in byte q (q = 0..3). For coarse
-// DM k the output word j is sum_c S[c][j + d1[k][c] - d1[kb][c]]: four outputs
-// per 32-bit load whatever the delays. Sums use the byte-lane identity
-//   sum w = sum(lo lanes) + 256 * sum(hi lanes)  (mod 2^32)
-// with the hi lanes (bytes 1, 3) accumulated separately as 16-bit lanes,
-// exact for up to 257 channels per sub-band.
+// windows (from 16-byte aligned ring positions) are copied with cp.async into
+// a raw buffer while the previous item is being summed, then rearranged so
+// that shared word S[c][j] holds channel c's samples at raw offsets j + qQ in
+// byte q (q = 0..3). For coarse DM k the output word j is
+// sum_c S[c][j + a_c + d1[k][c] - d1[kb][c]] (a_c the window's misalignment):
+// four outputs per 32-bit load whatever the delays. Sums use the byte-lane
+// identity  sum w = sum(lo lanes) + 256 * sum(hi lanes)  (mod 2^32)  with the hi
+// lanes (bytes 1, 3) accumulated separately as 16-bit lanes, exact for up to
+// 257 channels per sub-band. Warps take (coarse DM, part of the tile) tasks;
+// a chunk with few coarse DMs splits each tile between 2, 4 or 8 warps.
 template <int Q, typename PT>
 __global__ void __launch_bounds__(kStage1Warps * 32, 1)
 k_stage1(const uint8_t* __restrict__ ring, int R, int start, const Stage1Item* __restrict__ items,
          int nitems, const int32_t* __restrict__ d1, int nchan, int m, int nsub, const int32_t* __restrict__ abase,
          PT* __restrict__ P, int64_t Pp, uint32_t one) {
   extern __shared__ __align__(16) uint8_t smem1[];
-  constexpr int SW = 2 * Q + 32;                 // staged words per channel (>= Q + span + 30, span <= Q)
-  constexpr int RB = (5 * Q + 48 + 15) / 16 * 16;  // raw bytes per channel (>= 3Q + SW bytes)
+  constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
+  constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
   constexpr int NCH = RB / 16;
   constexpr int V = Q / 32;
   const int TS = (m + 1) & ~1;                   // offset-table row stride (8-byte aligned pairs)
@@ -155,15 +223,16 @@ k_stage1(const uint8_t* __restrict__ ring, int R, int start, const Stage1Item* _
   uint32_t* tab = reinterpret_cast<uint32_t*>(raw + (size_t)m * RB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // physical ring position of channel c's first staged sample for item idx
-  auto window_start = [&](const Stage1Item& it, int c) -> int {
-    const int64_t p = (int64_t)start + it.tau0 + d1[(size_t)it.kb * nchan + it.s * m + c];
-    return (int)(p % R);
+  // physical ring position of channel c's first wanted sample for an item
+  auto wstart = [&](const Stage1Item& it, int c) -> int {
+    int64_t p = (int64_t)start + it.tau0 + d1[(size_t)it.kb * nchan + it.s * m + c];
+    while (p >= R) p -= R;
+    return (int)p;
   };
   auto issue = [&](int idx) {
     const Stage1Item it = items[idx];
     for (int c = warp; c < m; c += kStage1Warps) {
-      const int pa = window_start(it, c) & ~15;
+      const int pa = wstart(it, c) & ~15;
       const uint8_t* row = ring + (size_t)(it.s * m + c) * R;
       uint8_t* dst = raw + (size_t)c * RB;
       for (int ch = lane; ch < NCH; ch += 32) {
@@ -184,104 +253,56 @@ k_stage1(const uint8_t* __restrict__ ring, int R, int start, const Stage1Item* _
     const int32_t* d1kb = d1 + (size_t)it.kb * nchan + c0;
     cp_async_wait_all();
     __syncthreads();
-    // Raw windows (16-byte aligned starts) -> four-quarter words: S[c][j] byte q
-    // = raw[c][j + qQ]. The window's misalignment a_c goes into the offsets.
-    // Lane g builds words 16g .. 16g + 15 from four aligned 16-byte loads.
-    const int n16 = (Q + it.span + 15 + 15) >> 4;
+    // raw -> four-quarter words; lane g builds words 4g .. 4g + 3 of a channel
+    const int n4 = (Q + it.span + 15 + 3) >> 2;
     for (int c = warp; c < m; c += kStage1Warps) {
       const uint8_t* rw = raw + (size_t)c * RB;
       uint32_t* srow = S + (size_t)c * SW;
-      for (int g = lane; g < n16; g += 32) {
-        const int j = g << 4;
-        uint4 x[4];
+      for (int g = lane; g < n4; g += 32) {
+        const int j = g << 2;
+        uint32_t r[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = *reinterpret_cast<const uint4*>(rw + j + q * Q);
-        uint32_t xs[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          xs[q][0] = x[q].x; xs[q][1] = x[q].y; xs[q][2] = x[q].z; xs[q][3] = x[q].w;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          // 4 x 4 byte transpose: word 4e+i collects byte i of each quarter's word e
-          const uint32_t t0 = __byte_perm(xs[0][e], xs[1][e], 0x5140), t1 = __byte_perm(xs[0][e], xs[1][e], 0x7362);
-          const uint32_t t2 = __byte_perm(xs[2][e], xs[3][e], 0x5140), t3 = __byte_perm(xs[2][e], xs[3][e], 0x7362);
-          uint4 w;
-          w.x = __byte_perm(t0, t2, 0x5410);
-          w.y = __byte_perm(t0, t2, 0x7632);
-          w.z = __byte_perm(t1, t3, 0x5410);
-          w.w = __byte_perm(t1, t3, 0x7632);
-          *reinterpret_cast<uint4*>(srow + j + 4 * e) = w;
-        }
+        for (int q = 0; q < 4; ++q) r[q] = *reinterpret_cast<const uint32_t*>(rw + j + q * Q);
+        // 4 x 4 byte transpose: word j+i collects byte i of each quarter
+        const uint32_t t0 = __byte_perm(r[0], r[1], 0x5140), t1 = __byte_perm(r[0], r[1], 0x7362);
+        const uint32_t t2 = __byte_perm(r[2], r[3], 0x5140), t3 = __byte_perm(r[2], r[3], 0x7362);
+        uint4 w;
+        w.x = __byte_perm(t0, t2, 0x5410);
+        w.y = __byte_perm(t0, t2, 0x7632);
+        w.z = __byte_perm(t1, t3, 0x5410);
+        w.w = __byte_perm(t1, t3, 0x7632);
+        *reinterpret_cast<uint4*>(srow + j) = w;
       }
     }
     // word offset of S[c][a_c + d1[k][c] - d1[kb][c]] for every (k, c)
     for (int kk = warp; kk < nkk; kk += kStage1Warps) {
       const int32_t* d1k = d1 + (size_t)(it.kb + kk) * nchan + c0;
       for (int c = lane; c < m; c += 32)
-        tab[kk * TS + c] = (uint32_t)(c * SW + (window_start(it, c) & 15) + d1k[c] - d1kb[c]);
+        tab[kk * TS + c] = (uint32_t)(c * SW + (wstart(it, c) & 15) + d1k[c] - d1kb[c]);
     }
     __syncthreads();
     const int next = idx + gridDim.x;
     if (next < nitems) issue(next);
 
-    const uint32_t* Sl = S + lane;
-    for (int kk = warp; kk < nkk; kk += kStage1Warps) {
+    // tasks: (coarse DM, part of the tile); split the tile when coarse DMs are few
+    int split = 1;
+    while (split < V && nkk * split * 2 <= kStage1Warps) split *= 2;
+    for (int task = warp; task < nkk * split; task += kStage1Warps) {
+      const int kk = task / split, part = task - kk * split;
       const int k = it.kb + kk;
       const int64_t ab = abase[(size_t)k * nsub + it.s];
       if ((int64_t)it.tau0 + 4 * Q <= ab || (int64_t)it.tau0 >= ab + Pp) continue;
-      uint32_t aw[V], ah[V];
-#pragma unroll
-      for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
-      const uint32_t* t = tab + kk * TS;
-      int c = 0;
-#pragma unroll 2
-      for (; c + 1 < m; c += 2) {
-        const uint2 oo = *reinterpret_cast<const uint2*>(t + c);
-        const uint32_t* r0 = Sl + oo.x;
-        const uint32_t* r1 = Sl + oo.y;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
-          madd(aw[v], w0, one);
-          madd(aw[v], w1, one);
-          ah[v] += __byte_perm(w0, 0u, 0x4341) + __byte_perm(w1, 0u, 0x4341);
-        }
-      }
-      if (c < m) {
-        const uint32_t* r0 = Sl + t[c];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const uint32_t w0 = r0[32 * v];
-          madd(aw[v], w0, one);
-          ah[v] += __byte_perm(w0, 0u, 0x4341);
-        }
-      }
       PT* prow = P + ((size_t)k * nsub + it.s) * Pp;
       const int rel0 = (int)((int64_t)it.tau0 - ab);  // |rel0| < 2^30
-      if (rel0 >= 0 && (int64_t)rel0 + 4 * Q <= Pp) {
-        // tile inside the row: unguarded stores at fixed offsets
-        PT* o = prow + rel0 + lane;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const uint32_t lo = aw[v] - (ah[v] << 8);
-          o[32 * v] = (PT)(lo & 0xFFFFu);
-          o[32 * v + Q] = (PT)(ah[v] & 0xFFFFu);
-          o[32 * v + 2 * Q] = (PT)(lo >> 16);
-          o[32 * v + 3 * Q] = (PT)(ah[v] >> 16);
-        }
+      const uint32_t* t = tab + kk * TS;
+      if (split == 1) {
+        stage1_sum<Q, V, PT>(S, t, m, one, lane, 0, prow, rel0, Pp);
+      } else if (split == 2) {
+        if constexpr (V >= 2) stage1_sum<Q, V / 2, PT>(S, t, m, one, lane, part * (Q / 2), prow, rel0, Pp);
+      } else if (split == 4) {
+        if constexpr (V >= 4) stage1_sum<Q, V / 4, PT>(S, t, m, one, lane, part * (Q / 4), prow, rel0, Pp);
       } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int j = lane + 32 * v;
-          const uint32_t lo = aw[v] - (ah[v] << 8);
-          const uint32_t val[4] = {lo & 0xFFFFu, ah[v] & 0xFFFFu, lo >> 16, ah[v] >> 16};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t u = (uint32_t)(rel0 + j + q * Q);
-            if (u < (uint64_t)Pp) prow[u] = (PT)val[q];
-          }
-        }
+        if constexpr (V >= 8) stage1_sum<Q, V / 8, PT>(S, t, m, one, lane, part * (Q / 8), prow, rel0, Pp);
       }
     }
     __syncthreads();
@@ -301,24 +322,29 @@ __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long
 }
 
 // Persistent blocks walk units (coarse group k, tile of 2 NW outputs) in
-// sub-band chunks; warp g sums fine DM kG + g. A chunk's uint16 stage-1 rows
-// are copied (cp.async, double-buffered) into shared memory as 32-bit words
-// of consecutive pairs (even copy) and re-paired one element later (odd copy),
-// so every delay, even or odd, is a 32-bit load feeding two outputs. Sums use
+// sub-band chunks; SPLIT warps share fine DM kG + g, each summing NW / SPLIT
+// words of the tile. A chunk's uint16 stage-1 rows are copied (cp.async,
+// double-buffered) into shared memory as 32-bit words of consecutive pairs
+// (even copy) and re-paired one element later (odd copy), so every delay,
+// even or odd, is a 32-bit load feeding two outputs. Sums use
 //   sum w = sum(lo) + 65536 * sum(hi) (mod 2^32), sum(hi) = sum(w >> 16),
 // exact because every stage-2 sum is below 2^32.
-template <int NW, int MAXWARPS>
+template <int NW, int MAXWARPS, int SPLIT>
 __global__ void __launch_bounds__(MAXWARPS * 32, 1)
 k_stage2_u16(const uint16_t* __restrict__ P, int64_t Pp, const int32_t* __restrict__ e2, int ndm, int nsub,
              int G, int nk, int SC, int SWW, int ntile, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
-             longlong2* __restrict__ part, uint32_t one) {
+             longlong2* __restrict__ part, int64_t* __restrict__ part_tmp) {
   extern __shared__ __align__(16) uint32_t smem2[];
-  constexpr int V = NW / 32;
+  constexpr int VW = NW / 32 / SPLIT;                    // words per lane
   uint32_t* Se = smem2;                                  // [2][SC][SWW]
   uint32_t* So = Se + 2 * (size_t)SC * SWW;              // [SC][SWW]
-  uint32_t* tab = So + (size_t)SC * SWW;                 // [MAXWARPS][SC] word offsets from smem2
+  uint32_t* tab = So + (size_t)SC * SWW;                 // [kStage2MaxGroup][SC] word offsets from smem2
+  __shared__ long long st1[MAXWARPS];
+  __shared__ unsigned long long st2[MAXWARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
+  const int g = warp / SPLIT, part_i = warp - g * SPLIT;  // fine DM of the group, part of the tile
+  const int jbase = part_i * (NW / SPLIT);
   const int nchunk = (nsub + SC - 1) / SC;
   const int nunits = nk * ntile;
   // steps (unit, chunk) of this block: unit = blockIdx.x + r * gridDim.x
@@ -343,9 +369,9 @@ k_stage2_u16(const uint16_t* __restrict__ P, int64_t Pp, const int32_t* __restri
     cp_async_commit();
   };
 
-  uint32_t aw[V], ah[V];
+  uint32_t aw[VW], ah[VW];
 #pragma unroll
-  for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
+  for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
   if (nsteps > 0) issue(0, 0);
   for (int step = 0; step < nsteps; ++step) {
     const int buf = step & 1;
@@ -371,53 +397,53 @@ k_stage2_u16(const uint16_t* __restrict__ P, int64_t Pp, const int32_t* __restri
                        __funnelshift_r(a.w, b, 16));
       }
     }
-    for (int g = warp; g < nd; g += nwarps) {
+    for (int gg = warp; gg < nd; gg += nwarps) {
       for (int ss = lane; ss < ns; ss += 32) {
         const int s = s0 + ss;
         const int32_t emin = e2[(size_t)dfirst * nsub + s];
-        const int off = e2[(size_t)(dfirst + g) * nsub + s] - emin + (int)((t0 + emin) & 7);
+        const int off = e2[(size_t)(dfirst + gg) * nsub + s] - emin + (int)((t0 + emin) & 7);
         const uint32_t* base = (off & 1) ? So : cur;
-        tab[g * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
+        tab[gg * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
       }
     }
     __syncthreads();
     if (step + 1 < nsteps) issue(step + 1, buf ^ 1);
 
-    if (warp < nd) {
-      const uint32_t* t = tab + warp * SC;
-      const uint32_t* Sl = smem2 + lane;
+    if (g < nd) {
+      const uint32_t* t = tab + g * SC;
+      const uint32_t* Sl = smem2 + jbase + lane;
       int ss = 0;
 #pragma unroll 2
       for (; ss + 1 < ns; ss += 2) {
         const uint32_t* r0 = Sl + t[ss];
         const uint32_t* r1 = Sl + t[ss + 1];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
+        for (int v = 0; v < VW; ++v) {
           const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
-          madd(aw[v], w0, one);
-          madd(aw[v], w1, one);
-          ah[v] += (w0 >> 16) + (w1 >> 16);
+          aw[v] += w0 + w1;
+          madd_hi16(ah[v], w0);
+          madd_hi16(ah[v], w1);
         }
       }
       if (ss < ns) {
         const uint32_t* r0 = Sl + t[ss];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
+        for (int v = 0; v < VW; ++v) {
           const uint32_t w0 = r0[32 * v];
-          madd(aw[v], w0, one);
-          ah[v] += w0 >> 16;
+          aw[v] += w0;
+          madd_hi16(ah[v], w0);
         }
       }
     }
     if (ch == nchunk - 1) {
-      if (warp < nd) {
-        const int d = dfirst + warp;
+      long long s1 = 0;
+      unsigned long long s2 = 0;
+      if (g < nd) {
+        const int d = dfirst + g;
         int32_t* drow = D + (size_t)d * Dp;
-        long long s1 = 0;
-        unsigned long long s2 = 0;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int64_t ta = t0 + 2 * (lane + 32 * v);
+        for (int v = 0; v < VW; ++v) {
+          const int64_t ta = t0 + 2 * (jbase + lane + 32 * v);
           const uint32_t lo = aw[v] - (ah[v] << 16), hi = ah[v];
           if (ta + 1 < Td && (Dp & 1) == 0) {
             *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
@@ -427,13 +453,23 @@ k_stage2_u16(const uint16_t* __restrict__ P, int64_t Pp, const int32_t* __restri
           }
           if (ta < T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
           if (ta + 1 < T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
-          aw[v] = ah[v] = 0u;
         }
-        warp_sum_stats(s1, s2);
-        if (lane == 0) part[(size_t)d * ntile + tile] = make_longlong2(s1, (long long)s2);
-      } else {
+      }
 #pragma unroll
-        for (int v = 0; v < V; ++v) aw[v] = ah[v] = 0u;
+      for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+      warp_sum_stats(s1, s2);
+      if (SPLIT == 1) {
+        if (g < nd && lane == 0) part[(size_t)(dfirst + g) * ntile + tile] = make_longlong2(s1, (long long)s2);
+      } else {
+        // combine the parts of each fine DM in a fixed order (deterministic sums)
+        if (lane == 0) { st1[warp] = s1; st2[warp] = s2; }
+        __syncthreads();
+        if (part_i == 0 && g < nd && lane == 0) {
+          long long a = 0;
+          unsigned long long b = 0;
+          for (int i = 0; i < SPLIT; ++i) { a += st1[warp + i]; b += st2[warp + i]; }
+          part[(size_t)(dfirst + g) * ntile + tile] = make_longlong2(a, (long long)b);
+        }
       }
     }
   }
@@ -733,10 +769,16 @@ int set_stage1_attr(int bytes) {
   return TX_OK;
 }
 
-template <int NW, int MAXWARPS>
+template <int NW, int MAXWARPS, int SPLIT>
 int set_stage2_attr(int bytes) {
-  TX_CUDA(cudaFuncSetAttribute(k_stage2_u16<NW, MAXWARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  TX_CUDA(cudaFuncSetAttribute(k_stage2_u16<NW, MAXWARPS, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return TX_OK;
+}
+
+// Warps per fine DM for the uint16 stage 2: enough to fill 32 warps.
+int stage2_split(const tx_plan* p) {
+  if (p->nw2 != 512) return 1;
+  return p->group <= 4 ? 8 : p->group <= 8 ? 4 : p->group <= 16 ? 2 : 1;
 }
 
 int do_upload(tx_plan* p) {
@@ -761,7 +803,13 @@ int do_upload(tx_plan* p) {
   if (rc) return rc;
   const int s2 = stage2_smem(p);
   if (u16) {
-    if ((rc = p->nw2 == 512 ? set_stage2_attr<512, 16>(s2) : set_stage2_attr<256, 32>(s2))) return rc;
+    switch (stage2_split(p)) {
+      case 8: rc = set_stage2_attr<512, 32, 8>(s2); break;
+      case 4: rc = set_stage2_attr<512, 32, 4>(s2); break;
+      case 2: rc = set_stage2_attr<512, 32, 2>(s2); break;
+      default: rc = set_stage2_attr<256, 32, 1>(s2); break;
+    }
+    if (rc) return rc;
   } else if (p->nw2 == 512) {
     TX_CUDA(cudaFuncSetAttribute(k_stage2_i32<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
   } else {
@@ -1015,14 +1063,19 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
     if (u16) {
       const int nunits = p->nk * p->ntile2;
       const int grid = std::min(nunits, std::max(p->dev.num_sms, 1));
-      if (p->nw2 == 512)
-        k_stage2_u16<512, 16><<<grid, threads, stage2_smem(p), st>>>(
-            static_cast<const uint16_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nk, p->nsub_chunk2,
-            p->sww2, p->ntile2, D, Dp, p->Td, p->T, part, 1u);
-      else
-        k_stage2_u16<256, 32><<<grid, threads, stage2_smem(p), st>>>(
-            static_cast<const uint16_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nk, p->nsub_chunk2,
-            p->sww2, p->ntile2, D, Dp, p->Td, p->T, part, 1u);
+      const int split = stage2_split(p);
+      const int nthreads = std::min(p->group, kStage2MaxGroup) * 32 * split;
+#define TX_S2(NW, SP)                                                                                          \
+  k_stage2_u16<NW, 32, SP><<<grid, nthreads, stage2_smem(p), st>>>(                                            \
+      static_cast<const uint16_t*>(P), p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nk, p->nsub_chunk2,     \
+      p->sww2, p->ntile2, D, Dp, p->Td, p->T, part, nullptr)
+      switch (split) {
+        case 8: TX_S2(512, 8); break;
+        case 4: TX_S2(512, 4); break;
+        case 2: TX_S2(512, 2); break;
+        default: TX_S2(256, 1); break;
+      }
+#undef TX_S2
     } else {
       dim3 grid((unsigned)p->ntile2, (unsigned)p->nk);
       if (p->nw2 == 512)

@@ -29,17 +29,13 @@ void set_error(const char* fmt, ...) {
 
 static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Raw window per channel: quarters reach byte 3q + (staged words) with staged
-// words <= q + span + 30 (span <= q, 15 for the misalignment, 15 to whole 16-byte
-// groups), rounded to 16-byte chunks.
-int64_t stage1_raw_bytes(int q) { return (5 * (int64_t)q + 48 + 15) / 16 * 16; }
-int64_t stage1_staged_words(int q) { return 2 * (int64_t)q + 32; }
-
+// Shared memory of the stage-1 kernel: staged words, raw prefetch buffer and
+// the offset table (rows padded to an even length).
 int64_t stage1_smem_bytes(int m, int q) {
-  // staged words, raw prefetch buffer, address table (rows padded to even length)
-  return (int64_t)m * stage1_staged_words(q) * 4 + (int64_t)m * stage1_raw_bytes(q) +
+  return (int64_t)m * kStage1StagedWords(q) * 4 + (int64_t)m * kStage1RawBytes(q) +
          (int64_t)kStage1MaxCoarse * ((m + 1) & ~1) * 4;
 }
+
 static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Eq. 1 in samples: rnd(K DM (1/f^2 - 1/f_ref^2) / t_samp), rnd = llround.
@@ -189,7 +185,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   // A sub-band's staged window starts at the tile start + emin rounded down to
   // 8 elements (16 bytes) and spans the tile, the group's delay spread and
   // that alignment: sww2 32-bit words.
-  p->nw2 = G <= 16 ? 512 : 256;
+  p->nw2 = G <= 16 ? 512 : 256;  // 512-word tiles split over 2-8 warps per fine DM; 256 for larger groups
   const int64_t tt2 = 2 * (int64_t)p->nw2;
   p->ntile2 = (int32_t)((p->Td + tt2 - 1) / tt2);
   p->sww2 = (int32_t)round_up(p->nw2 + (span2 + 7 + 2) / 2 + 6, 4);
@@ -217,7 +213,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   while (q1 > 32 && stage1_smem_bytes(m, q1) > kSmemMax) q1 /= 2;
   if (stage1_smem_bytes(m, q1) > kSmemMax) { set_error("too many channels per sub-band for stage 1 (%d)", m); return TX_ERR_UNSUPPORTED; }
   p->q1 = q1;
-  p->span1_max = q1;
+  p->span1_max = q1 - 16;
   const int64_t tt1 = 4 * (int64_t)q1;
   for (int s = 0; s < nsub; ++s) {
     int kb = 0;

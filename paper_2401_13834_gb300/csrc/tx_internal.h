@@ -19,7 +19,14 @@ constexpr double kDispersion = 4.148808e3;
 // samples of times j, j+q, j+2q, j+3q of one channel, so one 32-bit load feeds
 // four outputs whatever the per-channel delay.
 constexpr int kStage1MaxCoarse = 32;   // coarse DMs that share one staged tile
-constexpr int kStage1Warps = 16;
+constexpr int kStage1Warps = 32;
+// Staged words per channel for quarter length q: the tile (q words), the
+// chunk's delay spread (<= q - 16), the window's misalignment (< 16) and
+// rounding to 4-word groups: at most 2q + 2. Word j of a channel takes raw
+// bytes j + iq (i = 0..3), so the raw window spans 5q + 2 bytes, rounded to
+// 16-byte chunks plus one.
+constexpr int kStage1StagedWords(int q) { return 2 * q + 16; }
+constexpr int kStage1RawBytes(int q) { return (5 * q + 2 + 15) / 16 * 16 + 16; }
 constexpr int kSmemMax = 232448;       // opt-in dynamic shared memory per block (227 KB)
 
 // ---- stage 2 (sub-bands -> fine DMs) tiling ---------------------------------
@@ -59,8 +66,6 @@ struct DevicePlan {
 };
 
 void set_error(const char* fmt, ...);
-int64_t stage1_raw_bytes(int q);
-int64_t stage1_staged_words(int q);
 int64_t stage1_smem_bytes(int m, int q);
 
 }  // namespace tx

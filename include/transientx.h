@@ -255,6 +255,31 @@ int32_t tx_timer_read(tx_timer* timer, double* h_ms, int32_t* nsteps, double* h_
 
 void tx_timer_destroy(tx_timer* timer);
 
+/* ---- allocation-free de-dispersion (the paper has no counterpart) ----
+   For callers that cannot call cudaMalloc: real-time loops that must not take
+   the allocator's locks or its implicit synchronisation, hosts that embed the
+   library under a device-memory budget another framework owns, and code that
+   must not fail for lack of memory once running.
+
+   Computes the de-dispersed series of one window, as TX_OUT_SERIES does, and
+   allocates nothing (no cudaMalloc, cudaFree or allocating library call):
+     d_x       uint8 [nchan][ld] channel-major window: the L carried samples
+               then the T new ones (T + L <= ld); 16-byte aligned start, ld a
+               multiple of 64 (samples past T + L are read but never affect
+               the result)
+     d_series  int32 [ndm][T + W_max - 1], written
+   The stage-1 sums, per-tile sums and copies of the plan's tables live in one
+   32 MiB static device array that every GPU loading this library holds until
+   the process exits; plans that need more return TX_ERR_BUDGET with the size
+   in tx_last_error(). Only uint16-intermediate plans are supported.
+   The first call on each device looks up the array's device address; make
+   that first call outside any stream capture. Every call uses the same array
+   and leaves its contents behind (nothing in it needs to start at zero):
+   calls that overlap on the GPU, on any streams, race with each other. The
+   plan's tables are copied in from host memory on every call. */
+int32_t tx_dedisperse_noalloc(const tx_plan* plan, const uint8_t* d_x, int64_t ld, int32_t* d_series,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

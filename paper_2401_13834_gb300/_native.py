@@ -81,6 +81,7 @@ def _load():
         "tx_execute_timed": (I32, [P, P, VP, VP, VP, VP, VP, P]),
         "tx_timer_read": (I32, [P, VP, C.POINTER(I32), VP]),
         "tx_timer_destroy": (None, [P]),
+        "tx_dedisperse_noalloc": (I32, [P, VP, I64, VP, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -336,3 +337,12 @@ def cube_view(plan: Plan, out):
 def series_view(plan: Plan, out):
     import torch
     return out.view(torch.int32).view(plan.ndm, plan.series_len)
+
+
+def dedisperse_noalloc(plan: Plan, x, ld: int, series, stream=None):
+    """De-dispersed series of one window through the allocation-free entry point.
+
+    x: uint8 CUDA tensor holding [nchan][ld] (tail then block); series: int32
+    CUDA tensor of ndm * (T + W_max - 1) elements. Nothing is allocated.
+    """
+    _check(lib.tx_dedisperse_noalloc(plan.handle, _ptr(x), int(ld), _ptr(series), _stream_ptr(stream)))

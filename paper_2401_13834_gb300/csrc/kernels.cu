@@ -1210,3 +1210,141 @@ int32_t tx_execute_host(const tx_plan* p, tx_beam* b, const uint8_t* h_block, vo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free de-dispersion
+// ---------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc: a real-time acquisition loop that must
+// not take the allocator's locks or risk the implicit device synchronisation an
+// allocation can cause, a host that embeds this library under a fixed
+// device-memory budget owned by another framework, or code that must never
+// fail for lack of memory once running. tx_dedisperse_noalloc serves them: the
+// caller passes the input window and the output series; the stage-1 sums, the
+// per-tile sums and copies of the plan's tables live in the file-scope array
+// below, which every GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code cannot use the array's name as a device address).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  TX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) { set_error("device %d out of range", dev); return TX_ERR_INVALID_ARG; }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+      return TX_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TX_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, int32_t* d_series, void* stream) {
+  if (!p || !d_x || !d_series) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  if (p->interm != TX_INTERM_U16) { set_error("tx_dedisperse_noalloc needs a plan with uint16 intermediates"); return TX_ERR_UNSUPPORTED; }
+  if (ld < p->L + p->T || ld % 64 != 0 || ld >= (int64_t)1 << 30 || ((uintptr_t)d_x & 15) != 0) {
+    set_error("d_x needs a 16-byte aligned start and a row pitch ld that is a multiple of 64 and >= L + T (%lld)",
+              (long long)(p->L + p->T));
+    return TX_ERR_INVALID_ARG;
+  }
+  // scratch layout: stage-1 work items, d1, abase, e2, stage-1 sums, per-tile sums
+  const size_t b_items = align256(p->items1.size() * sizeof(Stage1Item));
+  const size_t b_d1 = align256(p->d1.size() * 4);
+  const size_t b_abase = align256(p->abase.size() * 4);
+  const size_t b_e2 = align256(p->e2.size() * 4);
+  const size_t b_P = align256((size_t)p->nk * p->nsub * p->Pp * 2);
+  const size_t b_part = align256((size_t)p->ndm * p->ntile2 * 16);
+  const size_t need = b_items + b_d1 + b_abase + b_e2 + b_P + b_part;
+  if (need > kNoAllocScratchBytes) {
+    set_error("this plan needs %zu bytes of scratch; the static scratch of tx_dedisperse_noalloc holds %zu",
+              need, kNoAllocScratchBytes);
+    return TX_ERR_BUDGET;
+  }
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  int dev = 0, nsm = 0;
+  TX_CUDA(cudaGetDevice(&dev));
+  TX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  Stage1Item* items = reinterpret_cast<Stage1Item*>(base);
+  int32_t* d1 = reinterpret_cast<int32_t*>(base + b_items);
+  int32_t* abase = reinterpret_cast<int32_t*>(base + b_items + b_d1);
+  int32_t* e2 = reinterpret_cast<int32_t*>(base + b_items + b_d1 + b_abase);
+  uint16_t* P = reinterpret_cast<uint16_t*>(base + b_items + b_d1 + b_abase + b_e2);
+  longlong2* part = reinterpret_cast<longlong2*>(base + b_items + b_d1 + b_abase + b_e2 + b_P);
+  cudaStream_t st = (cudaStream_t)stream;
+  TX_CUDA(cudaMemcpyAsync(items, p->items1.data(), p->items1.size() * sizeof(Stage1Item), cudaMemcpyHostToDevice, st));
+  TX_CUDA(cudaMemcpyAsync(d1, p->d1.data(), p->d1.size() * 4, cudaMemcpyHostToDevice, st));
+  TX_CUDA(cudaMemcpyAsync(abase, p->abase.data(), p->abase.size() * 4, cudaMemcpyHostToDevice, st));
+  TX_CUDA(cudaMemcpyAsync(e2, p->e2.data(), p->e2.size() * 4, cudaMemcpyHostToDevice, st));
+  // Nothing in the scratch must start at zero: stage 1 writes every stage-1
+  // sum that stage 2 reads, and stage 2 writes every per-tile sum.
+
+  // stage 1 on the caller's window (a linear buffer read as a ring of length ld)
+  const int nitems = (int)p->items1.size();
+  const int smem1 = (int)stage1_smem_bytes(p->m, p->q1);
+  const int grid1 = std::min(nitems, std::max(nsm, 1));
+#define TX_NA_S1(Q)                                                                                      \
+  do {                                                                                                   \
+    TX_CUDA(cudaFuncSetAttribute(k_stage1<Q, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1)); \
+    k_stage1<Q, uint16_t><<<grid1, kStage1Warps * 32, smem1, st>>>(d_x, (int)ld, 0, items, nitems, d1, p->nchan, \
+                                                                   p->m, p->nsub, abase, P, p->Pp, 1u);   \
+  } while (0)
+  switch (p->q1) {
+    case 256: TX_NA_S1(256); break;
+    case 128: TX_NA_S1(128); break;
+    case 64: TX_NA_S1(64); break;
+    default: TX_NA_S1(32); break;
+  }
+#undef TX_NA_S1
+  TX_CUDA(cudaGetLastError());
+
+  // stage 2 into the caller's series [ndm][T + W_max - 1]
+  const int smem2 = (3 * p->nsub_chunk2 * p->sww2 + kStage2MaxGroup * p->nsub_chunk2) * 4;
+  const int nunits = p->nk * p->ntile2;
+  const int grid2 = std::min(nunits, std::max(nsm, 1));
+  const int split = p->nw2 != 512 ? 1 : p->group <= 4 ? 8 : p->group <= 8 ? 4 : p->group <= 16 ? 2 : 1;
+  const int nthreads = std::min(p->group, kStage2MaxGroup) * 32 * split;
+#define TX_NA_S2(NW, SP)                                                                                        \
+  do {                                                                                                          \
+    TX_CUDA(cudaFuncSetAttribute(k_stage2_u16<NW, 32, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2)); \
+    k_stage2_u16<NW, 32, SP><<<grid2, nthreads, smem2, st>>>(P, p->Pp, e2, p->ndm, p->nsub, p->group, p->nk,      \
+                                                             p->nsub_chunk2, p->sww2, p->ntile2, d_series, p->Td, \
+                                                             p->Td, p->T, part, nullptr);                         \
+  } while (0)
+  switch (split) {
+    case 8: TX_NA_S2(512, 8); break;
+    case 4: TX_NA_S2(512, 4); break;
+    case 2: TX_NA_S2(512, 2); break;
+    default: TX_NA_S2(256, 1); break;
+  }
+#undef TX_NA_S2
+  TX_CUDA(cudaGetLastError());
+  return TX_OK;
+}
+
+}  // extern "C"

@@ -146,20 +146,24 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
   for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
   const uint32_t* base = S + jbase + lane;
   int c = 0;
-#pragma unroll 2
-  for (; c + 1 < m; c += 2) {
-    const uint2 oo = *reinterpret_cast<const uint2*>(t + c);
+  for (; c + 3 < m; c += 4) {
+    const uint4 oo = *reinterpret_cast<const uint4*>(t + c);
     const uint32_t* r0 = base + oo.x;
     const uint32_t* r1 = base + oo.y;
+    const uint32_t* r2 = base + oo.z;
+    const uint32_t* r3 = base + oo.w;
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
-      const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+      const uint32_t w0 = r0[32 * v], w1 = r1[32 * v], w2 = r2[32 * v], w3 = r3[32 * v];
       madd(aw[v], w0, one);
       madd(aw[v], w1, one);
+      madd(aw[v], w2, one);
+      madd(aw[v], w3, one);
       ah[v] += __byte_perm(w0, 0u, 0x4341) + __byte_perm(w1, 0u, 0x4341);
+      ah[v] += __byte_perm(w2, 0u, 0x4341) + __byte_perm(w3, 0u, 0x4341);
     }
   }
-  if (c < m) {
+  for (; c < m; ++c) {
     const uint32_t* r0 = base + t[c];
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
@@ -175,10 +179,11 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
       const uint32_t lo = aw[v] - (ah[v] << 8);
-      o[32 * v] = (PT)(lo & 0xFFFFu);
-      o[32 * v + Q] = (PT)(ah[v] & 0xFFFFu);
-      o[32 * v + 2 * Q] = (PT)(lo >> 16);
-      o[32 * v + 3 * Q] = (PT)(ah[v] >> 16);
+      const PT v0 = (PT)(lo & 0xFFFFu), v1 = (PT)(ah[v] & 0xFFFFu), v2 = (PT)(lo >> 16), v3 = (PT)(ah[v] >> 16);
+      o[32 * v] = v0;
+      o[32 * v + Q] = v1;
+      o[32 * v + 2 * Q] = v2;
+      o[32 * v + 3 * Q] = v3;
     }
   } else {
 #pragma unroll
@@ -217,7 +222,7 @@ k_stage1(const uint8_t* __restrict__ ring, int R, int start, const Stage1Item* _
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
   constexpr int NCH = RB / 16;
   constexpr int V = Q / 32;
-  const int TS = (m + 1) & ~1;                   // offset-table row stride (8-byte aligned pairs)
+  const int TS = (m + 3) & ~3;                   // offset-table row stride (16-byte aligned quads)
   uint32_t* S = reinterpret_cast<uint32_t*>(smem1);
   uint8_t* raw = smem1 + (size_t)m * SW * 4;
   uint32_t* tab = reinterpret_cast<uint32_t*>(raw + (size_t)m * RB);
@@ -541,7 +546,7 @@ __device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
 // Then, per width W: hi + lo = W mu (hi integer) and inv = 1 / (sigma sqrt W).
 __global__ void k_stats(const longlong2* __restrict__ part, int ntile, int ndm, int64_t T, int nw,
                         const int32_t* __restrict__ widths, int running, double lam, double* __restrict__ run,
-                        SnrConst* __restrict__ cst) {
+                        SnrConst* __restrict__ cst, double gamma) {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= ndm) return;
   unsigned long long s1 = 0, s2 = 0;
@@ -574,7 +579,13 @@ __global__ void k_stats(const longlong2* __restrict__ part, int ntile, int ndm, 
     c.hi = (int32_t)hi;
     c.lo = (float)__dsub_rn(cw, hi);
     c.inv = sigma > 0.0 ? (float)__ddiv_rn(1.0, __dmul_rn(sigma, sqrt(W))) : 0.f;
-    c.pad = 0.f;
+    if (sigma > 0.0) {
+      // smallest integer window sum whose S/N reaches gamma
+      const double t = ceil(__dadd_rn(cw, __dmul_rn(gamma, __dmul_rn(sigma, sqrt(W)))));
+      c.thr = t > 2147483647.0 ? INT32_MAX : t < -2147483647.0 ? -INT32_MAX : (int32_t)t;
+    } else {
+      c.thr = gamma <= 0.0 ? -INT32_MAX : INT32_MAX;  // S/N is 0 everywhere
+    }
     cst[(size_t)d * nw + w] = c;
   }
 }
@@ -582,127 +593,160 @@ __global__ void k_stats(const longlong2* __restrict__ part, int ntile, int ndm, 
 // ---------------------------------------------------------------------------
 // boxcar matched filter (Eq. 5 via prefix sums, Sec. 2.4) and outputs (Sec. 2.5)
 // ---------------------------------------------------------------------------
-// One block per (fine DM, tile of kBoxTile outputs): the series with its
-// W_max - 1 look-ahead goes to shared memory, becomes an inclusive prefix sum
-// C, and each output t takes B_W = C[t + W] - C[t] for every width.
+// Persistent blocks walk contiguous runs of units (fine DM d, tile of
+// kBoxTile outputs); each unit's series (with its W_max - 1 look-ahead) is
+// copied into shared memory with cp.async while the previous unit is being
+// filtered, then turned in place into the prefix sum P (P[0] = 0), and each
+// output t takes B_W = P[t + W] - P[t] for every width.
+//   CUBE / PLANE: S/N for every width (float), best width for the plane.
+//   CANDS: a point is a candidate when B_W >= thr_W for some width, an exact
+//   integer form of S/N >= gamma; float S/N and the best width are computed
+//   for those points only.
 // NWT > 0: exactly NWT widths, per-width constants in registers.
 // NWT = 0: any count up to kMaxWidths, constants in shared memory.
-template <int NWT>
+template <int NWT, int MODE>
 __global__ void __launch_bounds__(kBoxThreads)
 k_boxcar(const int32_t* __restrict__ D, int64_t Dp, int64_t T, int nw_rt, const int32_t* __restrict__ widths,
-         int wmax, const SnrConst* __restrict__ cst, int mode, float gamma, float* __restrict__ outf,
-         uint8_t* __restrict__ outw, tx_cand* __restrict__ cands, unsigned long long* __restrict__ ncand,
-         long long max_cands) {
+         int wmax, const SnrConst* __restrict__ cst, float* __restrict__ outf, uint8_t* __restrict__ outw,
+         tx_cand* __restrict__ cands, unsigned long long* __restrict__ ncand, long long max_cands, int ndm,
+         int ntile) {
   constexpr int NR = NWT > 0 ? NWT : 1;
-  extern __shared__ __align__(16) uint32_t C[];
+  extern __shared__ __align__(16) uint32_t smb[];
   __shared__ uint32_t wsum[kBoxThreads / 32];
   __shared__ int32_t sW[kMaxWidths];
   __shared__ SnrConst sC[kMaxWidths];
   const int nw = NWT > 0 ? NWT : nw_rt;
-  const int d = blockIdx.y;
-  const int64_t t0 = (int64_t)blockIdx.x * kBoxTile;
-  const int n = (int)min((int64_t)kBoxTile, T - t0);
-  const int N = n + wmax - 1;
-  int32_t Wr[NR], hi[NR];
-  float lo[NR], inv[NR];
-  if (NWT > 0) {
-#pragma unroll
-    for (int w = 0; w < NR; ++w) {
-      const SnrConst c = cst[(size_t)d * nw + w];
-      Wr[w] = __ldg(widths + w);
-      hi[w] = c.hi;
-      lo[w] = c.lo;
-      inv[w] = c.inv;
-    }
-  } else if (threadIdx.x < nw) {
-    sW[threadIdx.x] = widths[threadIdx.x];
-    sC[threadIdx.x] = cst[(size_t)d * nw + threadIdx.x];
-  }
-  const int32_t* drow = D + (size_t)d * Dp + t0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) C[i + 1] = (uint32_t)__ldg(drow + i);
-  if (threadIdx.x == 0) C[0] = 0u;
-  __syncthreads();
-  // inclusive scan of C[1..N] (uint32, wrap-around is harmless: window sums < 2^31)
-  const int E = (N + blockDim.x - 1) / blockDim.x;
-  const int beg = 1 + threadIdx.x * E, end = min(beg + E, N + 1);
-  uint32_t local = 0;
-  for (int i = beg; i < end; ++i) local += C[i];
+  const int bufw = (kBoxTile + wmax + 8 + 3) & ~3;  // words per buffer: 4 pad + series + chunk rounding
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[warp] = x;
-  __syncthreads();
-  uint32_t pre = x - local;
-  for (int w = 0; w < warp; ++w) pre += wsum[w];
-  for (int i = beg; i < end; ++i) {
-    pre += C[i];
-    C[i] = pre;
-  }
-  __syncthreads();
+  const int64_t nunits = (int64_t)ndm * ntile;
+  const int u_begin = (int)(nunits * blockIdx.x / gridDim.x), u_end = (int)(nunits * (blockIdx.x + 1) / gridDim.x);
 
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t* Ci = C + i;
-    const uint32_t cl = Ci[0];
-    float best = -INFINITY;
-    int bw = 0;
-    if (NWT > 0) {
-      float sv[NR];
+  auto issue = [&](int unit, int buf) {
+    const int d = unit / ntile, tile = unit - d * ntile;
+    const int64_t t0 = (int64_t)tile * kBoxTile;
+    const int n = (int)min((int64_t)kBoxTile, T - t0);
+    const int nq = (n + wmax - 1 + 3) >> 2;  // 16-byte chunks of the series window
+    const int32_t* src = D + (size_t)d * Dp + t0;
+    uint32_t* dst = smb + (size_t)buf * bufw + 4;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(dst + 4 * q, src + 4 * q);
+    cp_async_commit();
+  };
+
+  int32_t Wr[NR], thr[NR];
+  int cur_d = -1;
+  if (u_begin < u_end) issue(u_begin, 0);
+  for (int unit = u_begin, it = 0; unit < u_end; ++unit, ++it) {
+    const int buf = it & 1;
+    const int d = unit / ntile, tile = unit - d * ntile;
+    const int64_t t0 = (int64_t)tile * kBoxTile;
+    const int n = (int)min((int64_t)kBoxTile, T - t0);
+    const int N = n + wmax - 1;
+    uint32_t* C = smb + (size_t)buf * bufw + 3;  // C[0] = P[0] = 0, C[1 + j] = D[j] -> P[1 + j]
+    if (NWT > 0 && d != cur_d) {
 #pragma unroll
       for (int w = 0; w < NR; ++w) {
-        const uint32_t B = Ci[Wr[w]] - cl;
-        sv[w] = ((float)((int32_t)B - hi[w]) - lo[w]) * inv[w];
-      }
-      if (mode == TX_OUT_CUBE) {
-#pragma unroll
-        for (int w = 0; w < NR; ++w) outf[((size_t)d * nw + w) * T + t0 + i] = sv[w];
-      } else {
-#pragma unroll
-        for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
-        // best width, ties to the smaller width: needed for every point of the
-        // plane, only for the (rare) points above threshold of the candidates
-        if (mode == TX_OUT_PLANE || best >= gamma) {
-          bw = NR - 1;
-#pragma unroll
-          for (int w = NR - 1; w >= 0; --w)
-            if (sv[w] == best) bw = w;
-        }
-      }
-    } else {
-      for (int w = 0; w < nw; ++w) {
-        const uint32_t B = Ci[sW[w]] - cl;
-        const float snr = ((float)((int32_t)B - sC[w].hi) - sC[w].lo) * sC[w].inv;
-        if (mode == TX_OUT_CUBE) outf[((size_t)d * nw + w) * T + t0 + i] = snr;
-        if (snr > best) {
-          best = snr;
-          bw = w;
-        }
+        Wr[w] = __ldg(widths + w);
+        thr[w] = cst[(size_t)d * nw + w].thr;
       }
     }
-    if (mode == TX_OUT_PLANE) {
-      outf[(size_t)d * T + t0 + i] = best;
-      outw[(size_t)d * T + t0 + i] = (uint8_t)bw;
-    } else if (mode == TX_OUT_CANDS) {
-      const bool hit = best >= gamma;
-      const unsigned act = __activemask();
-      const unsigned hits = __ballot_sync(act, hit);
-      if (hits) {
-        const int leader = __ffs(hits) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(ncand, (unsigned long long)__popc(hits));
-        base = __shfl_sync(act, base, leader);
-        if (hit) {
-          const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
-          if (idx < (unsigned long long)max_cands) {
-            tx_cand r;
-            r.dm_index = d;
-            r.t = (int32_t)(t0 + i);
-            r.w_index = bw;
-            r.snr = best;
-            cands[idx] = r;
+    cp_async_wait_all();
+    __syncthreads();  // this unit's series landed; the previous unit is done with sW/sC and the other buffer
+    if (NWT == 0 && d != cur_d && threadIdx.x < nw) {
+      sW[threadIdx.x] = widths[threadIdx.x];
+      sC[threadIdx.x] = cst[(size_t)d * nw + threadIdx.x];
+    }
+    cur_d = d;
+    if (threadIdx.x == 0) C[0] = 0u;
+    if (unit + 1 < u_end) issue(unit + 1, buf ^ 1);
+    // inclusive scan of C[1..N] (uint32, wrap-around is harmless: window sums < 2^31)
+    const int E = (N + blockDim.x - 1) / blockDim.x;
+    const int beg = 1 + threadIdx.x * E, end = min(beg + E, N + 1);
+    uint32_t local = 0;
+    for (int i = beg; i < end; ++i) local += C[i];
+    uint32_t x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t pre = x - local;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    for (int i = beg; i < end; ++i) {
+      pre += C[i];
+      C[i] = pre;
+    }
+    __syncthreads();
+
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t* Ci = C + i;
+      const uint32_t cl = Ci[0];
+      float best = -INFINITY;
+      int bw = 0;
+      bool hit = false;
+      if (NWT > 0) {
+        if (MODE == TX_OUT_CANDS) {
+          int32_t m = INT32_MIN;
+#pragma unroll
+          for (int w = 0; w < NR; ++w) m = max(m, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
+          hit = m >= 0;
+          if (hit) {  // rare: float S/N and the best width of a candidate
+            for (int w = 0; w < NR; ++w) {
+              const SnrConst c = cst[(size_t)d * nw + w];
+              const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+              if (sv > best) { best = sv; bw = w; }
+            }
+          }
+        } else {
+          float sv[NR];
+#pragma unroll
+          for (int w = 0; w < NR; ++w) {
+            const SnrConst c = cst[(size_t)d * nw + w];
+            sv[w] = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+          }
+          if (MODE == TX_OUT_CUBE) {
+#pragma unroll
+            for (int w = 0; w < NR; ++w) outf[((size_t)d * nw + w) * T + t0 + i] = sv[w];
+          } else {
+#pragma unroll
+            for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
+            bw = NR - 1;
+#pragma unroll
+            for (int w = NR - 1; w >= 0; --w)
+              if (sv[w] == best) bw = w;
+          }
+        }
+      } else {
+        for (int w = 0; w < nw; ++w) {
+          const int32_t B = (int32_t)(Ci[sW[w]] - cl);
+          const float snr = ((float)(B - sC[w].hi) - sC[w].lo) * sC[w].inv;
+          if (MODE == TX_OUT_CUBE) outf[((size_t)d * nw + w) * T + t0 + i] = snr;
+          if (snr > best) { best = snr; bw = w; }
+          hit = hit || B >= sC[w].thr;
+        }
+      }
+      if (MODE == TX_OUT_PLANE) {
+        outf[(size_t)d * T + t0 + i] = best;
+        outw[(size_t)d * T + t0 + i] = (uint8_t)bw;
+      } else if (MODE == TX_OUT_CANDS) {
+        const unsigned act = __activemask();
+        const unsigned hits = __ballot_sync(act, hit);
+        if (hits) {
+          const int leader = __ffs(hits) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(ncand, (unsigned long long)__popc(hits));
+          base = __shfl_sync(act, base, leader);
+          if (hit) {
+            const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+            if (idx < (unsigned long long)max_cands) {
+              tx_cand r;
+              r.dm_index = d;
+              r.t = (int32_t)(t0 + i);
+              r.w_index = bw;
+              r.snr = best;
+              cands[idx] = r;
+            }
           }
         }
       }
@@ -711,33 +755,39 @@ k_boxcar(const int32_t* __restrict__ D, int64_t Dp, int64_t T, int nw_rt, const 
 }
 
 // Launch helper: exact width counts 1..12 and 16 get their own instantiation.
-template <int NWT>
+template <int NWT, int MODE>
 void launch_boxcar_t(dim3 grid, int smem, cudaStream_t st, const int32_t* D, int64_t Dp, int64_t T, int nw,
-                     const int32_t* widths, int wmax, const SnrConst* cst, int mode, float gamma, float* outf,
-                     uint8_t* outw, tx_cand* cands, unsigned long long* nc, long long max_cands) {
-  k_boxcar<NWT><<<grid, kBoxThreads, smem, st>>>(D, Dp, T, nw, widths, wmax, cst, mode, gamma, outf, outw, cands, nc,
-                                                 max_cands);
+                     const int32_t* widths, int wmax, const SnrConst* cst, float* outf, uint8_t* outw,
+                     tx_cand* cands, unsigned long long* nc, long long max_cands, int ndm, int ntile) {
+  k_boxcar<NWT, MODE><<<grid, kBoxThreads, smem, st>>>(D, Dp, T, nw, widths, wmax, cst, outf, outw, cands, nc,
+                                                       max_cands, ndm, ntile);
 }
 
 using BoxLaunch = void (*)(dim3, int, cudaStream_t, const int32_t*, int64_t, int64_t, int, const int32_t*, int,
-                           const SnrConst*, int, float, float*, uint8_t*, tx_cand*, unsigned long long*, long long);
-using BoxKernel = void (*)(const int32_t*, int64_t, int64_t, int, const int32_t*, int, const SnrConst*, int, float,
-                           float*, uint8_t*, tx_cand*, unsigned long long*, long long);
+                           const SnrConst*, float*, uint8_t*, tx_cand*, unsigned long long*, long long, int, int);
+using BoxKernel = void (*)(const int32_t*, int64_t, int64_t, int, const int32_t*, int, const SnrConst*, float*,
+                           uint8_t*, tx_cand*, unsigned long long*, long long, int, int);
 
 struct BoxEntry {
   BoxLaunch launch;
   BoxKernel kernel;
 };
 
-BoxEntry box_entry(int nw) {
+template <int MODE>
+BoxEntry box_entry_m(int nw) {
   switch (nw) {
 #define TX_BOX(N) \
-  case N: return {launch_boxcar_t<N>, k_boxcar<N>};
+  case N: return {launch_boxcar_t<N, MODE>, k_boxcar<N, MODE>};
     TX_BOX(1) TX_BOX(2) TX_BOX(3) TX_BOX(4) TX_BOX(5) TX_BOX(6) TX_BOX(7) TX_BOX(8) TX_BOX(9) TX_BOX(10)
     TX_BOX(11) TX_BOX(12) TX_BOX(16)
 #undef TX_BOX
-    default: return {launch_boxcar_t<0>, k_boxcar<0>};
+    default: return {launch_boxcar_t<0, MODE>, k_boxcar<0, MODE>};
   }
+}
+
+BoxEntry box_entry(int nw, int mode) {
+  return mode == TX_OUT_CANDS ? box_entry_m<TX_OUT_CANDS>(nw)
+         : mode == TX_OUT_PLANE ? box_entry_m<TX_OUT_PLANE>(nw) : box_entry_m<TX_OUT_CUBE>(nw);
 }
 
 __global__ void k_fill_run(double* run, int n) {
@@ -761,7 +811,8 @@ int stage2_smem(const tx_plan* p) {
   return p->nsub_chunk2 * p->sw2_i32 * 4;
 }
 
-int box_smem(const tx_plan* p) { return (kBoxTile + p->wmax + 4) * 4; }
+// two buffers of (4 pad words + tile + look-ahead, rounded to 16-byte chunks)
+int box_smem(const tx_plan* p) { return 2 * ((kBoxTile + p->wmax + 8 + 3) & ~3) * 4; }
 
 template <int Q, typename PT>
 int set_stage1_attr(int bytes) {
@@ -815,7 +866,13 @@ int do_upload(tx_plan* p) {
   } else {
     TX_CUDA(cudaFuncSetAttribute(k_stage2_i32<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
   }
-  TX_CUDA(cudaFuncSetAttribute(box_entry(p->nw).kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, box_smem(p)));
+  if (p->output != TX_OUT_SERIES) {
+    const BoxEntry be = box_entry(p->nw, p->output);
+    TX_CUDA(cudaFuncSetAttribute(be.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, box_smem(p)));
+    TX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->dev.box_blocks_per_sm, be.kernel, kBoxThreads,
+                                                          box_smem(p)));
+  }
+  p->dev.box_blocks_per_sm = std::max(p->dev.box_blocks_per_sm, 1);
   return TX_OK;
 }
 
@@ -1094,17 +1151,19 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   if (!series) {
     SnrConst* cst = reinterpret_cast<SnrConst*>(ws + p->ws_const);
     k_stats<<<(p->ndm + 127) / 128, 128, 0, st>>>(part, p->ntile2, p->ndm, p->T, p->nw, p->dev.widths,
-                                                  p->stats == TX_STATS_RUNNING, p->lambda, b->run, cst);
+                                                  p->stats == TX_STATS_RUNNING, p->lambda, b->run, cst,
+                                                  (double)p->gamma);
     TX_CUDA(cudaGetLastError());
     TX_MARK(4);
     if (p->output == TX_OUT_CANDS) TX_CUDA(cudaMemsetAsync(d_ncand, 0, sizeof(int64_t), st));
     float* outf = static_cast<float*>(d_out);
     uint8_t* outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(d_out) + (size_t)p->ndm * p->T * 4 : nullptr;
-    dim3 grid((unsigned)p->ntile3, (unsigned)p->ndm);
     auto* cands = static_cast<tx_cand*>(d_out);
     auto* nc = reinterpret_cast<unsigned long long*>(d_ncand);
-    box_entry(p->nw).launch(grid, box_smem(p), st, D, p->Dp, p->T, p->nw, p->dev.widths, p->wmax, cst, p->output,
-                            p->gamma, outf, outw, cands, nc, (long long)p->max_cands);
+    const int nunits = p->ndm * p->ntile3;
+    const dim3 grid((unsigned)std::min(nunits, std::max(p->dev.num_sms, 1) * p->dev.box_blocks_per_sm));
+    box_entry(p->nw, p->output).launch(grid, box_smem(p), st, D, p->Dp, p->T, p->nw, p->dev.widths, p->wmax, cst,
+                                       outf, outw, cands, nc, (long long)p->max_cands, p->ndm, p->ntile3);
     TX_CUDA(cudaGetLastError());
   } else {
     TX_MARK(4);

@@ -30,10 +30,10 @@ void set_error(const char* fmt, ...) {
 static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 // Shared memory of the stage-1 kernel: staged words, raw prefetch buffer and
-// the offset table (rows padded to an even length).
+// the offset table (rows padded to a multiple of four entries).
 int64_t stage1_smem_bytes(int m, int q) {
   return (int64_t)m * kStage1StagedWords(q) * 4 + (int64_t)m * kStage1RawBytes(q) +
-         (int64_t)kStage1MaxCoarse * ((m + 1) & ~1) * 4;
+         (int64_t)kStage1MaxCoarse * ((m + 3) & ~3) * 4;
 }
 
 static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }

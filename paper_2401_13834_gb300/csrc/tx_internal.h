@@ -47,17 +47,19 @@ struct Stage1Item {
 };
 
 // Per (fine DM, width) constants of the S/N normalisation (Eq. 5):
-// S/N = (float(B - hi) - lo) * inv with hi + lo = W * mu and inv = 1 / (sigma sqrt W).
+// S/N = (float(B - hi) - lo) * inv with hi + lo = W * mu and inv = 1 / (sigma sqrt W);
+// thr = ceil(W mu + gamma sigma sqrt W), so S/N >= gamma exactly when B >= thr.
 struct SnrConst {
   int32_t hi;
   float lo;
   float inv;
-  float pad;
+  int32_t thr;
 };
 
 struct DevicePlan {
   int device = -1;
   int num_sms = 0;
+  int box_blocks_per_sm = 1;     // resident boxcar blocks per SM (persistent grid)
   int32_t* d1 = nullptr;         // [nk][nchan]
   int32_t* abase = nullptr;      // [nk][nsub]
   int32_t* e2 = nullptr;         // [ndm][nsub]

@@ -233,7 +233,7 @@ def test_candidate_overflow_keeps_valid_records(tx, small_case):
     best_ref, _ = O.dm_time_plane(snr)
     for r in got:
         assert abs(float(r["snr"]) - best_ref[r["dm_index"], r["t"]]) <= RTOL * max(1, abs(float(r["snr"])))
-        assert float(r["snr"]) >= 2.0
+        assert float(r["snr"]) >= 2.0 - RTOL * 2.0  # the threshold decision is exact; the float S/N rounds
 
 
 def test_running_statistics(tx):

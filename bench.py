@@ -290,6 +290,23 @@ def load_workload(args):
     return wl
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (plain x when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_step: int, steps: int, world: int, seconds_max: float) -> float:
+    """Whole-job rate: every rank processed `steps` blocks of `units_per_step`
+    units (independent beam replicas); the job took the slowest rank's time."""
+    return world * units_per_step * steps / seconds_max
+
+
 def workload_config(wl, group, overlap, args, kind="ours"):
     return {
         "workload": wl.name, "nchan": wl.nchan, "band_mhz": [float(wl.freqs_mhz.min()), float(wl.freqs_mhz.max())],
@@ -376,12 +393,9 @@ def run_ours(args):
     ncand_last = int(ncand.item()) if ncand is not None else 0
     phase_ms, nsteps, step_ms = timer.read()
 
-    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t_max.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
     units = wl.ndm * T
-    value = world * units * args.steps / (elapsed_ms / 1e3)
+    value = aggregate_throughput(units, args.steps, world, elapsed_ms / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers ----------------
     e2e = None
@@ -406,10 +420,7 @@ def run_ours(args):
             d2h += (8 + 16 * min(n, args.max_cands)) if plan.output == "cands" else plan.out_bytes
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        tmax = torch.tensor([el], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * units * args.e2e_steps / float(tmax.item()), "unit": UNIT,
+        e2e = {"value": aggregate_throughput(units, args.e2e_steps, world, max_over_ranks(el, dev)), "unit": UNIT,
                "h2d_bytes_per_step": plan.block_bytes, "d2h_bytes_per_step": int(d2h / args.e2e_steps),
                "steps": args.e2e_steps, "api": "tx_execute_host (pinned host block in, results out, synchronous)"}
 

@@ -255,6 +255,71 @@ int32_t tx_timer_read(tx_timer* timer, double* h_ms, int32_t* nsteps, double* h_
 
 void tx_timer_destroy(tx_timer* timer);
 
+/* ---- batched execute: many beams of uneven shape per step ----
+   The paper processes a beam block by block (Sec. 2.3 data flow, Sec. 3:
+   blocks of about a second) on CPU cores; on one GPU many beams share each
+   step. A batch binds n (plan, beam) pairs -- any mix of channel counts,
+   block lengths, DM grids, width ladders, layouts, statistics and output
+   modes, all with uint16 intermediates -- and runs one block of every beam
+   per tx_execute_batch: one ingest launch for all beams, then, per wave, one
+   persistent launch per phase and kernel variant over the concatenated work
+   of the wave's beams (stage 1 per tile length, stage 2 per warp split,
+   statistics, boxcar per width-count class and output mode). Each beam's
+   results are exactly those tx_execute would give for the same block, and
+   its beam state (tail, running statistics, block count) advances the same way.
+
+   Waves: with workspace_budget > 0 the beams are split, in order, into waves
+   whose summed per-beam workspace (tx_plan_info.workspace_bytes) fits the
+   budget; waves run one after another in the same workspace. With
+   workspace_budget <= 0 all beams form one wave.
+
+   TX_BATCH_GRAPH: the first two steps are captured (on a private stream) as
+   CUDA graphs, one per argument buffer, and later steps replay them; without
+   the flag every step enqueues its launches directly. Either way a step first
+   copies the per-beam arguments (pointers, ring positions) from one of two
+   pinned host buffers, and a call waits for the step two calls back to finish
+   before it rewrites that step's buffer. Consecutive calls on one batch must
+   go to the same stream. A beam in a batch must not be used by other calls
+   while the batch is in use. */
+#define TX_BATCH_GRAPH 1
+
+typedef struct tx_batch tx_batch;
+
+typedef struct tx_batch_info {
+  int32_t nbeams;           /* n                                                    */
+  int32_t nwaves;           /* waves under the workspace budget                     */
+  int32_t nlaunches;        /* kernel launches per step                             */
+  int32_t flags;            /* TX_BATCH_* flags of the batch                        */
+  int64_t workspace_bytes;  /* d_workspace bytes tx_execute_batch needs             */
+  int64_t dm_trial_samples; /* sum over beams of ndm * T: DM-trial x samples a step */
+} tx_batch_info;
+
+/* Builds a batch on the current device: plans[i] with beams[i] (created for
+   that plan on this device, each beam at most once). Uploads the plans'
+   tables if needed and allocates the batch's work lists and argument
+   buffers. Errors: INVALID_ARG, UNSUPPORTED (int32 intermediates, or shapes
+   beyond a launch's limits), BUDGET (one beam's workspace exceeds the
+   budget), OOM, CUDA. */
+int32_t tx_batch_create(int32_t n, const tx_plan* const* plans, tx_beam* const* beams,
+                        int64_t workspace_budget, int32_t flags, tx_batch** out);
+
+int32_t tx_batch_get_info(const tx_batch* batch, tx_batch_info* info);
+
+/* One step of every beam of the batch. Host arrays of n device pointers:
+     d_blocks[i]  beam i's block, as d_block of tx_execute
+     d_outs[i]    beam i's output, info.out_bytes of its plan
+     d_ncands     may be NULL when no beam is in TX_OUT_CANDS mode; else
+                  d_ncands[i] is beam i's int64 counter (NULL for other modes)
+     d_workspace  tx_batch_info.workspace_bytes of device scratch
+   Enqueued on `stream`; may block the host until the step two calls back
+   has finished (see above). */
+int32_t tx_execute_batch(tx_batch* batch, const uint8_t* const* d_blocks, void* const* d_outs,
+                         int64_t* const* d_ncands, void* d_workspace, void* stream);
+
+/* Waits for the batch's steps in flight, then frees what it holds (not the
+   plans or beams). */
+void tx_batch_destroy(tx_batch* batch);
+
 /* ---- allocation-free de-dispersion (the paper has no counterpart) ----
    For callers that cannot call cudaMalloc: real-time loops that must not take
    the allocator's locks or its implicit synchronisation, hosts that embed the

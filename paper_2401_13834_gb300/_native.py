@@ -47,6 +47,16 @@ class _Info(C.Structure):
     ]
 
 
+class _BatchInfo(C.Structure):
+    _fields_ = [
+        ("nbeams", C.c_int32), ("nwaves", C.c_int32), ("nlaunches", C.c_int32), ("flags", C.c_int32),
+        ("workspace_bytes", C.c_int64), ("dm_trial_samples", C.c_int64),
+    ]
+
+
+TX_BATCH_GRAPH = 1
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -82,6 +92,10 @@ def _load():
         "tx_timer_read": (I32, [P, VP, C.POINTER(I32), VP]),
         "tx_timer_destroy": (None, [P]),
         "tx_dedisperse_noalloc": (I32, [P, VP, I64, VP, VP]),
+        "tx_batch_create": (I32, [I32, VP, VP, I64, I32, C.POINTER(P)]),
+        "tx_batch_get_info": (I32, [P, C.POINTER(_BatchInfo)]),
+        "tx_execute_batch": (I32, [P, VP, VP, VP, VP, VP]),
+        "tx_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -346,3 +360,52 @@ def dedisperse_noalloc(plan: Plan, x, ld: int, series, stream=None):
     CUDA tensor of ndm * (T + W_max - 1) elements. Nothing is allocated.
     """
     _check(lib.tx_dedisperse_noalloc(plan.handle, _ptr(x), int(ld), _ptr(series), _stream_ptr(stream)))
+
+
+class Batch:
+    """Many (plan, beam) pairs run one block each per step (tx_execute_batch).
+
+    ``workspace_budget`` > 0 splits the beams into waves that share a workspace
+    of at most that many bytes; ``graph`` replays the step's launches as CUDA
+    graphs. The plans and beams must outlive the batch.
+    """
+
+    def __init__(self, plans, beams, workspace_budget=0, graph=True):
+        assert len(plans) == len(beams) and len(plans) > 0
+        self.plans, self.beams = list(plans), list(beams)
+        n = len(plans)
+        ph = (C.c_void_p * n)(*[p.handle.value for p in plans])
+        bh = (C.c_void_p * n)(*[b.handle.value for b in beams])
+        h = C.c_void_p()
+        _check(lib.tx_batch_create(n, ph, bh, int(workspace_budget), TX_BATCH_GRAPH if graph else 0, C.byref(h)))
+        self._h = h
+        inf = _BatchInfo()
+        _check(lib.tx_batch_get_info(h, C.byref(inf)))
+        self.info = {k: int(getattr(inf, k)) for k, _ in _BatchInfo._fields_}
+        for k, v in self.info.items():
+            setattr(self, k, v)
+
+    def alloc_workspace(self, device=None):
+        import torch
+        return torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=device or "cuda")
+
+    def alloc_outs(self, device=None):
+        """[(out, ncand or None)] per beam."""
+        return [p.alloc_out(device) for p in self.plans]
+
+    def execute(self, blocks, outs, workspace, stream=None):
+        """One block per beam (uint8 CUDA tensors); outs as from alloc_outs."""
+        n = len(self.plans)
+        assert len(blocks) == n and len(outs) == n
+        for p, blk in zip(self.plans, blocks):
+            assert blk.is_cuda and blk.is_contiguous() and blk.numel() == p.nchan * p.nsamp
+        bp = (C.c_void_p * n)(*[b.data_ptr() for b in blocks])
+        op = (C.c_void_p * n)(*[o.data_ptr() for o, _ in outs])
+        cp = (C.c_void_p * n)(*[0 if c is None else c.data_ptr() for _, c in outs])
+        _check(lib.tx_execute_batch(self._h, bp, op, cp, _ptr(workspace), _stream_ptr(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and lib is not None:
+            lib.tx_batch_destroy(h)
+            self._h = None

@@ -2,10 +2,11 @@
 
     python -m paper_2401_13834_gb300.build [--force]
 
-Two translation units: plan.cpp (host tables, g++ with -ffp-contract=off so
-the Eq. 1 delay tables round identically on every host) and kernels.cu
-(nvcc, -gencode arch=compute_103a,code=sm_103a). They compile in parallel and
-link with nvcc -shared. The result lives next to this file under _lib/.
+Translation units: plan.cpp (host tables, g++ with -ffp-contract=off so the
+Eq. 1 delay tables round identically on every host) and every .cu file under
+csrc/ (nvcc, -gencode arch=compute_103a,code=sm_103a): kernels.cu (single
+beam) and batch.cu (batched execute), both on the kernels in kernels.cuh.
+They compile in parallel and link with nvcc -shared. The result lives next to this file under _lib/.
 """
 from __future__ import annotations
 
@@ -57,21 +58,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIBPATH
     os.makedirs(OUTDIR, exist_ok=True)
     nvcc = _nvcc()
-    obj_plan = os.path.join(OUTDIR, "plan.o")
-    obj_kern = os.path.join(OUTDIR, "kernels.o")
     cxx = os.environ.get("CXX", "g++")
-    cmd_plan = [cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-I", INCLUDE,
-                "-I", CSRC, "-c", os.path.join(CSRC, "plan.cpp"), "-o", obj_plan]
-    cmd_kern = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-                "-Xptxas", "-v" if verbose else "-O3",
-                "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, "kernels.cu"), "-o", obj_kern]
-    with ThreadPoolExecutor(2) as ex:
-        outs = list(ex.map(_run, [cmd_plan, cmd_kern]))
+    objs, cmds = [], []
+    obj_plan = os.path.join(OUTDIR, "plan.o")
+    cmds.append([cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-I", INCLUDE,
+                 "-I", CSRC, "-c", os.path.join(CSRC, "plan.cpp"), "-o", obj_plan])
+    objs.append(obj_plan)
+    for cu in sorted(f for f in os.listdir(CSRC) if f.endswith(".cu")):
+        obj = os.path.join(OUTDIR, cu[:-3] + ".o")
+        cmds.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+                     "-Xptxas", "-v" if verbose else "-O3",
+                     "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, cu), "-o", obj])
+        objs.append(obj)
+    with ThreadPoolExecutor(len(cmds)) as ex:
+        outs = list(ex.map(_run, cmds))
     if verbose:
         for o in outs:
             sys.stdout.write(o)
     tmp = LIBPATH + ".tmp"
-    _run([nvcc, ARCH, "-shared", "-o", tmp, obj_plan, obj_kern, "-lcudart"])
+    _run([nvcc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
     os.replace(tmp, LIBPATH)
     return LIBPATH
 

@@ -1,0 +1,474 @@
+// Batched execute: one block of each of many beams of uneven shape (channel
+// counts, block lengths, DM grids, widths, output modes) per step, with each
+// phase of the hot path run as persistent launches over the concatenated work
+// of all beams instead of one launch sequence per beam (Sec. 2.3 blocked
+// processing, applied to many beams at once). A step's launches can be
+// captured once as a CUDA graph and replayed; what changes from step to step
+// (input and output pointers, ring positions) lives in a per-beam argument
+// array that the step copies to the device first.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tx_internal.h"
+
+using namespace tx;
+
+#define TX_CUDA(expr)                                                               \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      set_error("%s failed: %s", #expr, cudaGetErrorString(e_));                    \
+      return TX_ERR_CUDA;                                                           \
+    }                                                                               \
+  } while (0)
+
+namespace {
+
+enum LaunchKind { kIngest = 0, kStage1 = 1, kStage2 = 2, kStats = 3, kBoxcar = 4 };
+
+// One persistent launch of a step over the units of its member beams.
+struct BatchLaunch {
+  int kind = 0;
+  int q1 = 0, split = 0, nwc = 0, mode = 0;  // template selectors
+  int grid = 0, threads = 0, smem = 0;
+  int nmem = 0, nunits = 0;                  // member beams, units (stage 1: work items)
+  int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
+  int64_t items = 0;                         // stage 1: offset of its work items
+  int layout = 0;                            // stage 1 mL, stage 2 slot words, boxcar wmaxL
+};
+
+int64_t mod64(int64_t a, int64_t r) { return ((a % r) + r) % r; }
+
+}  // namespace
+
+struct tx_batch {
+  int n = 0, device = -1, flags = 0, nwaves = 0, num_sms = 0;
+  std::vector<const tx_plan*> plans;
+  std::vector<tx_beam*> beams;
+  std::vector<int64_t> ws_off;   // per beam, inside the shared workspace (waves reuse it)
+  int64_t ws_bytes = 0;
+  int64_t dm_samples = 0;
+  std::vector<BatchLaunch> launches;
+  BeamArgs* d_args = nullptr;    // [n]
+  int32_t* d_tab = nullptr;      // unit offsets and member lists of every launch
+  Stage1Item* d_items = nullptr; // stage-1 work items of every stage-1 launch, pad0 = beam
+  BeamArgs* h_args[2] = {nullptr, nullptr};  // pinned, alternating between steps
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaStream_t cap = nullptr;    // private stream for graph capture
+  int64_t nsteps = 0;
+};
+
+namespace {
+
+// The kernel a batched launch runs.
+const void* launch_kernel(const BatchLaunch& L) {
+  switch (L.kind) {
+    case kIngest: return (const void*)k_ingest_batch;
+    case kStage1:
+      switch (L.q1) {
+        case 256: return (const void*)k_stage1<256, uint16_t, true>;
+        case 128: return (const void*)k_stage1<128, uint16_t, true>;
+        case 64: return (const void*)k_stage1<64, uint16_t, true>;
+        default: return (const void*)k_stage1<32, uint16_t, true>;
+      }
+    case kStage2:
+      switch (L.split) {
+        case 8: return (const void*)k_stage2_u16<512, 32, 8, true>;
+        case 4: return (const void*)k_stage2_u16<512, 32, 4, true>;
+        case 2: return (const void*)k_stage2_u16<512, 32, 2, true>;
+        default: return (const void*)k_stage2_u16<256, 32, 1, true>;
+      }
+    case kStats: return (const void*)k_stats<true>;
+    default: return (const void*)box_kernel<true>(L.nwc, L.mode);
+  }
+}
+
+int build_batch(tx_batch* B, int64_t budget) {
+  const int n = B->n;
+  // ---- waves under the workspace budget --------------------------------------
+  std::vector<int> wave(n, 0);
+  B->ws_off.assign(n, 0);
+  int64_t cur = 0;
+  int w = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t need = B->plans[i]->ws_bytes;
+    if (budget > 0 && need > budget) {
+      set_error("beam %d needs %lld workspace bytes, more than the budget %lld", i, (long long)need, (long long)budget);
+      return TX_ERR_BUDGET;
+    }
+    if (budget > 0 && cur + need > budget) { ++w; cur = 0; }
+    wave[i] = w;
+    B->ws_off[i] = cur;
+    cur += need;
+    B->ws_bytes = std::max(B->ws_bytes, cur);
+    B->dm_samples += (int64_t)B->plans[i]->ndm * B->plans[i]->T;
+  }
+  B->nwaves = w + 1;
+
+  std::vector<int32_t> tab;
+  std::vector<Stage1Item> items;
+  // unit offsets and member list of one launch
+  auto add_members = [&](BatchLaunch& L, const std::vector<int>& mem, auto units_of) -> int {
+    L.nmem = (int)mem.size();
+    L.off = (int64_t)tab.size();
+    int64_t total = 0;
+    for (int b : mem) {
+      tab.push_back((int32_t)total);
+      total += units_of(b);
+    }
+    tab.push_back((int32_t)total);
+    if (total >= INT32_MAX) { set_error("a batched launch has too many work units (%lld)", (long long)total); return TX_ERR_UNSUPPORTED; }
+    L.mem = (int64_t)tab.size();
+    for (int b : mem) tab.push_back(b);
+    L.nunits = (int)total;
+    return TX_OK;
+  };
+  const int nsm = std::max(B->num_sms, 1);
+  int rc;
+
+  // ---- ingest: every beam, one launch ----------------------------------------
+  {
+    BatchLaunch L;
+    L.kind = kIngest;
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    rc = add_members(L, all, [&](int b) -> int64_t {
+      const tx_plan* p = B->plans[b];
+      return p->layout == TX_LAYOUT_TF ? ((p->T + 63) / 64) * ((p->nchan + 63) / 64)
+                                       : (int64_t)p->nchan * ((p->T + 4095) / 4096);
+    });
+    if (rc) return rc;
+    L.threads = 256;
+    L.grid = std::min(L.nunits, nsm * 8);
+    if (L.nunits > 0) B->launches.push_back(L);
+  }
+
+  for (int wv = 0; wv < B->nwaves; ++wv) {
+    std::vector<int> mem;
+    for (int i = 0; i < n; ++i)
+      if (wave[i] == wv) mem.push_back(i);
+    // ---- stage 1, one launch per tile length q1 ----------------------------------
+    std::map<int, std::vector<int>> by_q;
+    for (int b : mem) by_q[B->plans[b]->q1].push_back(b);
+    for (auto& kv : by_q) {
+      BatchLaunch L;
+      L.kind = kStage1;
+      L.q1 = kv.first;
+      L.items = (int64_t)items.size();
+      int mL = 0;
+      for (int b : kv.second) {
+        const tx_plan* p = B->plans[b];
+        mL = std::max(mL, p->m);
+        for (Stage1Item it : p->items1) {
+          it.pad0 = b;
+          items.push_back(it);
+        }
+      }
+      const int64_t nit = (int64_t)items.size() - L.items;
+      if (nit >= INT32_MAX) { set_error("too many stage-1 items in one batched launch"); return TX_ERR_UNSUPPORTED; }
+      L.nunits = (int)nit;
+      L.layout = mL;
+      L.smem = (int)stage1_smem_bytes(mL, L.q1);
+      if (L.smem > kSmemMax) { set_error("stage-1 shared memory for %d channels per sub-band exceeds the limit", mL); return TX_ERR_UNSUPPORTED; }
+      L.threads = kStage1Warps * 32;
+      L.grid = std::min(L.nunits, nsm);
+      if (L.nunits > 0) B->launches.push_back(L);
+    }
+    // ---- stage 2, one launch per warp split (tile width follows) -------------------
+    // Shared memory is laid out for the largest staged chunk and table of the
+    // launch; a split class whose mix would not fit is launched per chunk size.
+    std::map<int, std::vector<int>> by_split;
+    for (int b : mem) by_split[stage2_split(B->plans[b])].push_back(b);
+    auto s2_smem = [&](const std::vector<int>& g) {
+      int slot = 0, sc = 0;
+      for (int b : g) {
+        slot = std::max(slot, B->plans[b]->nsub_chunk2 * B->plans[b]->sww2);
+        sc = std::max(sc, B->plans[b]->nsub_chunk2);
+      }
+      return std::make_pair(slot, stage2_u16_smem_for(slot, sc));
+    };
+    std::vector<std::pair<int, std::vector<int>>> s2groups;
+    for (auto& kv : by_split) {
+      if (s2_smem(kv.second).second <= kSmemMax - 1024) {  // room for the static sums
+        s2groups.push_back(kv);
+        continue;
+      }
+      std::map<int, std::vector<int>> by_sc;
+      for (int b : kv.second) by_sc[B->plans[b]->nsub_chunk2].push_back(b);
+      for (auto& kc : by_sc) s2groups.push_back({kv.first, kc.second});
+    }
+    for (auto& kv : s2groups) {
+      BatchLaunch L;
+      L.kind = kStage2;
+      L.split = kv.first;
+      if ((rc = add_members(L, kv.second, [&](int b) -> int64_t { return (int64_t)B->plans[b]->nk * B->plans[b]->ntile2; })))
+        return rc;
+      int threads = 0;
+      for (int b : kv.second) threads = std::max(threads, stage2_threads(B->plans[b]));
+      const auto sm = s2_smem(kv.second);
+      L.layout = sm.first;
+      L.smem = sm.second;
+      if (L.smem > kSmemMax - 1024) { set_error("batched stage-2 shared memory (%d bytes) exceeds the limit", L.smem); return TX_ERR_UNSUPPORTED; }
+      L.threads = threads;
+      L.grid = std::min(L.nunits, nsm);
+      if (L.nunits > 0) B->launches.push_back(L);
+    }
+    // ---- statistics, then boxcar per (width class, output mode) ----------------------
+    std::vector<int> filt;
+    for (int b : mem)
+      if (B->plans[b]->output != TX_OUT_SERIES) filt.push_back(b);
+    if (!filt.empty()) {
+      BatchLaunch L;
+      L.kind = kStats;
+      if ((rc = add_members(L, filt, [&](int b) -> int64_t { return B->plans[b]->ndm; }))) return rc;
+      L.threads = 128;
+      L.grid = (L.nunits + 127) / 128;
+      B->launches.push_back(L);
+    }
+    std::map<std::pair<int, int>, std::vector<int>> by_box;
+    for (int b : filt) by_box[{box_class(B->plans[b]->nw), B->plans[b]->output}].push_back(b);
+    for (auto& kv : by_box) {
+      BatchLaunch L;
+      L.kind = kBoxcar;
+      L.nwc = kv.first.first;
+      L.mode = kv.first.second;
+      if ((rc = add_members(L, kv.second, [&](int b) -> int64_t { return (int64_t)B->plans[b]->ndm * B->plans[b]->ntile3; })))
+        return rc;
+      int wm = 0;
+      for (int b : kv.second) wm = std::max(wm, B->plans[b]->wmax);
+      L.layout = wm;
+      L.smem = box_smem_for(wm);
+      const BoxKernel k = box_kernel<true>(L.nwc, L.mode);
+      TX_CUDA(raise_smem_limit((const void*)k, L.smem));  // before the occupancy query
+      int bps = 1;
+      TX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kBoxThreads, L.smem));
+      L.threads = kBoxThreads;
+      L.grid = std::min(L.nunits, nsm * std::max(bps, 1));
+      if (L.nunits > 0) B->launches.push_back(L);
+    }
+  }
+
+  // ---- shared memory limit of each batched kernel: the most any launch asks --------
+  std::map<const void*, int> need;
+  for (const BatchLaunch& L : B->launches) {
+    const void* k = launch_kernel(L);
+    need[k] = std::max(need[k], L.smem);
+  }
+  for (auto& kv : need)
+    TX_CUDA(raise_smem_limit(kv.first, kv.second));
+
+  // ---- device tables, pinned argument buffers ----------------------------------
+  TX_CUDA(cudaMalloc((void**)&B->d_args, (size_t)n * sizeof(BeamArgs)));
+  TX_CUDA(cudaMalloc((void**)&B->d_tab, std::max<size_t>(tab.size(), 1) * 4));
+  if (!tab.empty()) TX_CUDA(cudaMemcpy(B->d_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice));
+  TX_CUDA(cudaMalloc((void**)&B->d_items, std::max<size_t>(items.size(), 1) * sizeof(Stage1Item)));
+  if (!items.empty())
+    TX_CUDA(cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(Stage1Item), cudaMemcpyHostToDevice));
+  for (int i = 0; i < 2; ++i) {
+    TX_CUDA(cudaHostAlloc((void**)&B->h_args[i], (size_t)n * sizeof(BeamArgs), cudaHostAllocDefault));
+    std::memset(B->h_args[i], 0, (size_t)n * sizeof(BeamArgs));
+    TX_CUDA(cudaEventCreateWithFlags(&B->done[i], cudaEventDisableTiming));
+  }
+  TX_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  return TX_OK;
+}
+
+// Enqueues one step: the argument copy, then every launch in order.
+int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
+  TX_CUDA(cudaMemcpyAsync(B->d_args, h_src, (size_t)B->n * sizeof(BeamArgs), cudaMemcpyHostToDevice, st));
+  const BeamArgs none{};
+  for (const BatchLaunch& L : B->launches) {
+    const int32_t* off = B->d_tab + L.off;
+    const int32_t* mem = B->d_tab + L.mem;
+    switch (L.kind) {
+      case kIngest:
+        k_ingest_batch<<<L.grid, L.threads, 0, st>>>(B->d_args, off, mem, L.nmem, L.nunits);
+        break;
+      case kStage1: {
+        const Stage1Item* it = B->d_items + L.items;
+#define TX_B1(Q) \
+  k_stage1<Q, uint16_t, true><<<L.grid, L.threads, L.smem, st>>>(none, B->d_args, it, L.nunits, L.layout, 1u)
+        switch (L.q1) {
+          case 256: TX_B1(256); break;
+          case 128: TX_B1(128); break;
+          case 64: TX_B1(64); break;
+          default: TX_B1(32); break;
+        }
+#undef TX_B1
+        break;
+      }
+      case kStage2:
+#define TX_B2(NW, SP)                                                                                         \
+  k_stage2_u16<NW, 32, SP, true><<<L.grid, L.threads, L.smem, st>>>(none, B->d_args, off, mem, L.nmem, L.nunits, \
+                                                                    L.layout)
+        switch (L.split) {
+          case 8: TX_B2(512, 8); break;
+          case 4: TX_B2(512, 4); break;
+          case 2: TX_B2(512, 2); break;
+          default: TX_B2(256, 1); break;
+        }
+#undef TX_B2
+        break;
+      case kStats:
+        k_stats<true><<<L.grid, L.threads, 0, st>>>(none, B->d_args, off, mem, L.nmem, L.nunits);
+        break;
+      default:
+        box_kernel<true>(L.nwc, L.mode)<<<L.grid, L.threads, L.smem, st>>>(none, B->d_args, off, mem, L.nmem,
+                                                                          L.nunits, L.layout);
+        break;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, launch_kernel(L));
+      set_error("batched launch (phase %d, grid %d, %d threads, %d + %zu bytes shared; kernel allows %d threads, "
+                "%d dynamic bytes) failed: %s", L.kind, L.grid, L.threads, L.smem, fa.sharedSizeBytes,
+                fa.maxThreadsPerBlock, fa.maxDynamicSharedSizeBytes, cudaGetErrorString(e));
+      return TX_ERR_CUDA;
+    }
+  }
+  return TX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t tx_batch_create(int32_t n, const tx_plan* const* plans, tx_beam* const* beams, int64_t workspace_budget,
+                        int32_t flags, tx_batch** out) {
+  if (!out || !plans || !beams || n < 1) { set_error("need n >= 1 plans and beams and an output handle"); return TX_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (flags & ~TX_BATCH_GRAPH) { set_error("unknown batch flags 0x%x", flags); return TX_ERR_INVALID_ARG; }
+  int dev = 0;
+  TX_CUDA(cudaGetDevice(&dev));
+  for (int i = 0; i < n; ++i) {
+    const tx_plan* p = plans[i];
+    const tx_beam* b = beams[i];
+    if (!p || !b) { set_error("null plan or beam at %d", i); return TX_ERR_INVALID_ARG; }
+    if (b->plan != p) { set_error("beam %d was created for another plan", i); return TX_ERR_INVALID_ARG; }
+    if (b->device != dev) { set_error("beam %d lives on device %d, current device is %d", i, b->device, dev); return TX_ERR_INVALID_ARG; }
+    if (p->interm != TX_INTERM_U16) { set_error("batched execute needs uint16 intermediates (beam %d)", i); return TX_ERR_UNSUPPORTED; }
+    for (int j = 0; j < i; ++j)
+      if (beams[j] == b) { set_error("beam %d appears twice in the batch", i); return TX_ERR_INVALID_ARG; }
+    int rc = tx_upload_plan(p);
+    if (rc) return rc;
+  }
+  tx_batch* B = new (std::nothrow) tx_batch();
+  if (!B) { set_error("out of host memory"); return TX_ERR_OOM; }
+  B->n = n;
+  B->device = dev;
+  B->flags = flags;
+  B->plans.assign(plans, plans + n);
+  B->beams.assign(beams, beams + n);
+  int rc = TX_OK;
+  if (cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    set_error("cudaDeviceGetAttribute failed");
+    rc = TX_ERR_CUDA;
+  }
+  if (rc == TX_OK) {
+    try {
+      rc = build_batch(B, workspace_budget);
+    } catch (const std::bad_alloc&) {
+      set_error("out of host memory");
+      rc = TX_ERR_OOM;
+    }
+  }
+  if (rc) { tx_batch_destroy(B); return rc; }
+  *out = B;
+  return TX_OK;
+}
+
+int32_t tx_batch_get_info(const tx_batch* B, tx_batch_info* info) {
+  if (!B || !info) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  std::memset(info, 0, sizeof(*info));
+  info->nbeams = B->n;
+  info->nwaves = B->nwaves;
+  info->nlaunches = (int32_t)B->launches.size();
+  info->flags = B->flags;
+  info->workspace_bytes = B->ws_bytes;
+  info->dm_trial_samples = B->dm_samples;
+  return TX_OK;
+}
+
+int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* const* d_outs, int64_t* const* d_ncands,
+                         void* d_workspace, void* stream) {
+  if (!B || !d_blocks || !d_outs || !d_workspace) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  int dev = 0;
+  TX_CUDA(cudaGetDevice(&dev));
+  if (dev != B->device) { set_error("batch lives on device %d, current device is %d", B->device, dev); return TX_ERR_INVALID_ARG; }
+  for (int i = 0; i < B->n; ++i) {
+    if (!d_blocks[i] || !d_outs[i]) { set_error("null block or output of beam %d", i); return TX_ERR_INVALID_ARG; }
+    if (B->plans[i]->output == TX_OUT_CANDS && (!d_ncands || !d_ncands[i])) { set_error("beam %d is in candidate mode and needs d_ncands", i); return TX_ERR_INVALID_ARG; }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int slot = (int)(B->nsteps & 1);
+  if (B->used[slot]) TX_CUDA(cudaEventSynchronize(B->done[slot]));  // the step that last read this buffer
+  BeamArgs* h = B->h_args[slot];
+  uint8_t* ws = static_cast<uint8_t*>(d_workspace);
+  for (int i = 0; i < B->n; ++i) {
+    const tx_plan* p = B->plans[i];
+    tx_beam* b = B->beams[i];
+    const int64_t start = mod64(b->head - p->L, p->R);
+    h[i] = make_args(p, b, d_blocks[i], d_outs[i], d_ncands ? d_ncands[i] : nullptr, ws + B->ws_off[i], b->head,
+                     start);
+  }
+  if (B->flags & TX_BATCH_GRAPH) {
+    if (!B->exec[slot]) {
+      cudaGraph_t g = nullptr;
+      TX_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+      const int rc = enqueue(B, h, B->cap);
+      const cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      TX_CUDA(e);
+      const cudaError_t ei = cudaGraphInstantiate(&B->exec[slot], g, 0);
+      cudaGraphDestroy(g);
+      TX_CUDA(ei);
+    }
+    TX_CUDA(cudaGraphLaunch(B->exec[slot], st));
+  } else {
+    const int rc = enqueue(B, h, st);
+    if (rc) return rc;
+  }
+  TX_CUDA(cudaEventRecord(B->done[slot], st));
+  B->used[slot] = true;
+  ++B->nsteps;
+  for (int i = 0; i < B->n; ++i) {
+    tx_beam* b = B->beams[i];
+    b->head = mod64(b->head + B->plans[i]->T, B->plans[i]->R);
+    ++b->nblocks;
+  }
+  return TX_OK;
+}
+
+void tx_batch_destroy(tx_batch* B) {
+  if (!B) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (B->device >= 0) cudaSetDevice(B->device);
+  for (int i = 0; i < 2; ++i) {
+    if (B->used[i]) cudaEventSynchronize(B->done[i]);
+    if (B->exec[i]) cudaGraphExecDestroy(B->exec[i]);
+    if (B->done[i]) cudaEventDestroy(B->done[i]);
+    if (B->h_args[i]) cudaFreeHost(B->h_args[i]);
+  }
+  if (B->cap) cudaStreamDestroy(B->cap);
+  cudaFree(B->d_args);
+  cudaFree(B->d_tab);
+  cudaFree(B->d_items);
+  cudaSetDevice(prev);
+  delete B;
+}
+
+}  // extern "C"

@@ -1,0 +1,1049 @@
+// Device kernels (sm_103a) of the hot path: ingest, two-stage sub-band
+// de-dispersion (Sec. 2.3), block statistics, and the boxcar matched filter
+// with its outputs (Sec. 2.4, 2.5). Included by kernels.cu (one beam per
+// execute) and batch.cu (many beams of uneven shape per launch); each
+// translation unit instantiates the templates it launches.
+//
+// Kernel map (one execute):
+//   k_ingest_*   Sec. 2.3 data-flow steps 1, 2 and 4: the new block lands
+//                channel-major in the beam's circular buffer behind the carried
+//                tail (time-major input is transposed on the way); nothing is
+//                shifted, the buffer start advances by T instead.
+//   k_stage1     stage 1: P[k][s][t] = sum_{c in s} X[c][t + d1[k][c]]
+//   k_stage2_*   stage 2: D[d][t] = sum_s P[k(d)][s][t + d2[d][s]], plus exact
+//                per-tile sums of D and D^2
+//   k_stats      mean / sigma per DM (block or running) and the per-width
+//                constants of Eq. 5
+//   k_boxcar     prefix sums, window sums for every width, S/N (Eq. 5), best
+//                width, and cube / plane / candidates
+//
+// Every kernel reads what it needs about a beam from a BeamArgs. With
+// BATCH = false the BeamArgs is a kernel parameter (one beam, constant bank);
+// with BATCH = true the kernel walks the concatenated work units of several
+// beams and looks each unit's beam up in a device array (unit offsets per
+// member beam, binary search).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "tx_internal.h"
+
+namespace {
+
+using namespace tx;
+
+// ---------------------------------------------------------------------------
+// per-beam arguments of one execute
+// ---------------------------------------------------------------------------
+struct BeamArgs {
+  const uint8_t* block;          // this step's input block (plan layout)
+  uint8_t* ring;                 // [nchan][R] circular buffer
+  void* P;                       // stage-1 sums [nk][nsub][Pp] (uint16 or int32)
+  int32_t* D;                    // series [ndm][Dp]
+  longlong2* part;               // per-tile (sum D, sum D^2) [ndm][ntile2]
+  SnrConst* cst;                 // per (DM, width) S/N constants [ndm][nw]
+  double* run;                   // running (mu, var) [ndm][2]
+  const int32_t* d1;             // [nk][nchan]
+  const int32_t* abase;          // [nk][nsub]
+  const int32_t* e2;             // [ndm][nsub]
+  const int32_t* widths;         // [nw]
+  float* outf;                   // cube / plane S/N
+  uint8_t* outw;                 // plane best-width index
+  tx_cand* cands;                // candidate records
+  unsigned long long* ncand;     // candidate counter
+  int64_t R, head, start, T, Pp, Dp, Td, max_cands;
+  double lam, gamma;
+  int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
+  int32_t layout, ingest_vec, running, output;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ BeamArgs pick(const BeamArgs& one, const BeamArgs* __restrict__ beams, int i) {
+  if constexpr (BATCH) {
+    return beams[i];
+  } else {
+    return one;
+  }
+}
+
+// Member j of a batched launch owns units [off[j], off[j + 1]); returns the
+// j with off[j] <= u < off[j + 1] (off has n + 1 entries).
+__device__ __forceinline__ int find_member(const int32_t* __restrict__ off, int n, int u) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+// a * one + c with `one` a runtime value (always 1): the add is issued as an
+// integer multiply-add on the FMA pipe, leaving the ALU pipe to the byte
+// permutes and the other adds.
+__device__ __forceinline__ void madd(uint32_t& acc, uint32_t a, uint32_t one) {
+  asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(a), "r"(one));
+}
+
+// acc += a >> 16 as one integer multiply-add on the FMA pipe: the high 32 bits
+// of a * 65536 are a >> 16.
+__device__ __forceinline__ void madd_hi16(uint32_t& acc, uint32_t a) {
+  asm("mad.hi.u32 %0, %1, 65536, %0;" : "+r"(acc) : "r"(a));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// ingest (Sec. 2.3 data flow)
+// ---------------------------------------------------------------------------
+// Channel-major rows: ring[c][dst_off + i] = src[c][src_off + i], i < n.
+__global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t src_pitch, int64_t src_off, int64_t n,
+                            uint8_t* __restrict__ ring, int64_t R, int64_t dst_off, int vec) {
+  const int c = blockIdx.y;
+  const uint8_t* s = src + (int64_t)c * src_pitch + src_off;
+  uint8_t* d = ring + (int64_t)c * R + dst_off;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(s);
+    uint4* d4 = reinterpret_cast<uint4*>(d);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 16; i += stride) d4[i] = s4[i];
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) d[i] = s[i];
+  }
+}
+
+// Loads a 64-time x 64-channel byte tile of a time-major block [t][nchan]
+// (times t0.., channels c0..) into tile[time][channel]; 256 threads.
+__device__ __forceinline__ void tf_load_tile(uint8_t (*tile)[80], const uint8_t* __restrict__ src, int64_t t0,
+                                             int64_t n, int c0, int nchan, int vec) {
+  const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+  const int64_t t = t0 + r;
+  const int c = c0 + 16 * q;
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (t < n) {
+    const uint8_t* sp = src + t * nchan + c;
+    if (vec && c + 16 <= nchan) {
+      v = __ldg(reinterpret_cast<const uint4*>(sp));
+    } else {
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      for (int i = 0; i < 16; ++i)
+        if (c + i < nchan) w[i >> 2] |= (uint32_t)sp[i] << (8 * (i & 3));
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  *reinterpret_cast<uint4*>(&tile[r][16 * q]) = v;
+}
+
+// Column cc of a tile, times 16 pq .. 16 pq + 15, as four little-endian words.
+__device__ __forceinline__ void tf_column(const uint8_t (*tile)[80], int cc, int pq, uint32_t w[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w[i] = (uint32_t)tile[16 * pq + 4 * i][cc] | ((uint32_t)tile[16 * pq + 4 * i + 1][cc] << 8) |
+           ((uint32_t)tile[16 * pq + 4 * i + 2][cc] << 16) | ((uint32_t)tile[16 * pq + 4 * i + 3][cc] << 24);
+}
+
+// Time-major block rows [t][nchan], t in [t_off, t_off + n) -> ring[c][dst_off + t - t_off],
+// through a 64-time x 64-channel byte tile. vec: 16-byte loads and stores
+// (nchan, dst_off and the source all 16-byte aligned).
+__global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ src, int64_t t_off, int64_t n,
+                                                   int nchan, uint8_t* __restrict__ ring, int64_t R,
+                                                   int64_t dst_off, int vec) {
+  __shared__ __align__(16) uint8_t tile[64][80];
+  const int64_t t0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
+  tf_load_tile(tile, src + t_off * nchan, t0, n, c0, nchan, vec);
+  __syncthreads();
+  const int cc = threadIdx.x & 63, pq = threadIdx.x >> 6;
+  const int c = c0 + cc;
+  if (c < nchan) {
+    uint32_t w[4];
+    tf_column(tile, cc, pq, w);
+    const int64_t t = t0 + 16 * pq;
+    uint8_t* dp = ring + (int64_t)c * R + dst_off + t;
+    if (vec && t + 16 <= n) {
+      *reinterpret_cast<uint4*>(dp) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      for (int i = 0; i < 16; ++i)
+        if (t + i < n) dp[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+    }
+  }
+}
+
+// Batched ingest: persistent blocks walk the tiles of every member beam's
+// block and write them into that beam's ring at ring position head + t
+// (mod R, R a multiple of 64, so an aligned 16-byte group never straddles the
+// wrap). Time-major tiles are 64 times x 64 channels; channel-major tiles are
+// 4096 samples of one channel.
+__global__ void __launch_bounds__(256) k_ingest_batch(const BeamArgs* __restrict__ beams,
+                                                      const int32_t* __restrict__ uoff,
+                                                      const int32_t* __restrict__ umem, int nmem, int nunits) {
+  __shared__ __align__(16) uint8_t tile[64][80];
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int j = find_member(uoff, nmem, u);
+    const int lu = u - uoff[j];
+    const BeamArgs a = beams[umem[j]];
+    if (a.layout == TX_LAYOUT_TF) {
+      const int nct = (a.nchan + 63) >> 6;
+      const int64_t t0 = (int64_t)(lu / nct) * 64;
+      const int c0 = (lu % nct) * 64;
+      __syncthreads();  // the previous tile's readers are done with `tile`
+      tf_load_tile(tile, a.block, t0, a.T, c0, a.nchan, a.ingest_vec);
+      __syncthreads();
+      const int cc = threadIdx.x & 63, pq = threadIdx.x >> 6;
+      const int c = c0 + cc;
+      if (c < a.nchan) {
+        uint32_t w[4];
+        tf_column(tile, cc, pq, w);
+        const int64_t t = t0 + 16 * pq;
+        int64_t pos = a.head + t;
+        if (pos >= a.R) pos -= a.R;
+        uint8_t* row = a.ring + (int64_t)c * a.R;
+        if (a.ingest_vec && t + 16 <= a.T) {
+          *reinterpret_cast<uint4*>(row + pos) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+          for (int i = 0; i < 16; ++i) {
+            if (t + i >= a.T) break;
+            int64_t pb = pos + i;
+            if (pb >= a.R) pb -= a.R;
+            row[pb] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+          }
+        }
+      }
+    } else {
+      const int nchunk = (int)((a.T + 4095) >> 12);
+      const int c = lu / nchunk;
+      const int64_t t = (int64_t)(lu - c * nchunk) * 4096 + 16 * threadIdx.x;
+      if (t < a.T) {
+        const uint8_t* src = a.block + (int64_t)c * a.T;
+        uint8_t* row = a.ring + (int64_t)c * a.R;
+        int64_t pos = a.head + t;
+        if (pos >= a.R) pos -= a.R;
+        if (a.ingest_vec && t + 16 <= a.T) {
+          *reinterpret_cast<uint4*>(row + pos) = __ldg(reinterpret_cast<const uint4*>(src + t));
+        } else {
+          for (int i = 0; i < 16 && t + i < a.T; ++i) {
+            int64_t pb = pos + i;
+            if (pb >= a.R) pb -= a.R;
+            row[pb] = src[t + i];
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage 1 (Sec. 2.3: de-disperse each sub-band on the coarse DM grid)
+// ---------------------------------------------------------------------------
+// Sums one coarse DM over the sub-band's m channels for VW words per lane,
+// starting at word jbase of the tile, and stores the 4 * VW * 32 outputs.
+template <int Q, int VW, typename PT>
+__device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const uint32_t* __restrict__ t, int m,
+                                           uint32_t one, int lane, int jbase, PT* __restrict__ prow, int rel0,
+                                           int64_t Pp) {
+  uint32_t aw[VW], ah[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+  const uint32_t* base = S + jbase + lane;
+  int c = 0;
+  for (; c + 3 < m; c += 4) {
+    const uint4 oo = *reinterpret_cast<const uint4*>(t + c);
+    const uint32_t* r0 = base + oo.x;
+    const uint32_t* r1 = base + oo.y;
+    const uint32_t* r2 = base + oo.z;
+    const uint32_t* r3 = base + oo.w;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const uint32_t w0 = r0[32 * v], w1 = r1[32 * v], w2 = r2[32 * v], w3 = r3[32 * v];
+      madd(aw[v], w0, one);
+      madd(aw[v], w1, one);
+      madd(aw[v], w2, one);
+      madd(aw[v], w3, one);
+      ah[v] += __byte_perm(w0, 0u, 0x4341) + __byte_perm(w1, 0u, 0x4341);
+      ah[v] += __byte_perm(w2, 0u, 0x4341) + __byte_perm(w3, 0u, 0x4341);
+    }
+  }
+  for (; c < m; ++c) {
+    const uint32_t* r0 = base + t[c];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const uint32_t w0 = r0[32 * v];
+      madd(aw[v], w0, one);
+      ah[v] += __byte_perm(w0, 0u, 0x4341);
+    }
+  }
+  const int r = rel0 + jbase;
+  if (r >= 0 && (int64_t)r + 4 * Q - jbase <= Pp) {
+    // every output inside the row: unguarded stores at fixed offsets
+    PT* o = prow + r + lane;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const uint32_t lo = aw[v] - (ah[v] << 8);
+      const PT v0 = (PT)(lo & 0xFFFFu), v1 = (PT)(ah[v] & 0xFFFFu), v2 = (PT)(lo >> 16), v3 = (PT)(ah[v] >> 16);
+      o[32 * v] = v0;
+      o[32 * v + Q] = v1;
+      o[32 * v + 2 * Q] = v2;
+      o[32 * v + 3 * Q] = v3;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const int j = lane + 32 * v;
+      const uint32_t lo = aw[v] - (ah[v] << 8);
+      const uint32_t val[4] = {lo & 0xFFFFu, ah[v] & 0xFFFFu, lo >> 16, ah[v] >> 16};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t u = (uint32_t)(r + j + q * Q);
+        if (u < (uint64_t)Pp) prow[u] = (PT)val[q];
+      }
+    }
+  }
+}
+
+// Persistent blocks walk the work items (sub-band s, coarse DMs [kb, ke),
+// absolute times [tau0, tau0 + 4Q)); in a batch, item field pad0 names the
+// beam. For each item the channels' input windows (from 16-byte aligned ring
+// positions) are copied with cp.async into a raw buffer while the previous
+// item is being summed, then rearranged so that shared word S[c][j] holds
+// channel c's samples at raw offsets j + qQ in byte q (q = 0..3). For coarse
+// DM k the output word j is sum_c S[c][j + a_c + d1[k][c] - d1[kb][c]] (a_c
+// the window's misalignment): four outputs per 32-bit load whatever the
+// delays. Sums use the byte-lane identity
+//   sum w = sum(lo lanes) + 256 * sum(hi lanes)  (mod 2^32)
+// with the hi lanes (bytes 1, 3) accumulated separately as 16-bit lanes,
+// exact for up to 257 channels per sub-band. Warps take (coarse DM, part of
+// the tile) tasks; a chunk with few coarse DMs splits each tile between 2, 4
+// or 8 warps. Shared memory is laid out for mL channels (the largest sub-band
+// of the launch), so an item's prefetch never overlaps the previous item's
+// staged words or table.
+template <int Q, typename PT, bool BATCH>
+__global__ void __launch_bounds__(kStage1Warps * 32, 1)
+k_stage1(const BeamArgs one, const BeamArgs* __restrict__ beams, const Stage1Item* __restrict__ items, int nitems,
+         int mL, uint32_t unit) {
+  extern __shared__ __align__(16) uint8_t smem1[];
+  constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
+  constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
+  constexpr int NCH = RB / 16;
+  constexpr int V = Q / 32;
+  uint32_t* S = reinterpret_cast<uint32_t*>(smem1);
+  uint8_t* raw = smem1 + (size_t)mL * SW * 4;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(raw + (size_t)mL * RB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // physical ring position of channel c's first wanted sample for an item
+  auto wstart = [&](const BeamArgs& a, const Stage1Item& it, int c) -> int {
+    int64_t p = a.start + it.tau0 + a.d1[(size_t)it.kb * a.nchan + it.s * a.m + c];
+    while (p >= a.R) p -= a.R;
+    return (int)p;
+  };
+  auto issue = [&](int idx) {
+    const Stage1Item it = items[idx];
+    const BeamArgs a = pick<BATCH>(one, beams, it.pad0);
+    const int R = (int)a.R;
+    for (int c = warp; c < a.m; c += kStage1Warps) {
+      const int pa = wstart(a, it, c) & ~15;
+      const uint8_t* row = a.ring + (size_t)(it.s * a.m + c) * R;
+      uint8_t* dst = raw + (size_t)c * RB;
+      for (int ch = lane; ch < NCH; ch += 32) {
+        int q = pa + 16 * ch;  // R is a multiple of 64: a chunk never straddles the wrap
+        while (q >= R) q -= R;
+        cp_async16(dst + 16 * ch, row + q);
+      }
+    }
+    cp_async_commit();
+  };
+
+  int idx = blockIdx.x;
+  if (idx < nitems) issue(idx);
+  while (idx < nitems) {
+    const Stage1Item it = items[idx];
+    const BeamArgs a = pick<BATCH>(one, beams, it.pad0);
+    const int m = a.m;
+    const int TS = (m + 3) & ~3;                 // offset-table row stride (16-byte aligned quads)
+    const int c0 = it.s * m;
+    const int nkk = it.ke - it.kb;
+    const int32_t* d1kb = a.d1 + (size_t)it.kb * a.nchan + c0;
+    cp_async_wait_all();
+    __syncthreads();
+    // raw -> four-quarter words; lane g builds words 4g .. 4g + 3 of a channel
+    const int n4 = (Q + it.span + 15 + 3) >> 2;
+    for (int c = warp; c < m; c += kStage1Warps) {
+      const uint8_t* rw = raw + (size_t)c * RB;
+      uint32_t* srow = S + (size_t)c * SW;
+      for (int g = lane; g < n4; g += 32) {
+        const int j = g << 2;
+        uint32_t r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = *reinterpret_cast<const uint32_t*>(rw + j + q * Q);
+        // 4 x 4 byte transpose: word j+i collects byte i of each quarter
+        const uint32_t t0 = __byte_perm(r[0], r[1], 0x5140), t1 = __byte_perm(r[0], r[1], 0x7362);
+        const uint32_t t2 = __byte_perm(r[2], r[3], 0x5140), t3 = __byte_perm(r[2], r[3], 0x7362);
+        uint4 w;
+        w.x = __byte_perm(t0, t2, 0x5410);
+        w.y = __byte_perm(t0, t2, 0x7632);
+        w.z = __byte_perm(t1, t3, 0x5410);
+        w.w = __byte_perm(t1, t3, 0x7632);
+        *reinterpret_cast<uint4*>(srow + j) = w;
+      }
+    }
+    // word offset of S[c][a_c + d1[k][c] - d1[kb][c]] for every (k, c)
+    for (int kk = warp; kk < nkk; kk += kStage1Warps) {
+      const int32_t* d1k = a.d1 + (size_t)(it.kb + kk) * a.nchan + c0;
+      for (int c = lane; c < m; c += 32)
+        tab[kk * TS + c] = (uint32_t)(c * SW + (wstart(a, it, c) & 15) + d1k[c] - d1kb[c]);
+    }
+    __syncthreads();
+    const int next = idx + gridDim.x;
+    if (next < nitems) issue(next);
+
+    // tasks: (coarse DM, part of the tile); split the tile when coarse DMs are few
+    int split = 1;
+    while (split < V && nkk * split * 2 <= kStage1Warps) split *= 2;
+    for (int task = warp; task < nkk * split; task += kStage1Warps) {
+      const int kk = task / split, part = task - kk * split;
+      const int k = it.kb + kk;
+      const int64_t ab = a.abase[(size_t)k * a.nsub + it.s];
+      if ((int64_t)it.tau0 + 4 * Q <= ab || (int64_t)it.tau0 >= ab + a.Pp) continue;
+      PT* prow = static_cast<PT*>(a.P) + ((size_t)k * a.nsub + it.s) * a.Pp;
+      const int rel0 = (int)((int64_t)it.tau0 - ab);  // |rel0| < 2^30
+      const uint32_t* t = tab + kk * TS;
+      if (split == 1) {
+        stage1_sum<Q, V, PT>(S, t, m, unit, lane, 0, prow, rel0, a.Pp);
+      } else if (split == 2) {
+        if constexpr (V >= 2) stage1_sum<Q, V / 2, PT>(S, t, m, unit, lane, part * (Q / 2), prow, rel0, a.Pp);
+      } else if (split == 4) {
+        if constexpr (V >= 4) stage1_sum<Q, V / 4, PT>(S, t, m, unit, lane, part * (Q / 4), prow, rel0, a.Pp);
+      } else {
+        if constexpr (V >= 8) stage1_sum<Q, V / 8, PT>(S, t, m, unit, lane, part * (Q / 8), prow, rel0, a.Pp);
+      }
+    }
+    __syncthreads();
+    idx = next;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage 2 (Sec. 2.3: de-disperse the sub-bands on the fine DM grid)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long& s2) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+}
+
+// Persistent blocks walk units (coarse group k, tile of 2 NW outputs) in
+// sub-band chunks; SPLIT warps share fine DM kG + g, each summing NW / SPLIT
+// words of the tile. A chunk's uint16 stage-1 rows are copied (cp.async,
+// double-buffered) into shared memory as 32-bit words of consecutive pairs
+// (even copy) and re-paired one element later (odd copy), so every delay,
+// even or odd, is a 32-bit load feeding two outputs. Sums use
+//   sum w = sum(lo) + 65536 * sum(hi) (mod 2^32), sum(hi) = sum(w >> 16),
+// exact because every stage-2 sum is below 2^32. Shared memory holds two
+// even-copy slots and one odd-copy slot of `slot` words (the largest
+// SC * SWW of the launch) and the address table.
+template <int NW, int MAXWARPS, int SPLIT, bool BATCH>
+__global__ void __launch_bounds__(MAXWARPS * 32, 1)
+k_stage2_u16(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* __restrict__ uoff,
+             const int32_t* __restrict__ umem, int nmem, int nunits, int slot) {
+  extern __shared__ __align__(16) uint32_t smem2[];
+  constexpr int VW = NW / 32 / SPLIT;                    // words per lane
+  uint32_t* Se = smem2;                                  // [2][slot]
+  uint32_t* So = Se + 2 * (size_t)slot;                  // [slot]
+  uint32_t* tab = So + (size_t)slot;                     // [kStage2MaxGroup][SC] word offsets from smem2
+  __shared__ long long st1[MAXWARPS];
+  __shared__ unsigned long long st2[MAXWARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int g = warp / SPLIT, part_i = warp - g * SPLIT;  // fine DM of the group, part of the tile
+  const int jbase = part_i * (NW / SPLIT);
+
+  auto locate = [&](int u, int& lu) -> BeamArgs {
+    if constexpr (BATCH) {
+      const int j = find_member(uoff, nmem, u);
+      lu = u - uoff[j];
+      return beams[umem[j]];
+    } else {
+      lu = u;
+      return one;
+    }
+  };
+  auto issue = [&](int u, int ch, int buf) {
+    int lu;
+    const BeamArgs a = locate(u, lu);
+    const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
+    const int64_t t0 = (int64_t)tile * 2 * NW;
+    const int s0 = ch * a.SC, ns = min(a.SC, a.nsub - s0);
+    const int nq = a.SWW >> 2;
+    const uint16_t* P = static_cast<const uint16_t*>(a.P);
+    uint32_t* dst = Se + (size_t)buf * slot;
+    for (int ss = warp; ss < ns; ss += nwarps) {
+      const int s = s0 + ss;
+      const int64_t b = (t0 + a.e2[(size_t)k * a.G * a.nsub + s]) & ~(int64_t)7;
+      const uint16_t* src = P + ((size_t)k * a.nsub + s) * a.Pp + b;
+      uint32_t* d = dst + (size_t)ss * a.SWW;
+      for (int q = lane; q < nq; q += 32) cp_async16(d + 4 * q, src + 8 * q);
+    }
+    cp_async_commit();
+  };
+
+  uint32_t aw[VW], ah[VW];
+#pragma unroll
+  for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+  int u = blockIdx.x, ch = 0, buf = 0;
+  if (u < nunits) issue(u, 0, 0);
+  while (u < nunits) {
+    int lu;
+    const BeamArgs a = locate(u, lu);
+    const int SC = a.SC, SWW = a.SWW, nsub = a.nsub;
+    const int nchunk = (nsub + SC - 1) / SC;
+    const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
+    const int64_t t0 = (int64_t)tile * 2 * NW;
+    const int dfirst = k * a.G;
+    const int nd = min(a.G, a.ndm - dfirst);
+    const int s0 = ch * SC, ns = min(SC, nsub - s0);
+    uint32_t* cur = Se + (size_t)buf * slot;
+    cp_async_wait_all();
+    __syncthreads();
+    // odd copy: So[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged base
+    for (int ss = warp; ss < ns; ss += nwarps) {
+      const uint32_t* r = cur + (size_t)ss * SWW;
+      uint32_t* o = So + (size_t)ss * SWW;
+      for (int j = 4 * lane; j < SWW - 4; j += 128) {
+        const uint4 x = *reinterpret_cast<const uint4*>(r + j);
+        const uint32_t y = r[j + 4];
+        *reinterpret_cast<uint4*>(o + j) =
+            make_uint4(__funnelshift_r(x.x, x.y, 16), __funnelshift_r(x.y, x.z, 16), __funnelshift_r(x.z, x.w, 16),
+                       __funnelshift_r(x.w, y, 16));
+      }
+    }
+    for (int gg = warp; gg < nd; gg += nwarps) {
+      for (int ss = lane; ss < ns; ss += 32) {
+        const int s = s0 + ss;
+        const int32_t emin = a.e2[(size_t)dfirst * nsub + s];
+        const int off = a.e2[(size_t)(dfirst + gg) * nsub + s] - emin + (int)((t0 + emin) & 7);
+        const uint32_t* base = (off & 1) ? So : cur;
+        tab[gg * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
+      }
+    }
+    __syncthreads();
+    int nu = u, nch = ch + 1;
+    if (nch == nchunk) { nu = u + gridDim.x; nch = 0; }
+    if (nu < nunits) issue(nu, nch, buf ^ 1);
+
+    if (g < nd) {
+      const uint32_t* t = tab + g * SC;
+      const uint32_t* Sl = smem2 + jbase + lane;
+      int ss = 0;
+#pragma unroll 2
+      for (; ss + 1 < ns; ss += 2) {
+        const uint32_t* r0 = Sl + t[ss];
+        const uint32_t* r1 = Sl + t[ss + 1];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+          aw[v] += w0 + w1;
+          madd_hi16(ah[v], w0);
+          madd_hi16(ah[v], w1);
+        }
+      }
+      if (ss < ns) {
+        const uint32_t* r0 = Sl + t[ss];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const uint32_t w0 = r0[32 * v];
+          aw[v] += w0;
+          madd_hi16(ah[v], w0);
+        }
+      }
+    }
+    if (ch == nchunk - 1) {
+      long long s1 = 0;
+      unsigned long long s2 = 0;
+      if (g < nd) {
+        const int d = dfirst + g;
+        int32_t* drow = a.D + (size_t)d * a.Dp;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const int64_t ta = t0 + 2 * (jbase + lane + 32 * v);
+          const uint32_t lo = aw[v] - (ah[v] << 16), hi = ah[v];
+          if (ta + 1 < a.Td && (a.Dp & 1) == 0) {
+            *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
+          } else {
+            if (ta < a.Td) drow[ta] = (int32_t)lo;
+            if (ta + 1 < a.Td) drow[ta + 1] = (int32_t)hi;
+          }
+          if (ta < a.T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
+          if (ta + 1 < a.T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+      warp_sum_stats(s1, s2);
+      if (SPLIT == 1) {
+        if (g < nd && lane == 0) a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(s1, (long long)s2);
+      } else {
+        // combine the parts of each fine DM in a fixed order (deterministic sums)
+        if (lane == 0) { st1[warp] = s1; st2[warp] = s2; }
+        __syncthreads();
+        if (part_i == 0 && g < nd && lane == 0) {
+          long long x = 0;
+          unsigned long long y = 0;
+          for (int i = 0; i < SPLIT; ++i) { x += st1[warp + i]; y += st2[warp + i]; }
+          a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(x, (long long)y);
+        }
+      }
+    }
+    u = nu;
+    ch = nch;
+    buf ^= 1;
+  }
+}
+
+// Stage 2 from int32 intermediates (plain layout, one output per load); one
+// block per (tile of 2 NW outputs, coarse group), sub-band chunks in turn.
+template <int NW>
+__global__ void __launch_bounds__(kStage2MaxGroup * 32)
+k_stage2_i32(const int32_t* __restrict__ P, int64_t Pp, const int32_t* __restrict__ e2, int ndm, int nsub,
+             int G, int SC, int SW, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
+             longlong2* __restrict__ part, int ntile) {
+  extern __shared__ __align__(16) uint32_t smem3[];
+  constexpr int V = 2 * NW / 32;
+  const int tile = blockIdx.x, k = blockIdx.y;
+  const int64_t t0 = (int64_t)tile * 2 * NW;
+  const int dfirst = k * G;
+  const int nd = min(G, ndm - dfirst);
+  int32_t* S = reinterpret_cast<int32_t*>(smem3);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0;
+  for (int sb = 0; sb < nsub; sb += SC) {
+    const int ns = min(SC, nsub - sb);
+    for (int i = threadIdx.x; i < ns * SW; i += blockDim.x) {
+      const int ss = i / SW, j = i - ss * SW;
+      const int s = sb + ss;
+      S[(size_t)ss * SW + j] = __ldg(P + ((size_t)k * nsub + s) * Pp + t0 + e2[(size_t)dfirst * nsub + s] + j);
+    }
+    __syncthreads();
+    if (warp < nd) {
+      for (int ss = 0; ss < ns; ++ss) {
+        const int s = sb + ss;
+        const int o = e2[(size_t)(dfirst + warp) * nsub + s] - e2[(size_t)dfirst * nsub + s];
+        const int32_t* rw = S + (size_t)ss * SW + o + lane;
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += rw[32 * v];
+      }
+    }
+    __syncthreads();
+  }
+  if (warp < nd) {
+    const int d = dfirst + warp;
+    int32_t* drow = D + (size_t)d * Dp;
+    long long s1 = 0;
+    unsigned long long s2 = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int64_t t = t0 + lane + 32 * v;
+      if (t < Td) drow[t] = acc[v];
+      if (t < T) { s1 += acc[v]; s2 += (unsigned long long)((long long)acc[v] * acc[v]); }
+    }
+    warp_sum_stats(s1, s2);
+    if (lane == 0) part[(size_t)d * ntile + tile] = make_longlong2(s1, (long long)s2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// statistics (Eq. 5's sigma: the standard deviation of the noise)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
+  const unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;
+  return __dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), (double)lo);
+}
+
+// One thread per fine DM. mu = S1 / T, var = (T S2 - S1^2) / T^2 with an exact
+// 128-bit numerator; the running mode updates (mu, var) <- (1 - l) prev + l new.
+// Then, per width W: hi + lo = W mu (hi integer) and inv = 1 / (sigma sqrt W).
+// In a batch the thread of a candidate-mode beam's first DM also zeroes that
+// beam's candidate counter (the boxcar launch comes after this one).
+template <bool BATCH>
+__global__ void k_stats(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* __restrict__ uoff,
+                        const int32_t* __restrict__ umem, int nmem, int nunits) {
+  const int gd = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gd >= nunits) return;
+  int d;
+  BeamArgs a;
+  if constexpr (BATCH) {
+    const int j = find_member(uoff, nmem, gd);
+    d = gd - uoff[j];
+    a = beams[umem[j]];
+    if (d == 0 && a.output == TX_OUT_CANDS) *a.ncand = 0ull;
+  } else {
+    d = gd;
+    a = one;
+  }
+  const int64_t T = a.T;
+  unsigned long long s1 = 0, s2 = 0;
+  for (int i = 0; i < a.ntile2; ++i) {
+    const longlong2 v = a.part[(size_t)d * a.ntile2 + i];
+    s1 += (unsigned long long)v.x;
+    s2 += (unsigned long long)v.y;
+  }
+  double mu = __ddiv_rn((double)s1, (double)T);
+  const unsigned __int128 num = (unsigned __int128)(unsigned long long)T * s2 - (unsigned __int128)s1 * s1;
+  double var = __ddiv_rn(u128_to_double(num), __dmul_rn((double)T, (double)T));
+  if (a.running) {
+    double* r = a.run + (size_t)d * 2;
+    const double lam = a.lam;
+    if (r[1] < 0.0) {  // never initialised (reset writes -1)
+      r[0] = mu;
+      r[1] = var;
+    } else {
+      mu = __dadd_rn(__dmul_rn(1.0 - lam, r[0]), __dmul_rn(lam, mu));
+      var = __dadd_rn(__dmul_rn(1.0 - lam, r[1]), __dmul_rn(lam, var));
+      r[0] = mu;
+      r[1] = var;
+    }
+  }
+  const double sigma = sqrt(var);
+  const double gamma = a.gamma;
+  for (int w = 0; w < a.nw; ++w) {
+    const double W = (double)a.widths[w];
+    const double cw = __dmul_rn(W, mu);
+    const double hi = rint(cw);
+    SnrConst c;
+    c.hi = (int32_t)hi;
+    c.lo = (float)__dsub_rn(cw, hi);
+    c.inv = sigma > 0.0 ? (float)__ddiv_rn(1.0, __dmul_rn(sigma, sqrt(W))) : 0.f;
+    if (sigma > 0.0) {
+      // smallest integer window sum whose S/N reaches gamma
+      const double t = ceil(__dadd_rn(cw, __dmul_rn(gamma, __dmul_rn(sigma, sqrt(W)))));
+      c.thr = t > 2147483647.0 ? INT32_MAX : t < -2147483647.0 ? -INT32_MAX : (int32_t)t;
+    } else {
+      c.thr = gamma <= 0.0 ? -INT32_MAX : INT32_MAX;  // S/N is 0 everywhere
+    }
+    a.cst[(size_t)d * a.nw + w] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// boxcar matched filter (Eq. 5 via prefix sums, Sec. 2.4) and outputs (Sec. 2.5)
+// ---------------------------------------------------------------------------
+// Persistent blocks walk contiguous runs of units (fine DM d, tile of
+// kBoxTile outputs; in a batch, the units of all member beams in turn); each
+// unit's series (with its W_max - 1 look-ahead) is copied into shared memory
+// with cp.async while the previous unit is being filtered, then turned in
+// place into the prefix sum P (P[0] = 0), and each output t takes
+// B_W = P[t + W] - P[t] for every width.
+//   CUBE / PLANE: S/N for every width (float), best width for the plane.
+//   CANDS: a point is a candidate when B_W >= thr_W for some width, an exact
+//   integer form of S/N >= gamma; float S/N and the best width are computed
+//   for those points only.
+// NWT > 0: exactly NWT widths, per-width constants in registers.
+// NWT = 0: any count up to kMaxWidths, constants in shared memory.
+// The two shared buffers are sized for wmaxL (the largest W_max of the launch).
+template <int NWT, int MODE, bool BATCH>
+__global__ void __launch_bounds__(kBoxThreads)
+k_boxcar(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* __restrict__ uoff,
+         const int32_t* __restrict__ umem, int nmem, int nunits, int wmaxL) {
+  constexpr int NR = NWT > 0 ? NWT : 1;
+  extern __shared__ __align__(16) uint32_t smb[];
+  __shared__ uint32_t wsum[kBoxThreads / 32];
+  __shared__ int32_t sW[kMaxWidths];
+  __shared__ SnrConst sC[kMaxWidths];
+  const int bufw = (kBoxTile + wmaxL + 8 + 3) & ~3;  // words per buffer: 4 pad + series + chunk rounding
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int u_begin = (int)((int64_t)nunits * blockIdx.x / gridDim.x);
+  const int u_end = (int)((int64_t)nunits * (blockIdx.x + 1) / gridDim.x);
+
+  auto locate = [&](int u, int& lu, int& j) -> BeamArgs {
+    if constexpr (BATCH) {
+      j = find_member(uoff, nmem, u);
+      lu = u - uoff[j];
+      return beams[umem[j]];
+    } else {
+      j = 0;
+      lu = u;
+      return one;
+    }
+  };
+  auto issue = [&](int u, int buf) {
+    int lu, j;
+    const BeamArgs a = locate(u, lu, j);
+    const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
+    const int64_t t0 = (int64_t)tile * kBoxTile;
+    const int n = (int)min((int64_t)kBoxTile, a.T - t0);
+    const int nq = (n + a.wmax - 1 + 3) >> 2;  // 16-byte chunks of the series window
+    const int32_t* src = a.D + (size_t)d * a.Dp + t0;
+    uint32_t* dst = smb + (size_t)buf * bufw + 4;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(dst + 4 * q, src + 4 * q);
+    cp_async_commit();
+  };
+
+  int32_t Wr[NR], thr[NR];
+  int cur_d = -1, cur_j = -1;
+  if (u_begin < u_end) issue(u_begin, 0);
+  for (int u = u_begin, it = 0; u < u_end; ++u, ++it) {
+    const int buf = it & 1;
+    int lu, j;
+    const BeamArgs a = locate(u, lu, j);
+    const int nw = NWT > 0 ? NWT : a.nw;
+    const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
+    const int64_t T = a.T;
+    const int64_t t0 = (int64_t)tile * kBoxTile;
+    const int n = (int)min((int64_t)kBoxTile, T - t0);
+    const int N = n + a.wmax - 1;
+    const SnrConst* cst = a.cst + (size_t)d * nw;
+    uint32_t* C = smb + (size_t)buf * bufw + 3;  // C[0] = P[0] = 0, C[1 + j] = D[j] -> P[1 + j]
+    const bool fresh = d != cur_d || j != cur_j;
+    if (NWT > 0 && fresh) {
+#pragma unroll
+      for (int w = 0; w < NR; ++w) {
+        Wr[w] = __ldg(a.widths + w);
+        thr[w] = cst[w].thr;
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();  // this unit's series landed; the previous unit is done with sW/sC and the other buffer
+    if (NWT == 0 && fresh && threadIdx.x < nw) {
+      sW[threadIdx.x] = a.widths[threadIdx.x];
+      sC[threadIdx.x] = cst[threadIdx.x];
+    }
+    cur_d = d;
+    cur_j = j;
+    if (threadIdx.x == 0) C[0] = 0u;
+    if (u + 1 < u_end) issue(u + 1, buf ^ 1);
+    // inclusive scan of C[1..N] (uint32, wrap-around is harmless: window sums < 2^31)
+    const int E = (N + blockDim.x - 1) / blockDim.x;
+    const int beg = 1 + threadIdx.x * E, end = min(beg + E, N + 1);
+    uint32_t local = 0;
+    for (int i = beg; i < end; ++i) local += C[i];
+    uint32_t x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t pre = x - local;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    for (int i = beg; i < end; ++i) {
+      pre += C[i];
+      C[i] = pre;
+    }
+    __syncthreads();
+
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t* Ci = C + i;
+      const uint32_t cl = Ci[0];
+      float best = -INFINITY;
+      int bw = 0;
+      bool hit = false;
+      if (NWT > 0) {
+        if (MODE == TX_OUT_CANDS) {
+          int32_t mx = INT32_MIN;
+#pragma unroll
+          for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
+          hit = mx >= 0;
+          if (hit) {  // rare: float S/N and the best width of a candidate
+            for (int w = 0; w < NR; ++w) {
+              const SnrConst c = cst[w];
+              const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+              if (sv > best) { best = sv; bw = w; }
+            }
+          }
+        } else {
+          float sv[NR];
+#pragma unroll
+          for (int w = 0; w < NR; ++w) {
+            const SnrConst c = cst[w];
+            sv[w] = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+          }
+          if (MODE == TX_OUT_CUBE) {
+#pragma unroll
+            for (int w = 0; w < NR; ++w) a.outf[((size_t)d * nw + w) * T + t0 + i] = sv[w];
+          } else {
+#pragma unroll
+            for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
+            bw = NR - 1;
+#pragma unroll
+            for (int w = NR - 1; w >= 0; --w)
+              if (sv[w] == best) bw = w;
+          }
+        }
+      } else {
+        for (int w = 0; w < nw; ++w) {
+          const int32_t B = (int32_t)(Ci[sW[w]] - cl);
+          const float snr = ((float)(B - sC[w].hi) - sC[w].lo) * sC[w].inv;
+          if (MODE == TX_OUT_CUBE) a.outf[((size_t)d * nw + w) * T + t0 + i] = snr;
+          if (snr > best) { best = snr; bw = w; }
+          hit = hit || B >= sC[w].thr;
+        }
+      }
+      if (MODE == TX_OUT_PLANE) {
+        a.outf[(size_t)d * T + t0 + i] = best;
+        a.outw[(size_t)d * T + t0 + i] = (uint8_t)bw;
+      } else if (MODE == TX_OUT_CANDS) {
+        const unsigned act = __activemask();
+        const unsigned hits = __ballot_sync(act, hit);
+        if (hits) {
+          const int leader = __ffs(hits) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+          base = __shfl_sync(act, base, leader);
+          if (hit) {
+            const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+            if (idx < (unsigned long long)a.max_cands) {
+              tx_cand r;
+              r.dm_index = d;
+              r.t = (int32_t)(t0 + i);
+              r.w_index = bw;
+              r.snr = best;
+              a.cands[idx] = r;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+using BoxKernel = void (*)(const BeamArgs, const BeamArgs*, const int32_t*, const int32_t*, int, int, int);
+
+// Exact width counts 1..12 and 16 get their own instantiation; others use
+// the generic one (NWT = 0).
+template <int MODE, bool BATCH>
+BoxKernel box_kernel_m(int nw) {
+  switch (nw) {
+#define TX_BOX(N) \
+  case N: return k_boxcar<N, MODE, BATCH>;
+    TX_BOX(1) TX_BOX(2) TX_BOX(3) TX_BOX(4) TX_BOX(5) TX_BOX(6) TX_BOX(7) TX_BOX(8) TX_BOX(9) TX_BOX(10)
+    TX_BOX(11) TX_BOX(12) TX_BOX(16)
+#undef TX_BOX
+    default: return k_boxcar<0, MODE, BATCH>;
+  }
+}
+
+template <bool BATCH>
+BoxKernel box_kernel(int nw, int mode) {
+  return mode == TX_OUT_CANDS ? box_kernel_m<TX_OUT_CANDS, BATCH>(nw)
+         : mode == TX_OUT_PLANE ? box_kernel_m<TX_OUT_PLANE, BATCH>(nw) : box_kernel_m<TX_OUT_CUBE, BATCH>(nw);
+}
+
+// Instantiation class of a width count: the exact-count kernels, or 0 (generic).
+inline int box_class(int nw) { return (nw >= 1 && nw <= 12) || nw == 16 ? nw : 0; }
+
+__global__ void k_fill_run(double* run, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) run[2 * i + 1] = -1.0;  // marks "not initialised"
+}
+
+// ---------------------------------------------------------------------------
+// host helpers shared by the single-beam and batched launchers
+// ---------------------------------------------------------------------------
+// Raises kernel k's dynamic shared memory limit on the current device to at
+// least `bytes`, never lowering it: plans of different shapes share kernels,
+// and the limit one plan needs must survive another plan's set-up.
+inline cudaError_t raise_smem_limit(const void* k, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> lim;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_pair(dev, k);
+  const auto it = lim.find(key);
+  const int cur = it == lim.end() ? 48 * 1024 : it->second;  // the default limit
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) lim[key] = bytes;
+  return e;
+}
+
+// two buffers of (4 pad words + tile + look-ahead, rounded to 16-byte chunks)
+inline int box_smem_for(int wmax) { return 2 * ((kBoxTile + wmax + 8 + 3) & ~3) * 4; }
+
+// uint16 stage 2: two even-copy slots, one odd-copy slot, address table
+inline int stage2_u16_smem_for(int slot, int sc) { return (3 * slot + kStage2MaxGroup * sc) * 4; }
+
+// Warps per fine DM for the uint16 stage 2: enough to fill 32 warps.
+inline int stage2_split(const tx_plan* p) {
+  if (p->nw2 != 512) return 1;
+  return p->group <= 4 ? 8 : p->group <= 8 ? 4 : p->group <= 16 ? 2 : 1;
+}
+
+inline int stage2_threads(const tx_plan* p) { return std::min(p->group, kStage2MaxGroup) * 32 * stage2_split(p); }
+
+// The arguments of one execute of plan p on beam b: the block lands at ring
+// position `head`, buffer time 0 sits at `start`; ws is the execute's
+// workspace; out / ncand as tx_execute.
+inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* block, void* out, int64_t* ncand,
+                          void* ws_ptr, int64_t head, int64_t start) {
+  uint8_t* ws = static_cast<uint8_t*>(ws_ptr);
+  const bool series = p->output == TX_OUT_SERIES;
+  BeamArgs a{};
+  a.block = block;
+  a.ring = b->ring;
+  a.P = ws + p->ws_P;
+  a.D = series ? static_cast<int32_t*>(out) : reinterpret_cast<int32_t*>(ws + p->ws_D);
+  a.part = reinterpret_cast<longlong2*>(ws + p->ws_part);
+  a.cst = reinterpret_cast<SnrConst*>(ws + p->ws_const);
+  a.run = b->run;
+  a.d1 = p->dev.d1;
+  a.abase = p->dev.abase;
+  a.e2 = p->dev.e2;
+  a.widths = p->dev.widths;
+  a.outf = static_cast<float*>(out);
+  a.outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(out) + (size_t)p->ndm * p->T * 4 : nullptr;
+  a.cands = static_cast<tx_cand*>(out);
+  a.ncand = reinterpret_cast<unsigned long long*>(ncand);
+  a.R = p->R;
+  a.head = head;
+  a.start = start;
+  a.T = p->T;
+  a.Pp = p->Pp;
+  a.Dp = series ? p->Td : p->Dp;
+  a.Td = p->Td;
+  a.max_cands = p->max_cands;
+  a.lam = p->lambda;
+  a.gamma = (double)p->gamma;
+  a.nchan = p->nchan;
+  a.m = p->m;
+  a.nsub = p->nsub;
+  a.ndm = p->ndm;
+  a.G = p->group;
+  a.nk = p->nk;
+  a.SC = p->nsub_chunk2;
+  a.SWW = p->sww2;
+  a.ntile2 = p->ntile2;
+  a.ntile3 = p->ntile3;
+  a.nw = p->nw;
+  a.wmax = p->wmax;
+  a.layout = p->layout;
+  const bool al = ((uintptr_t)block & 15) == 0 && head % 16 == 0;
+  a.ingest_vec = p->layout == TX_LAYOUT_TF ? (al && p->nchan % 16 == 0) : (al && p->T % 16 == 0);
+  a.running = p->stats == TX_STATS_RUNNING;
+  a.output = p->output;
+  return a;
+}
+
+}  // namespace

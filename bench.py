@@ -54,7 +54,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS), default="meerkat_l")
+    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched"], default="meerkat_l")
+    ap.add_argument("--beams", type=int, default=64, help="batched: number of beams")
+    ap.add_argument("--ws-budget-gb", type=float, default=96.0, help="batched: workspace budget (GiB) for waves")
+    ap.add_argument("--plain-steps", type=int, default=3, help="batched: steps of the one-beam-at-a-time loop")
+    ap.add_argument("--batch-max-cands", type=int, default=1 << 22)
+    ap.add_argument("--tune", action="store_true", help="batched: autotune shapes missing from the cache first")
     ap.add_argument("--output", choices=["cands", "plane", "cube"], default="cands")
     ap.add_argument("--layout", choices=["tf", "ft"], default="tf")
     ap.add_argument("--interm", choices=["u16", "i32"], default="u16")
@@ -283,6 +288,8 @@ def run_reference(args):
 
 
 def load_workload(args):
+    if args.workload == "batched":
+        return synth.batched_workloads(args.beams)[0]
     wl = synth.WORKLOADS[args.workload]()
     if args.nsamp:
         wl.nsamp = int(args.nsamp)
@@ -479,10 +486,283 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------
+# batched arm: many uneven beams per step
+# ----------------------------------------------------------------------------
+def init_dist():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, torch.device("cuda", torch.cuda.current_device())
+
+
+def phase_roofline(name, ms_per_step, work_units, peaks):
+    """Roofline entry of one phase: achieved vs peak for its bound."""
+    bound = "alu" if name in ("stage1", "stage2") else "hbm"
+    entry = {"ms_per_step": ms_per_step, "bound": bound}
+    if ms_per_step <= 0:
+        return entry
+    if bound == "hbm":
+        ach = work_units / (ms_per_step / 1e3) / 1e9
+        entry.update({"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                      "algorithmic": work_units})
+    else:
+        pk = alu_peak(name, SM_MAX_MHZ_NOMINAL) / 1e12
+        ach = work_units / (ms_per_step / 1e3) / 1e12
+        entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": work_units})
+    return entry
+
+
+def run_batched(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, dev = init_dist()
+    from paper_2401_13834_gb300 import autotune
+    from paper_2401_13834_gb300 import build as _build
+    _build.build()
+    import paper_2401_13834_gb300 as tx
+
+    wls = synth.batched_workloads(args.beams)
+    if args.tune and rank == 0:
+        autotune.tune_all(wls, args.layout, args.output, args.interm, verbose=True, snr_threshold=args.gamma)
+    if world > 1:
+        dist.barrier()
+    plans, tuned = [], 0
+    for wl in wls:
+        ch = autotune.lookup(wl, args.layout, args.output, args.interm)
+        tuned += ch is not None
+        kw = ch or dict(nsub=wl.nsub, group=0, tile_q1=0, tile_split2=0)
+        plans.append(tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, kw["nsub"], wl.widths, wl.nsamp, group=kw["group"],
+                             layout=args.layout, interm=args.interm, output=args.output, snr_threshold=args.gamma,
+                             max_cands=args.batch_max_cands, tile_q1=kw["tile_q1"], tile_split2=kw["tile_split2"]))
+    beams, blocks = [], []
+    host0 = None
+    for i, (wl, p) in enumerate(zip(wls, plans)):
+        x = synth.device_spectrum(wl, p.overlap + p.nsamp, synth.batched_pulses(wl, seed=100 + i),
+                                  seed=1000 * rank + i, device=dev)
+        if i == 0 and rank == 0 and not args.no_cpu_baseline:
+            host0 = x.cpu().numpy()
+        tail, blk = x[:, :p.overlap], x[:, p.overlap:]
+        if args.layout == "tf":
+            tail, blk = tail.t().contiguous(), blk.t().contiguous()
+        else:
+            tail, blk = tail.contiguous(), blk.contiguous()
+        b = tx.Beam(p)
+        b.prime(tail)
+        beams.append(b)
+        blocks.append(blk)
+        del x, tail
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    budget = int(args.ws_budget_gb * 2 ** 30)
+    batch = tx.Batch(plans, beams, workspace_budget=budget, graph=True)
+    ws = batch.alloc_workspace(dev)
+    outs = batch.alloc_outs(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        batch.execute(blocks, outs, ws)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = None
+    for attempt in range(2):
+        sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        if sampler:
+            sampler.start()
+        barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
+            batch.execute(blocks, outs, ws)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        elapsed_ms = evs[0].elapsed_time(evs[-1])
+        step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        if sampler:
+            clocks = sampler.stop()
+        bad = clocks and any(r in clocks["reasons"] for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"))
+        if not bad:
+            break
+    ncands = [int(nc.item()) if nc is not None else 0 for _, nc in outs]
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
+    units = batch.dm_trial_samples
+    value = aggregate_throughput(units, args.steps, world, elapsed_ms / 1e3)
+
+    # ---- per-phase times from a profiling batch (direct launches) -------------
+    pbatch = tx.Batch(plans, beams, workspace_budget=budget, graph=False, profile=True)
+    for _ in range(3):
+        pbatch.execute(blocks, outs, ws)
+    phase_ms, pn = pbatch.read_profile()
+    del pbatch
+
+    # ---- end to end: pinned host blocks in, candidates out --------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = []
+        for blk in blocks:
+            h = torch.empty(blk.shape, dtype=torch.uint8, pin_memory=True)
+            h.copy_(blk)
+            pinned.append(h)
+        nsteps_e2e = max(1, min(args.e2e_steps, 5))
+        cap = max(p.max_cands for p in plans)
+        h_cands = torch.empty((cap, 4), dtype=torch.int32, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(nsteps_e2e):
+            for blk, h in zip(blocks, pinned):
+                blk.copy_(h, non_blocking=True)
+            batch.execute(blocks, outs, ws)
+            counts = torch.stack([nc for _, nc in outs if nc is not None]).cpu()
+            d2h += counts.numel() * 8
+            j = 0
+            for p, (o, nc) in zip(plans, outs):
+                if nc is None:
+                    continue
+                n = min(int(counts[j]), p.max_cands)
+                j += 1
+                if n:
+                    h_cands[:n].copy_(o[:n])
+                    d2h += n * 16
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": aggregate_throughput(units, nsteps_e2e, world, el), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(p.block_bytes for p in plans)),
+               "d2h_bytes_per_step": int(d2h / nsteps_e2e), "steps": nsteps_e2e,
+               "api": "Batch.execute with host blocks copied in from pinned memory and candidates copied out"}
+        del pinned
+
+    # ---- the same beams one at a time through tx_execute ---------------------
+    # (after the batch's own measurements; its workspace is released first)
+    del ws
+    torch.cuda.empty_cache()
+
+    def plain_loop(pl, bm):
+        wsp = torch.empty(max(p.workspace_bytes for p in pl), dtype=torch.uint8, device=dev)
+        for p, b, blk, (o, nc) in zip(pl, bm, blocks, outs):
+            tx.execute(p, b, blk, out=o, ncand=nc, workspace=wsp)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.plain_steps):
+            for p, b, blk, (o, nc) in zip(pl, bm, blocks, outs):
+                tx.execute(p, b, blk, out=o, ncand=nc, workspace=wsp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pel = max_over_ranks(e0.elapsed_time(e1), dev)
+        timer = tx.Timer(len(pl))  # phase times of the same loop (events between phases)
+        for p, b, blk, (o, nc) in zip(pl, bm, blocks, outs):
+            tx.execute_timed(p, b, blk, o, nc, wsp, timer)
+        pms, _, _ = timer.read()
+        del wsp
+        torch.cuda.empty_cache()
+        return {"value": aggregate_throughput(units, args.plain_steps, world, pel / 1e3),
+                "ms_per_step": pel / args.plain_steps, "steps": args.plain_steps, "phase_ms_per_step": pms}
+
+    plain = plain_i32 = None
+    if args.plain_steps > 0:
+        plain = plain_loop(plans, beams)
+        plain["what"] = "the same plans (uint16 intermediates), beams and blocks, one tx_execute per beam in turn"
+        # the integer reference path: int32 intermediates, same tiles and sub-bands
+        p32 = [tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, p.nsub, wl.widths, wl.nsamp, group=p.group,
+                       layout=args.layout, interm="i32", output=args.output, snr_threshold=args.gamma,
+                       max_cands=args.batch_max_cands, tile_q1=p.tile_q1) for wl, p in zip(wls, plans)]
+        b32 = []
+        for p, b in zip(p32, beams):
+            nb_ = tx.Beam(p)
+            b32.append(nb_)
+        plain_i32 = plain_loop(p32, b32)
+        plain_i32["what"] = ("int32 intermediates (the exact reference form of the method), same sub-bands, groups "
+                             "and blocks, one tx_execute per beam in turn")
+        del b32, p32
+        torch.cuda.empty_cache()
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        work = {k: 0 for k in ("ingest", "stage1", "stage2", "stats", "boxcar")}
+        for p, n in zip(plans, ncands):
+            for k, (_, amount) in algorithmic_work(p, n).items():
+                work[k] += amount
+        total = max(sum(phase_ms.values()), 1e-12)
+        phases = {}
+        for name, ms in phase_ms.items():
+            e = phase_roofline(name, ms / max(pn, 1), work[name], peaks)
+            e["share"] = ms / total
+            phases[name] = e
+        dom = max(phase_ms, key=phase_ms.get)
+        d = phases[dom]
+        roof = {"bound": d["bound"], "achieved": d.get("achieved"), "peak": d.get("peak"), "unit": d.get("unit"),
+                "frac": d.get("frac"), "traffic": None, "kernel": {"stage1": "k_stage1", "stage2": "k_stage2_u16",
+                                                                      "boxcar": "k_boxcar", "ingest": "k_ingest_batch",
+                                                                      "stats": "k_stats"}[dom],
+                "peak_source": (f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
+                                "derived: 152 SMs x shared-memory port 128 B/clk x 2.07 GHz, "
+                                f"{'1' if dom == 'stage1' else '2'} B per sample-add"),
+                "phase_times_from": f"{pn} steps of a TX_BATCH_PROFILE batch (direct launches, events per launch)"}
+        cpu = None
+        if host0 is not None and world == 1:
+            cpu = cpu_baseline(wls[0], host0, args.gamma, args.cpu_seconds)
+            cpu["sample"] = f"beam 0 ({wls[0].name}): " + cpu["sample"]
+        shapes = {}
+        for wl in wls:
+            k = f"{wl.nchan}ch-{wl.ndm}dm-T{wl.nsamp}"
+            shapes[k] = shapes.get(k, 0) + 1
+        data_s = sum(p.nsamp * wl.tsamp_s for p, wl in zip(plans, wls))
+        step = elapsed_ms / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8->int32 sums, f32 S/N", "data": "synthetic",
+            "config": {"workload": f"batched-{len(wls)}-beams", "beams": len(wls), "shapes": shapes,
+                       "band_mhz": [856.0, 1712.0], "tsamp_us": 153.12, "dm_max": 3000.0,
+                       "widths": [int(w) for w in wls[0].widths], "output": args.output, "layout": args.layout,
+                       "interm": args.interm, "snr_threshold": args.gamma, "autotuned_beams": tuned,
+                       "nsub_per_beam": [p.nsub for p in plans], "group_per_beam": [p.group for p in plans],
+                       "workspace_budget_gib": args.ws_budget_gb, "waves": batch.nwaves,
+                       "launches_per_step": batch.nlaunches, "graph": True,
+                       "l2": f"inputs larger than L2: {sum(p.block_bytes for p in plans) / 1e9:.1f} GB of blocks per step",
+                       "parallelism": f"replicas{world}"},
+            "beam_blocks_per_s": world * len(wls) * args.steps / (elapsed_ms / 1e3),
+            "p50_block_ms": float(np.percentile(step_ms, 50)), "p99_block_ms": float(np.percentile(step_ms, 99)),
+            "latency_note": "a beam's block completes within its batch step; latency percentiles are of the step",
+            "real_time_factor": min(p.nsamp * wl.tsamp_s for p, wl in zip(plans, wls)) / (step / 1e3),
+            "data_seconds_per_second": data_s / (step / 1e3),
+            "candidates_per_step": int(sum(ncands)),
+            "plain_loop": plain,
+            "speedup_vs_plain_loop": (value / plain["value"]) if plain else None,
+            "plain_loop_i32": plain_i32,
+            "speedup_vs_plain_i32": (value / plain_i32["value"]) if plain_i32 else None,
+            "roofline": roof, "phases": phases, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": batch.nlaunches * args.steps,
+            "paper_context": "TransientX de-dispersion runs in real time on one i7-10750H core for 4096 channels x "
+                             "4096 DM trials at 153 us (>= 2.68e7 DM-trial*samples/s); CPU, other hardware",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

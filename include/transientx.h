@@ -105,6 +105,14 @@ typedef struct tx_plan_desc {
   int64_t        max_cands;      /* capacity of the candidate buffer, >= 1          */
   int32_t        stats;          /* enum tx_stats                                   */
   double         stats_lambda;   /* weight of a new block in TX_STATS_RUNNING, (0,1]*/
+  /* Tile shapes (results do not depend on them; 0 = automatic choice):     */
+  int32_t        tile_q1;        /* stage-1 tile of 4 * tile_q1 samples: 32, 64, 128
+                                    or 256 (must fit shared memory); 0 = the
+                                    largest that fits                               */
+  int32_t        tile_split2;    /* stage-2 warps per fine DM: 1 (tiles of 512
+                                    outputs) or 2, 4, 8 (tiles of 1024), with
+                                    min(group, 32) * tile_split2 <= 32; 0 = 8, 4, 2
+                                    or 1 for groups of <= 4, 8, 16 or more        */
 } tx_plan_desc;
 
 typedef struct tx_plan_info {
@@ -121,6 +129,8 @@ typedef struct tx_plan_info {
   int64_t ring_len;         /* samples per channel of a beam's circular buffer (>= L + T);
                                a block that wraps its end is ingested in two launches */
   int64_t ring_head0;       /* where a fresh beam's first block lands in it        */
+  int32_t tile_q1;          /* the stage-1 tile chosen (see tx_plan_desc)           */
+  int32_t tile_split2;      /* the stage-2 warps per fine DM chosen                 */
 } tx_plan_info;
 
 /* One candidate of TX_OUT_CANDS: a DM-time plane point with S/N >= threshold. */
@@ -281,7 +291,11 @@ void tx_timer_destroy(tx_timer* timer);
    before it rewrites that step's buffer. Consecutive calls on one batch must
    go to the same stream. A beam in a batch must not be used by other calls
    while the batch is in use. */
-#define TX_BATCH_GRAPH 1
+#define TX_BATCH_GRAPH   1
+/* TX_BATCH_PROFILE (direct launches only): CUDA events around every launch;
+   each call first waits for the previous step's events and adds its launch
+   times to per-phase sums read by tx_batch_read_profile. */
+#define TX_BATCH_PROFILE 2
 
 typedef struct tx_batch tx_batch;
 
@@ -315,6 +329,11 @@ int32_t tx_batch_get_info(const tx_batch* batch, tx_batch_info* info);
    has finished (see above). */
 int32_t tx_execute_batch(tx_batch* batch, const uint8_t* const* d_blocks, void* const* d_outs,
                          int64_t* const* d_ncands, void* d_workspace, void* stream);
+
+/* TX_BATCH_PROFILE batches: waits for the last step, then writes the summed
+   milliseconds of each phase's launches over all steps to h_ms[TX_NPHASES]
+   (indexed by TX_PHASE_*) and the step count to *nsteps (may be NULL). */
+int32_t tx_batch_read_profile(tx_batch* batch, double* h_ms, int32_t* nsteps);
 
 /* Waits for the batch's steps in flight, then frees what it holds (not the
    plans or beams). */

@@ -32,7 +32,7 @@ class _Desc(C.Structure):
         ("nwidth", C.c_int32), ("widths", C.POINTER(C.c_int32)), ("nsamp", C.c_int64),
         ("layout", C.c_int32), ("interm", C.c_int32), ("output", C.c_int32),
         ("snr_threshold", C.c_float), ("max_cands", C.c_int64), ("stats", C.c_int32),
-        ("stats_lambda", C.c_double),
+        ("stats_lambda", C.c_double), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32),
     ]
 
 
@@ -43,7 +43,7 @@ class _Info(C.Structure):
         ("nsamp", C.c_int64), ("overlap", C.c_int64), ("max_delay", C.c_int64), ("series_len", C.c_int64),
         ("workspace_bytes", C.c_int64), ("beam_state_bytes", C.c_int64), ("out_bytes", C.c_int64),
         ("export_bytes", C.c_int64), ("block_bytes", C.c_int64), ("ring_len", C.c_int64),
-        ("ring_head0", C.c_int64),
+        ("ring_head0", C.c_int64), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32),
     ]
 
 
@@ -55,6 +55,7 @@ class _BatchInfo(C.Structure):
 
 
 TX_BATCH_GRAPH = 1
+TX_BATCH_PROFILE = 2
 
 
 def library_path() -> str:
@@ -95,6 +96,7 @@ def _load():
         "tx_batch_create": (I32, [I32, VP, VP, I64, I32, C.POINTER(P)]),
         "tx_batch_get_info": (I32, [P, C.POINTER(_BatchInfo)]),
         "tx_execute_batch": (I32, [P, VP, VP, VP, VP, VP]),
+        "tx_batch_read_profile": (I32, [P, VP, C.POINTER(I32)]),
         "tx_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -143,7 +145,8 @@ class Plan:
     """A de-dispersion + matched-filter plan (tables on the host until first use)."""
 
     def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group=0, layout="ft", interm="u16",
-                 output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25):
+                 output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25,
+                 tile_q1=0, tile_split2=0):
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
         self.dms = np.ascontiguousarray(dms, dtype=np.float64)
         self.widths = np.ascontiguousarray(widths, dtype=np.int32)
@@ -165,6 +168,8 @@ class Plan:
         d.max_cands = int(max_cands)
         d.stats = STATS[stats]
         d.stats_lambda = float(stats_lambda)
+        d.tile_q1 = int(tile_q1)
+        d.tile_split2 = int(tile_split2)
         self.layout, self.interm, self.output, self.stats = layout, interm, output, stats
         self.snr_threshold = float(snr_threshold)
         self.max_cands = int(max_cands)
@@ -367,17 +372,19 @@ class Batch:
 
     ``workspace_budget`` > 0 splits the beams into waves that share a workspace
     of at most that many bytes; ``graph`` replays the step's launches as CUDA
-    graphs. The plans and beams must outlive the batch.
+    graphs; ``profile`` (direct launches) times every launch for
+    ``read_profile``. The plans and beams must outlive the batch.
     """
 
-    def __init__(self, plans, beams, workspace_budget=0, graph=True):
+    def __init__(self, plans, beams, workspace_budget=0, graph=True, profile=False):
         assert len(plans) == len(beams) and len(plans) > 0
         self.plans, self.beams = list(plans), list(beams)
         n = len(plans)
         ph = (C.c_void_p * n)(*[p.handle.value for p in plans])
         bh = (C.c_void_p * n)(*[b.handle.value for b in beams])
         h = C.c_void_p()
-        _check(lib.tx_batch_create(n, ph, bh, int(workspace_budget), TX_BATCH_GRAPH if graph else 0, C.byref(h)))
+        flags = (TX_BATCH_GRAPH if graph else 0) | (TX_BATCH_PROFILE if profile else 0)
+        _check(lib.tx_batch_create(n, ph, bh, int(workspace_budget), flags, C.byref(h)))
         self._h = h
         inf = _BatchInfo()
         _check(lib.tx_batch_get_info(h, C.byref(inf)))
@@ -403,6 +410,13 @@ class Batch:
         op = (C.c_void_p * n)(*[o.data_ptr() for o, _ in outs])
         cp = (C.c_void_p * n)(*[0 if c is None else c.data_ptr() for _, c in outs])
         _check(lib.tx_execute_batch(self._h, bp, op, cp, _ptr(workspace), _stream_ptr(stream)))
+
+    def read_profile(self):
+        """(summed ms per phase over the profiled steps, step count)."""
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        n = C.c_int32()
+        _check(lib.tx_batch_read_profile(self._h, ms.ctypes.data_as(C.c_void_p), C.byref(n)))
+        return dict(zip(PHASES, ms.tolist())), int(n.value)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -1,18 +1,19 @@
 // Batched execute: one block of each of many beams of uneven shape (channel
 // counts, block lengths, DM grids, widths, output modes) per step, with each
 // phase of the hot path run as persistent launches over the concatenated work
-// of all beams instead of one launch sequence per beam (Sec. 2.3 blocked
+// of many beams instead of one launch sequence per beam (Sec. 2.3 blocked
 // processing, applied to many beams at once). A step's launches can be
 // captured once as a CUDA graph and replayed; what changes from step to step
-// (input and output pointers, ring positions) lives in a per-beam argument
-// array that the step copies to the device first.
+// (input and output pointers, ring positions) lives in per-beam arguments that
+// each wave of the step first copies into a constant-memory slot, where the
+// kernels read them as cheaply as the single-beam kernels read parameters.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
-#include <tuple>
 #include <vector>
 
 #include "kernels.cuh"
@@ -31,11 +32,36 @@ using namespace tx;
 
 namespace {
 
-enum LaunchKind { kIngest = 0, kStage1 = 1, kStage2 = 2, kStats = 3, kBoxcar = 4 };
+// Constant-memory argument slots: a batch holds one slot for its lifetime; a
+// wave has at most kArgSlotBeams beams.
+constexpr int kArgSlots = 2;
+constexpr int kArgSlotBeams = 96;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+static __constant__ BeamArgs c_args[kArgSlots * kArgSlotBeams];
+
+namespace {
+
+// Batched argument source: member i of a launch is c_args[base + i].
+struct SlotArgs {
+  static constexpr bool kBatch = true;
+  int base;
+  __device__ __forceinline__ BeamArgs get(int i) const { return c_args[base + i]; }
+};
+
+std::mutex g_slot_mu;
+bool g_slot_used[kMaxDevices][kArgSlots] = {};
+
+// A launch's kind is the phase it belongs to (TX_PHASE_* order).
+enum LaunchKind { kIngest = TX_PHASE_INGEST, kStage1 = TX_PHASE_STAGE1, kStage2 = TX_PHASE_STAGE2,
+                  kStats = TX_PHASE_STATS, kBoxcar = TX_PHASE_BOXCAR };
 
 // One persistent launch of a step over the units of its member beams.
 struct BatchLaunch {
   int kind = 0;
+  int wave = 0;
   int q1 = 0, split = 0, nwc = 0, mode = 0;  // template selectors
   int grid = 0, threads = 0, smem = 0;
   int nmem = 0, nunits = 0;                  // member beams, units (stage 1: work items)
@@ -49,22 +75,28 @@ int64_t mod64(int64_t a, int64_t r) { return ((a % r) + r) % r; }
 }  // namespace
 
 struct tx_batch {
-  int n = 0, device = -1, flags = 0, nwaves = 0, num_sms = 0;
+  int n = 0, device = -1, flags = 0, nwaves = 0, num_sms = 0, slot = -1;
   std::vector<const tx_plan*> plans;
   std::vector<tx_beam*> beams;
+  std::vector<int> wave_first;   // first beam of each wave, plus n
   std::vector<int64_t> ws_off;   // per beam, inside the shared workspace (waves reuse it)
   int64_t ws_bytes = 0;
   int64_t dm_samples = 0;
-  std::vector<BatchLaunch> launches;
-  BeamArgs* d_args = nullptr;    // [n]
+  std::vector<BatchLaunch> launches;  // wave by wave
+  BeamArgs* d_slot = nullptr;    // device address of the batch's constant-memory slot
   int32_t* d_tab = nullptr;      // unit offsets and member lists of every launch
-  Stage1Item* d_items = nullptr; // stage-1 work items of every stage-1 launch, pad0 = beam
+  Stage1Item* d_items = nullptr; // stage-1 work items of every stage-1 launch, pad0 = member
   BeamArgs* h_args[2] = {nullptr, nullptr};  // pinned, alternating between steps
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool used[2] = {false, false};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaStream_t cap = nullptr;    // private stream for graph capture
   int64_t nsteps = 0;
+  // TX_BATCH_PROFILE: an event before each launch and one after the last
+  std::vector<cudaEvent_t> prof_ev;
+  bool prof_pending = false;
+  double prof_ms[TX_NPHASES] = {0, 0, 0, 0, 0};
+  int32_t prof_steps = 0;
 };
 
 namespace {
@@ -72,52 +104,55 @@ namespace {
 // The kernel a batched launch runs.
 const void* launch_kernel(const BatchLaunch& L) {
   switch (L.kind) {
-    case kIngest: return (const void*)k_ingest_batch;
+    case kIngest: return (const void*)k_ingest_batch<SlotArgs>;
     case kStage1:
       switch (L.q1) {
-        case 256: return (const void*)k_stage1<256, uint16_t, true>;
-        case 128: return (const void*)k_stage1<128, uint16_t, true>;
-        case 64: return (const void*)k_stage1<64, uint16_t, true>;
-        default: return (const void*)k_stage1<32, uint16_t, true>;
+        case 256: return (const void*)k_stage1<256, uint16_t, SlotArgs>;
+        case 128: return (const void*)k_stage1<128, uint16_t, SlotArgs>;
+        case 64: return (const void*)k_stage1<64, uint16_t, SlotArgs>;
+        default: return (const void*)k_stage1<32, uint16_t, SlotArgs>;
       }
     case kStage2:
       switch (L.split) {
-        case 8: return (const void*)k_stage2_u16<512, 32, 8, true>;
-        case 4: return (const void*)k_stage2_u16<512, 32, 4, true>;
-        case 2: return (const void*)k_stage2_u16<512, 32, 2, true>;
-        default: return (const void*)k_stage2_u16<256, 32, 1, true>;
+        case 8: return (const void*)k_stage2_u16<512, 32, 8, SlotArgs>;
+        case 4: return (const void*)k_stage2_u16<512, 32, 4, SlotArgs>;
+        case 2: return (const void*)k_stage2_u16<512, 32, 2, SlotArgs>;
+        default: return (const void*)k_stage2_u16<256, 32, 1, SlotArgs>;
       }
-    case kStats: return (const void*)k_stats<true>;
-    default: return (const void*)box_kernel<true>(L.nwc, L.mode);
+    case kStats: return (const void*)k_stats<SlotArgs>;
+    default: return (const void*)box_kernel<SlotArgs>(L.nwc, L.mode);
   }
 }
 
 int build_batch(tx_batch* B, int64_t budget) {
   const int n = B->n;
-  // ---- waves under the workspace budget --------------------------------------
-  std::vector<int> wave(n, 0);
+  // ---- waves: consecutive beams within the workspace budget and a slot --------
   B->ws_off.assign(n, 0);
+  B->wave_first.assign(1, 0);
   int64_t cur = 0;
-  int w = 0;
   for (int i = 0; i < n; ++i) {
     const int64_t need = B->plans[i]->ws_bytes;
     if (budget > 0 && need > budget) {
       set_error("beam %d needs %lld workspace bytes, more than the budget %lld", i, (long long)need, (long long)budget);
       return TX_ERR_BUDGET;
     }
-    if (budget > 0 && cur + need > budget) { ++w; cur = 0; }
-    wave[i] = w;
+    const bool full = i - B->wave_first.back() == kArgSlotBeams;
+    if (i > 0 && (full || (budget > 0 && cur + need > budget))) {
+      B->wave_first.push_back(i);
+      cur = 0;
+    }
     B->ws_off[i] = cur;
     cur += need;
     B->ws_bytes = std::max(B->ws_bytes, cur);
     B->dm_samples += (int64_t)B->plans[i]->ndm * B->plans[i]->T;
   }
-  B->nwaves = w + 1;
+  B->wave_first.push_back(n);
+  B->nwaves = (int)B->wave_first.size() - 1;
 
   std::vector<int32_t> tab;
   std::vector<Stage1Item> items;
-  // unit offsets and member list of one launch
-  auto add_members = [&](BatchLaunch& L, const std::vector<int>& mem, auto units_of) -> int {
+  // unit offsets and member list (wave-local indices) of one launch
+  auto add_members = [&](BatchLaunch& L, const std::vector<int>& mem, int first, auto units_of) -> int {
     L.nmem = (int)mem.size();
     L.off = (int64_t)tab.size();
     int64_t total = 0;
@@ -128,40 +163,39 @@ int build_batch(tx_batch* B, int64_t budget) {
     tab.push_back((int32_t)total);
     if (total >= INT32_MAX) { set_error("a batched launch has too many work units (%lld)", (long long)total); return TX_ERR_UNSUPPORTED; }
     L.mem = (int64_t)tab.size();
-    for (int b : mem) tab.push_back(b);
+    for (int b : mem) tab.push_back(b - first);
     L.nunits = (int)total;
     return TX_OK;
   };
   const int nsm = std::max(B->num_sms, 1);
   int rc;
 
-  // ---- ingest: every beam, one launch ----------------------------------------
-  {
-    BatchLaunch L;
-    L.kind = kIngest;
-    std::vector<int> all(n);
-    for (int i = 0; i < n; ++i) all[i] = i;
-    rc = add_members(L, all, [&](int b) -> int64_t {
-      const tx_plan* p = B->plans[b];
-      return p->layout == TX_LAYOUT_TF ? ((p->T + 63) / 64) * ((p->nchan + 63) / 64)
-                                       : (int64_t)p->nchan * ((p->T + 4095) / 4096);
-    });
-    if (rc) return rc;
-    L.threads = 256;
-    L.grid = std::min(L.nunits, nsm * 8);
-    if (L.nunits > 0) B->launches.push_back(L);
-  }
-
   for (int wv = 0; wv < B->nwaves; ++wv) {
+    const int first = B->wave_first[wv];
     std::vector<int> mem;
-    for (int i = 0; i < n; ++i)
-      if (wave[i] == wv) mem.push_back(i);
+    for (int i = first; i < B->wave_first[wv + 1]; ++i) mem.push_back(i);
+    // ---- ingest: every beam of the wave ------------------------------------------
+    {
+      BatchLaunch L;
+      L.kind = kIngest;
+      L.wave = wv;
+      rc = add_members(L, mem, first, [&](int b) -> int64_t {
+        const tx_plan* p = B->plans[b];
+        return p->layout == TX_LAYOUT_TF ? ((p->T + 63) / 64) * ((p->nchan + 63) / 64)
+                                         : (int64_t)p->nchan * ((p->T + 4095) / 4096);
+      });
+      if (rc) return rc;
+      L.threads = 256;
+      L.grid = std::min(L.nunits, nsm * 8);
+      if (L.nunits > 0) B->launches.push_back(L);
+    }
     // ---- stage 1, one launch per tile length q1 ----------------------------------
     std::map<int, std::vector<int>> by_q;
     for (int b : mem) by_q[B->plans[b]->q1].push_back(b);
     for (auto& kv : by_q) {
       BatchLaunch L;
       L.kind = kStage1;
+      L.wave = wv;
       L.q1 = kv.first;
       L.items = (int64_t)items.size();
       int mL = 0;
@@ -169,7 +203,7 @@ int build_batch(tx_batch* B, int64_t budget) {
         const tx_plan* p = B->plans[b];
         mL = std::max(mL, p->m);
         for (Stage1Item it : p->items1) {
-          it.pad0 = b;
+          it.pad0 = b - first;
           items.push_back(it);
         }
       }
@@ -209,8 +243,10 @@ int build_batch(tx_batch* B, int64_t budget) {
     for (auto& kv : s2groups) {
       BatchLaunch L;
       L.kind = kStage2;
+      L.wave = wv;
       L.split = kv.first;
-      if ((rc = add_members(L, kv.second, [&](int b) -> int64_t { return (int64_t)B->plans[b]->nk * B->plans[b]->ntile2; })))
+      if ((rc = add_members(L, kv.second, first,
+                            [&](int b) -> int64_t { return (int64_t)B->plans[b]->nk * B->plans[b]->ntile2; })))
         return rc;
       int threads = 0;
       for (int b : kv.second) threads = std::max(threads, stage2_threads(B->plans[b]));
@@ -229,7 +265,8 @@ int build_batch(tx_batch* B, int64_t budget) {
     if (!filt.empty()) {
       BatchLaunch L;
       L.kind = kStats;
-      if ((rc = add_members(L, filt, [&](int b) -> int64_t { return B->plans[b]->ndm; }))) return rc;
+      L.wave = wv;
+      if ((rc = add_members(L, filt, first, [&](int b) -> int64_t { return B->plans[b]->ndm; }))) return rc;
       L.threads = 128;
       L.grid = (L.nunits + 127) / 128;
       B->launches.push_back(L);
@@ -239,16 +276,18 @@ int build_batch(tx_batch* B, int64_t budget) {
     for (auto& kv : by_box) {
       BatchLaunch L;
       L.kind = kBoxcar;
+      L.wave = wv;
       L.nwc = kv.first.first;
       L.mode = kv.first.second;
-      if ((rc = add_members(L, kv.second, [&](int b) -> int64_t { return (int64_t)B->plans[b]->ndm * B->plans[b]->ntile3; })))
+      if ((rc = add_members(L, kv.second, first,
+                            [&](int b) -> int64_t { return (int64_t)B->plans[b]->ndm * B->plans[b]->ntile3; })))
         return rc;
       int wm = 0;
       for (int b : kv.second) wm = std::max(wm, B->plans[b]->wmax);
       L.layout = wm;
       L.smem = box_smem_for(wm);
-      const BoxKernel k = box_kernel<true>(L.nwc, L.mode);
-      TX_CUDA(raise_smem_limit((const void*)k, L.smem));  // before the occupancy query
+      const void* k = launch_kernel(L);
+      TX_CUDA(raise_smem_limit(k, L.smem));  // before the occupancy query
       int bps = 1;
       TX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kBoxThreads, L.smem));
       L.threads = kBoxThreads;
@@ -263,11 +302,12 @@ int build_batch(tx_batch* B, int64_t budget) {
     const void* k = launch_kernel(L);
     need[k] = std::max(need[k], L.smem);
   }
-  for (auto& kv : need)
-    TX_CUDA(raise_smem_limit(kv.first, kv.second));
+  for (auto& kv : need) TX_CUDA(raise_smem_limit(kv.first, kv.second));
 
   // ---- device tables, pinned argument buffers ----------------------------------
-  TX_CUDA(cudaMalloc((void**)&B->d_args, (size_t)n * sizeof(BeamArgs)));
+  void* sym = nullptr;
+  TX_CUDA(cudaGetSymbolAddress(&sym, c_args));
+  B->d_slot = static_cast<BeamArgs*>(sym) + (size_t)B->slot * kArgSlotBeams;
   TX_CUDA(cudaMalloc((void**)&B->d_tab, std::max<size_t>(tab.size(), 1) * 4));
   if (!tab.empty()) TX_CUDA(cudaMemcpy(B->d_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice));
   TX_CUDA(cudaMalloc((void**)&B->d_items, std::max<size_t>(items.size(), 1) * sizeof(Stage1Item)));
@@ -279,24 +319,51 @@ int build_batch(tx_batch* B, int64_t budget) {
     TX_CUDA(cudaEventCreateWithFlags(&B->done[i], cudaEventDisableTiming));
   }
   TX_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  if (B->flags & TX_BATCH_PROFILE) {
+    B->prof_ev.assign(B->launches.size() + 1, nullptr);
+    for (auto& e : B->prof_ev) TX_CUDA(cudaEventCreate(&e));
+  }
   return TX_OK;
 }
 
-// Enqueues one step: the argument copy, then every launch in order.
+// Adds the previous profiled step's launch times to the per-phase sums.
+int collect_profile(tx_batch* B) {
+  if (!B->prof_pending) return TX_OK;
+  TX_CUDA(cudaEventSynchronize(B->prof_ev.back()));
+  for (size_t i = 0; i < B->launches.size(); ++i) {
+    float ms = 0.f;
+    TX_CUDA(cudaEventElapsedTime(&ms, B->prof_ev[i], B->prof_ev[i + 1]));
+    B->prof_ms[B->launches[i].kind] += ms;
+  }
+  ++B->prof_steps;
+  B->prof_pending = false;
+  return TX_OK;
+}
+
+// Enqueues one step: per wave, the copy of its beams' arguments into the
+// batch's constant slot, then the wave's launches in order.
 int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
-  TX_CUDA(cudaMemcpyAsync(B->d_args, h_src, (size_t)B->n * sizeof(BeamArgs), cudaMemcpyHostToDevice, st));
-  const BeamArgs none{};
-  for (const BatchLaunch& L : B->launches) {
+  const bool prof = (B->flags & TX_BATCH_PROFILE) != 0;
+  const SlotArgs src{B->slot * kArgSlotBeams};
+  int wave = -1;
+  for (size_t li = 0; li < B->launches.size(); ++li) {
+    const BatchLaunch& L = B->launches[li];
+    if (L.wave != wave) {
+      wave = L.wave;
+      const int first = B->wave_first[wave], cnt = B->wave_first[wave + 1] - first;
+      TX_CUDA(cudaMemcpyAsync(B->d_slot, h_src + first, (size_t)cnt * sizeof(BeamArgs), cudaMemcpyHostToDevice, st));
+    }
+    if (prof) TX_CUDA(cudaEventRecord(B->prof_ev[li], st));
     const int32_t* off = B->d_tab + L.off;
     const int32_t* mem = B->d_tab + L.mem;
     switch (L.kind) {
       case kIngest:
-        k_ingest_batch<<<L.grid, L.threads, 0, st>>>(B->d_args, off, mem, L.nmem, L.nunits);
+        k_ingest_batch<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, off, mem, L.nmem, L.nunits);
         break;
       case kStage1: {
         const Stage1Item* it = B->d_items + L.items;
 #define TX_B1(Q) \
-  k_stage1<Q, uint16_t, true><<<L.grid, L.threads, L.smem, st>>>(none, B->d_args, it, L.nunits, L.layout, 1u)
+  k_stage1<Q, uint16_t, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, it, L.nunits, L.layout, 1u)
         switch (L.q1) {
           case 256: TX_B1(256); break;
           case 128: TX_B1(128); break;
@@ -307,9 +374,9 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
         break;
       }
       case kStage2:
-#define TX_B2(NW, SP)                                                                                         \
-  k_stage2_u16<NW, 32, SP, true><<<L.grid, L.threads, L.smem, st>>>(none, B->d_args, off, mem, L.nmem, L.nunits, \
-                                                                    L.layout)
+#define TX_B2(NW, SP)                                                                                     \
+  k_stage2_u16<NW, 32, SP, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits, \
+                                                                        L.layout)
         switch (L.split) {
           case 8: TX_B2(512, 8); break;
           case 4: TX_B2(512, 4); break;
@@ -319,11 +386,11 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
 #undef TX_B2
         break;
       case kStats:
-        k_stats<true><<<L.grid, L.threads, 0, st>>>(none, B->d_args, off, mem, L.nmem, L.nunits);
+        k_stats<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, off, mem, L.nmem, L.nunits);
         break;
       default:
-        box_kernel<true>(L.nwc, L.mode)<<<L.grid, L.threads, L.smem, st>>>(none, B->d_args, off, mem, L.nmem,
-                                                                          L.nunits, L.layout);
+        box_kernel<SlotArgs>(L.nwc, L.mode)<<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits,
+                                                                               L.layout);
         break;
     }
     const cudaError_t e = cudaGetLastError();
@@ -336,6 +403,10 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
       return TX_ERR_CUDA;
     }
   }
+  if (prof) {
+    TX_CUDA(cudaEventRecord(B->prof_ev.back(), st));
+    B->prof_pending = true;
+  }
   return TX_OK;
 }
 
@@ -347,9 +418,11 @@ int32_t tx_batch_create(int32_t n, const tx_plan* const* plans, tx_beam* const* 
                         int32_t flags, tx_batch** out) {
   if (!out || !plans || !beams || n < 1) { set_error("need n >= 1 plans and beams and an output handle"); return TX_ERR_INVALID_ARG; }
   *out = nullptr;
-  if (flags & ~TX_BATCH_GRAPH) { set_error("unknown batch flags 0x%x", flags); return TX_ERR_INVALID_ARG; }
+  if (flags & ~(TX_BATCH_GRAPH | TX_BATCH_PROFILE)) { set_error("unknown batch flags 0x%x", flags); return TX_ERR_INVALID_ARG; }
+  if ((flags & TX_BATCH_GRAPH) && (flags & TX_BATCH_PROFILE)) { set_error("TX_BATCH_PROFILE needs direct launches (no TX_BATCH_GRAPH)"); return TX_ERR_INVALID_ARG; }
   int dev = 0;
   TX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) { set_error("device %d out of range", dev); return TX_ERR_INVALID_ARG; }
   for (int i = 0; i < n; ++i) {
     const tx_plan* p = plans[i];
     const tx_beam* b = beams[i];
@@ -369,6 +442,20 @@ int32_t tx_batch_create(int32_t n, const tx_plan* const* plans, tx_beam* const* 
   B->flags = flags;
   B->plans.assign(plans, plans + n);
   B->beams.assign(beams, beams + n);
+  {
+    std::lock_guard<std::mutex> g(g_slot_mu);
+    for (int s = 0; s < kArgSlots; ++s)
+      if (!g_slot_used[dev][s]) {
+        g_slot_used[dev][s] = true;
+        B->slot = s;
+        break;
+      }
+  }
+  if (B->slot < 0) {
+    delete B;
+    set_error("all %d batch argument slots of device %d are in use (destroy a batch first)", kArgSlots, dev);
+    return TX_ERR_BUDGET;
+  }
   int rc = TX_OK;
   if (cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     set_error("cudaDeviceGetAttribute failed");
@@ -410,6 +497,8 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
     if (B->plans[i]->output == TX_OUT_CANDS && (!d_ncands || !d_ncands[i])) { set_error("beam %d is in candidate mode and needs d_ncands", i); return TX_ERR_INVALID_ARG; }
   }
   cudaStream_t st = (cudaStream_t)stream;
+  int rc = collect_profile(B);
+  if (rc) return rc;
   const int slot = (int)(B->nsteps & 1);
   if (B->used[slot]) TX_CUDA(cudaEventSynchronize(B->done[slot]));  // the step that last read this buffer
   BeamArgs* h = B->h_args[slot];
@@ -425,7 +514,7 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
     if (!B->exec[slot]) {
       cudaGraph_t g = nullptr;
       TX_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
-      const int rc = enqueue(B, h, B->cap);
+      rc = enqueue(B, h, B->cap);
       const cudaError_t e = cudaStreamEndCapture(B->cap, &g);
       if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -438,7 +527,7 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
     }
     TX_CUDA(cudaGraphLaunch(B->exec[slot], st));
   } else {
-    const int rc = enqueue(B, h, st);
+    rc = enqueue(B, h, st);
     if (rc) return rc;
   }
   TX_CUDA(cudaEventRecord(B->done[slot], st));
@@ -449,6 +538,16 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
     b->head = mod64(b->head + B->plans[i]->T, B->plans[i]->R);
     ++b->nblocks;
   }
+  return TX_OK;
+}
+
+int32_t tx_batch_read_profile(tx_batch* B, double* h_ms, int32_t* nsteps) {
+  if (!B || !h_ms) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  if (!(B->flags & TX_BATCH_PROFILE)) { set_error("the batch was created without TX_BATCH_PROFILE"); return TX_ERR_INVALID_ARG; }
+  const int rc = collect_profile(B);
+  if (rc) return rc;
+  for (int i = 0; i < TX_NPHASES; ++i) h_ms[i] = B->prof_ms[i];
+  if (nsteps) *nsteps = B->prof_steps;
   return TX_OK;
 }
 
@@ -464,9 +563,14 @@ void tx_batch_destroy(tx_batch* B) {
     if (B->h_args[i]) cudaFreeHost(B->h_args[i]);
   }
   if (B->cap) cudaStreamDestroy(B->cap);
-  cudaFree(B->d_args);
+  for (auto e : B->prof_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(B->d_tab);
   cudaFree(B->d_items);
+  if (B->slot >= 0 && B->device >= 0) {
+    std::lock_guard<std::mutex> g(g_slot_mu);
+    g_slot_used[B->device][B->slot] = false;
+  }
   cudaSetDevice(prev);
   delete B;
 }

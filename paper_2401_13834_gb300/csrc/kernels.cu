@@ -45,13 +45,13 @@ int box_smem(const tx_plan* p) { return box_smem_for(p->wmax); }
 
 template <int Q, typename PT>
 int set_stage1_attr(int bytes) {
-  TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, PT, false>, bytes));
+  TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, PT, OneBeam>, bytes));
   return TX_OK;
 }
 
 template <int NW, int MAXWARPS, int SPLIT>
 int set_stage2_attr(int bytes) {
-  TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, MAXWARPS, SPLIT, false>, bytes));
+  TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, MAXWARPS, SPLIT, OneBeam>, bytes));
   return TX_OK;
 }
 
@@ -90,7 +90,7 @@ int do_upload(tx_plan* p) {
     TX_CUDA(raise_smem_limit((const void*)k_stage2_i32<256>, s2));
   }
   if (p->output != TX_OUT_SERIES) {
-    const BoxKernel bk = box_kernel<false>(p->nw, p->output);
+    const BoxKernel<OneBeam> bk = box_kernel<OneBeam>(p->nw, p->output);
     TX_CUDA(raise_smem_limit((const void*)bk, box_smem(p)));
     TX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->dev.box_blocks_per_sm, bk, kBoxThreads, box_smem(p)));
   }
@@ -102,8 +102,8 @@ template <int Q, typename PT>
 void launch_stage1(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
   const int nitems = (int)p->items1.size();
   const int grid = std::min(nitems, std::max(p->dev.num_sms, 1));
-  k_stage1<Q, PT, false><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
-      a, nullptr, p->dev.items1, nitems, p->m, 1u);
+  k_stage1<Q, PT, OneBeam><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
+      OneBeam{a}, p->dev.items1, nitems, p->m, 1u);
 }
 
 int check_beam(const tx_plan* p, const tx_beam* b) {
@@ -338,8 +338,8 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
       const int grid = std::min(nunits, std::max(p->dev.num_sms, 1));
       const int slot = p->nsub_chunk2 * p->sww2;
 #define TX_S2(NW, SP)                                                                                       \
-  k_stage2_u16<NW, 32, SP, false><<<grid, stage2_threads(p), stage2_smem(p), st>>>(a, nullptr, nullptr, nullptr, \
-                                                                                   1, nunits, slot)
+  k_stage2_u16<NW, 32, SP, OneBeam><<<grid, stage2_threads(p), stage2_smem(p), st>>>(OneBeam{a}, nullptr, nullptr, \
+                                                                                     1, nunits, slot)
       switch (stage2_split(p)) {
         case 8: TX_S2(512, 8); break;
         case 4: TX_S2(512, 4); break;
@@ -365,14 +365,14 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   TX_MARK(3);
 
   if (!series) {
-    k_stats<false><<<(p->ndm + 127) / 128, 128, 0, st>>>(a, nullptr, nullptr, nullptr, 1, p->ndm);
+    k_stats<OneBeam><<<(p->ndm + 127) / 128, 128, 0, st>>>(OneBeam{a}, nullptr, nullptr, 1, p->ndm);
     TX_CUDA(cudaGetLastError());
     TX_MARK(4);
     if (p->output == TX_OUT_CANDS) TX_CUDA(cudaMemsetAsync(d_ncand, 0, sizeof(int64_t), st));
     const int nunits = p->ndm * p->ntile3;
     const int grid = std::min(nunits, std::max(p->dev.num_sms, 1) * p->dev.box_blocks_per_sm);
-    box_kernel<false>(p->nw, p->output)<<<grid, kBoxThreads, box_smem(p), st>>>(a, nullptr, nullptr, nullptr, 1,
-                                                                                 nunits, p->wmax);
+    box_kernel<OneBeam>(p->nw, p->output)<<<grid, kBoxThreads, box_smem(p), st>>>(OneBeam{a}, nullptr, nullptr, 1,
+                                                                                   nunits, p->wmax);
     TX_CUDA(cudaGetLastError());
   } else {
     TX_MARK(4);
@@ -603,8 +603,8 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   const int grid1 = std::min(nitems, std::max(nsm, 1));
 #define TX_NA_S1(Q)                                                                                               \
   do {                                                                                                            \
-    TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, uint16_t, false>, smem1));                             \
-    k_stage1<Q, uint16_t, false><<<grid1, kStage1Warps * 32, smem1, st>>>(a, nullptr, items, nitems, p->m, 1u);    \
+    TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, uint16_t, OneBeam>, smem1));                           \
+    k_stage1<Q, uint16_t, OneBeam><<<grid1, kStage1Warps * 32, smem1, st>>>(OneBeam{a}, items, nitems, p->m, 1u); \
   } while (0)
   switch (p->q1) {
     case 256: TX_NA_S1(256); break;
@@ -622,9 +622,9 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   const int grid2 = std::min(nunits, std::max(nsm, 1));
 #define TX_NA_S2(NW, SP)                                                                                       \
   do {                                                                                                         \
-    TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, 32, SP, false>, smem2));                            \
-    k_stage2_u16<NW, 32, SP, false><<<grid2, stage2_threads(p), smem2, st>>>(a, nullptr, nullptr, nullptr, 1,   \
-                                                                             nunits, slot);                    \
+    TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, 32, SP, OneBeam>, smem2));                          \
+    k_stage2_u16<NW, 32, SP, OneBeam><<<grid2, stage2_threads(p), smem2, st>>>(OneBeam{a}, nullptr, nullptr, 1,   \
+                                                                               nunits, slot);                    \
   } while (0)
   switch (stage2_split(p)) {
     case 8: TX_NA_S2(512, 8); break;

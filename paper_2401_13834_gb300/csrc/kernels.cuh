@@ -17,11 +17,11 @@
 //   k_boxcar     prefix sums, window sums for every width, S/N (Eq. 5), best
 //                width, and cube / plane / candidates
 //
-// Every kernel reads what it needs about a beam from a BeamArgs. With
-// BATCH = false the BeamArgs is a kernel parameter (one beam, constant bank);
-// with BATCH = true the kernel walks the concatenated work units of several
-// beams and looks each unit's beam up in a device array (unit offsets per
-// member beam, binary search).
+// Every kernel reads what it needs about a beam from a BeamArgs, through an
+// argument source (OneBeam: one beam, a kernel parameter; batched sources:
+// the kernel walks the concatenated work units of several member beams,
+// finds each unit's member from per-member unit offsets, and reads that
+// member's arguments from constant memory).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -64,14 +64,16 @@ struct BeamArgs {
   int32_t layout, ingest_vec, running, output;
 };
 
-template <bool BATCH>
-__device__ __forceinline__ BeamArgs pick(const BeamArgs& one, const BeamArgs* __restrict__ beams, int i) {
-  if constexpr (BATCH) {
-    return beams[i];
-  } else {
-    return one;
-  }
-}
+// Where a kernel finds a beam's arguments (the Src template parameter).
+// OneBeam holds them as a kernel parameter (one execute, constant bank); the
+// batched source of batch.cu reads member i of a launch from a constant-memory
+// slot. Both return the arguments by value so that a kernel loads only the
+// fields it uses. Src::kBatch selects the walk over several members' units.
+struct OneBeam {
+  static constexpr bool kBatch = false;
+  BeamArgs a;
+  __device__ __forceinline__ BeamArgs get(int) const { return a; }
+};
 
 // Member j of a batched launch owns units [off[j], off[j + 1]); returns the
 // j with off[j] <= u < off[j + 1] (off has n + 1 entries).
@@ -83,6 +85,27 @@ __device__ __forceinline__ int find_member(const int32_t* __restrict__ off, int 
   }
   return lo;
 }
+
+// Member lookup for a unit index that only grows (a block's units in turn):
+// the member's range stays in registers and is searched only when the unit
+// leaves it, walking forward (at most nmem steps over a whole kernel).
+struct MemberCursor {
+  int j = -1, lo = 0, hi = 0, beam = 0;  // member, its unit range, its argument index
+  // returns true when u belongs to another member than the previous call's
+  __device__ __forceinline__ bool seek(const int32_t* __restrict__ off, const int32_t* __restrict__ mem, int n,
+                                       int u) {
+    if (j >= 0 && u >= lo && u < hi) return false;
+    if (j < 0 || u < lo) {
+      j = find_member(off, n, u);
+    } else {
+      while (u >= __ldg(off + j + 1)) ++j;
+    }
+    lo = __ldg(off + j);
+    hi = __ldg(off + j + 1);
+    beam = __ldg(mem + j);
+    return true;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -191,14 +214,15 @@ __global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ s
 // (mod R, R a multiple of 64, so an aligned 16-byte group never straddles the
 // wrap). Time-major tiles are 64 times x 64 channels; channel-major tiles are
 // 4096 samples of one channel.
-__global__ void __launch_bounds__(256) k_ingest_batch(const BeamArgs* __restrict__ beams,
-                                                      const int32_t* __restrict__ uoff,
+template <typename Src>
+__global__ void __launch_bounds__(256) k_ingest_batch(const Src src, const int32_t* __restrict__ uoff,
                                                       const int32_t* __restrict__ umem, int nmem, int nunits) {
   __shared__ __align__(16) uint8_t tile[64][80];
+  MemberCursor cur;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int j = find_member(uoff, nmem, u);
-    const int lu = u - uoff[j];
-    const BeamArgs a = beams[umem[j]];
+    cur.seek(uoff, umem, nmem, u);
+    const int lu = u - cur.lo;
+    const BeamArgs a = src.get(cur.beam);
     if (a.layout == TX_LAYOUT_TF) {
       const int nct = (a.nchan + 63) >> 6;
       const int64_t t0 = (int64_t)(lu / nct) * 64;
@@ -333,10 +357,9 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 // or 8 warps. Shared memory is laid out for mL channels (the largest sub-band
 // of the launch), so an item's prefetch never overlaps the previous item's
 // staged words or table.
-template <int Q, typename PT, bool BATCH>
+template <int Q, typename PT, typename Src>
 __global__ void __launch_bounds__(kStage1Warps * 32, 1)
-k_stage1(const BeamArgs one, const BeamArgs* __restrict__ beams, const Stage1Item* __restrict__ items, int nitems,
-         int mL, uint32_t unit) {
+k_stage1(const Src src, const Stage1Item* __restrict__ items, int nitems, int mL, uint32_t unit) {
   extern __shared__ __align__(16) uint8_t smem1[];
   constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
@@ -355,7 +378,7 @@ k_stage1(const BeamArgs one, const BeamArgs* __restrict__ beams, const Stage1Ite
   };
   auto issue = [&](int idx) {
     const Stage1Item it = items[idx];
-    const BeamArgs a = pick<BATCH>(one, beams, it.pad0);
+    const BeamArgs a = src.get(it.pad0);
     const int R = (int)a.R;
     for (int c = warp; c < a.m; c += kStage1Warps) {
       const int pa = wstart(a, it, c) & ~15;
@@ -374,7 +397,7 @@ k_stage1(const BeamArgs one, const BeamArgs* __restrict__ beams, const Stage1Ite
   if (idx < nitems) issue(idx);
   while (idx < nitems) {
     const Stage1Item it = items[idx];
-    const BeamArgs a = pick<BATCH>(one, beams, it.pad0);
+    const BeamArgs a = src.get(it.pad0);
     const int m = a.m;
     const int TS = (m + 3) & ~3;                 // offset-table row stride (16-byte aligned quads)
     const int c0 = it.s * m;
@@ -460,10 +483,10 @@ __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long
 // exact because every stage-2 sum is below 2^32. Shared memory holds two
 // even-copy slots and one odd-copy slot of `slot` words (the largest
 // SC * SWW of the launch) and the address table.
-template <int NW, int MAXWARPS, int SPLIT, bool BATCH>
+template <int NW, int MAXWARPS, int SPLIT, typename Src>
 __global__ void __launch_bounds__(MAXWARPS * 32, 1)
-k_stage2_u16(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* __restrict__ uoff,
-             const int32_t* __restrict__ umem, int nmem, int nunits, int slot) {
+k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
+             int slot) {
   extern __shared__ __align__(16) uint32_t smem2[];
   constexpr int VW = NW / 32 / SPLIT;                    // words per lane
   uint32_t* Se = smem2;                                  // [2][slot]
@@ -476,19 +499,20 @@ k_stage2_u16(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32
   const int g = warp / SPLIT, part_i = warp - g * SPLIT;  // fine DM of the group, part of the tile
   const int jbase = part_i * (NW / SPLIT);
 
-  auto locate = [&](int u, int& lu) -> BeamArgs {
-    if constexpr (BATCH) {
-      const int j = find_member(uoff, nmem, u);
-      lu = u - uoff[j];
-      return beams[umem[j]];
+  MemberCursor cur_c, cur_i;  // units being computed / being prefetched
+  auto locate = [&](MemberCursor& c, int u, int& lu) -> BeamArgs {
+    if constexpr (Src::kBatch) {
+      c.seek(uoff, umem, nmem, u);
+      lu = u - c.lo;
+      return src.get(c.beam);
     } else {
       lu = u;
-      return one;
+      return src.get(0);
     }
   };
   auto issue = [&](int u, int ch, int buf) {
     int lu;
-    const BeamArgs a = locate(u, lu);
+    const BeamArgs a = locate(cur_i, u, lu);
     const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
     const int64_t t0 = (int64_t)tile * 2 * NW;
     const int s0 = ch * a.SC, ns = min(a.SC, a.nsub - s0);
@@ -512,7 +536,7 @@ k_stage2_u16(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32
   if (u < nunits) issue(u, 0, 0);
   while (u < nunits) {
     int lu;
-    const BeamArgs a = locate(u, lu);
+    const BeamArgs a = locate(cur_c, u, lu);
     const int SC = a.SC, SWW = a.SWW, nsub = a.nsub;
     const int nchunk = (nsub + SC - 1) / SC;
     const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
@@ -684,21 +708,21 @@ __device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
 // Then, per width W: hi + lo = W mu (hi integer) and inv = 1 / (sigma sqrt W).
 // In a batch the thread of a candidate-mode beam's first DM also zeroes that
 // beam's candidate counter (the boxcar launch comes after this one).
-template <bool BATCH>
-__global__ void k_stats(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* __restrict__ uoff,
-                        const int32_t* __restrict__ umem, int nmem, int nunits) {
+template <typename Src>
+__global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem,
+                        int nunits) {
   const int gd = blockIdx.x * blockDim.x + threadIdx.x;
   if (gd >= nunits) return;
   int d;
   BeamArgs a;
-  if constexpr (BATCH) {
+  if constexpr (Src::kBatch) {
     const int j = find_member(uoff, nmem, gd);
     d = gd - uoff[j];
-    a = beams[umem[j]];
+    a = src.get(umem[j]);
     if (d == 0 && a.output == TX_OUT_CANDS) *a.ncand = 0ull;
   } else {
     d = gd;
-    a = one;
+    a = src.get(0);
   }
   const int64_t T = a.T;
   unsigned long long s1 = 0, s2 = 0;
@@ -760,10 +784,10 @@ __global__ void k_stats(const BeamArgs one, const BeamArgs* __restrict__ beams, 
 // NWT > 0: exactly NWT widths, per-width constants in registers.
 // NWT = 0: any count up to kMaxWidths, constants in shared memory.
 // The two shared buffers are sized for wmaxL (the largest W_max of the launch).
-template <int NWT, int MODE, bool BATCH>
-__global__ void __launch_bounds__(kBoxThreads)
-k_boxcar(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* __restrict__ uoff,
-         const int32_t* __restrict__ umem, int nmem, int nunits, int wmaxL) {
+template <int NWT, int MODE, typename Src>
+__global__ void __launch_bounds__(kBoxThreads, NWT > 12 ? 3 : 4)
+k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
+         int wmaxL) {
   constexpr int NR = NWT > 0 ? NWT : 1;
   extern __shared__ __align__(16) uint32_t smb[];
   __shared__ uint32_t wsum[kBoxThreads / 32];
@@ -774,20 +798,22 @@ k_boxcar(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* 
   const int u_begin = (int)((int64_t)nunits * blockIdx.x / gridDim.x);
   const int u_end = (int)((int64_t)nunits * (blockIdx.x + 1) / gridDim.x);
 
-  auto locate = [&](int u, int& lu, int& j) -> BeamArgs {
-    if constexpr (BATCH) {
-      j = find_member(uoff, nmem, u);
-      lu = u - uoff[j];
-      return beams[umem[j]];
+  MemberCursor cur_c, cur_i;  // units being filtered / being prefetched
+  auto locate = [&](MemberCursor& c, int u, int& lu, int& j) -> BeamArgs {
+    if constexpr (Src::kBatch) {
+      c.seek(uoff, umem, nmem, u);
+      j = c.j;
+      lu = u - c.lo;
+      return src.get(c.beam);
     } else {
       j = 0;
       lu = u;
-      return one;
+      return src.get(0);
     }
   };
   auto issue = [&](int u, int buf) {
     int lu, j;
-    const BeamArgs a = locate(u, lu, j);
+    const BeamArgs a = locate(cur_i, u, lu, j);
     const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
     const int64_t t0 = (int64_t)tile * kBoxTile;
     const int n = (int)min((int64_t)kBoxTile, a.T - t0);
@@ -804,7 +830,7 @@ k_boxcar(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* 
   for (int u = u_begin, it = 0; u < u_end; ++u, ++it) {
     const int buf = it & 1;
     int lu, j;
-    const BeamArgs a = locate(u, lu, j);
+    const BeamArgs a = locate(cur_c, u, lu, j);
     const int nw = NWT > 0 ? NWT : a.nw;
     const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
     const int64_t T = a.T;
@@ -927,26 +953,27 @@ k_boxcar(const BeamArgs one, const BeamArgs* __restrict__ beams, const int32_t* 
   }
 }
 
-using BoxKernel = void (*)(const BeamArgs, const BeamArgs*, const int32_t*, const int32_t*, int, int, int);
+template <typename Src>
+using BoxKernel = void (*)(const Src, const int32_t*, const int32_t*, int, int, int);
 
 // Exact width counts 1..12 and 16 get their own instantiation; others use
 // the generic one (NWT = 0).
-template <int MODE, bool BATCH>
-BoxKernel box_kernel_m(int nw) {
+template <int MODE, typename Src>
+BoxKernel<Src> box_kernel_m(int nw) {
   switch (nw) {
 #define TX_BOX(N) \
-  case N: return k_boxcar<N, MODE, BATCH>;
+  case N: return k_boxcar<N, MODE, Src>;
     TX_BOX(1) TX_BOX(2) TX_BOX(3) TX_BOX(4) TX_BOX(5) TX_BOX(6) TX_BOX(7) TX_BOX(8) TX_BOX(9) TX_BOX(10)
     TX_BOX(11) TX_BOX(12) TX_BOX(16)
 #undef TX_BOX
-    default: return k_boxcar<0, MODE, BATCH>;
+    default: return k_boxcar<0, MODE, Src>;
   }
 }
 
-template <bool BATCH>
-BoxKernel box_kernel(int nw, int mode) {
-  return mode == TX_OUT_CANDS ? box_kernel_m<TX_OUT_CANDS, BATCH>(nw)
-         : mode == TX_OUT_PLANE ? box_kernel_m<TX_OUT_PLANE, BATCH>(nw) : box_kernel_m<TX_OUT_CUBE, BATCH>(nw);
+template <typename Src>
+BoxKernel<Src> box_kernel(int nw, int mode) {
+  return mode == TX_OUT_CANDS ? box_kernel_m<TX_OUT_CANDS, Src>(nw)
+         : mode == TX_OUT_PLANE ? box_kernel_m<TX_OUT_PLANE, Src>(nw) : box_kernel_m<TX_OUT_CUBE, Src>(nw);
 }
 
 // Instantiation class of a width count: the exact-count kernels, or 0 (generic).
@@ -985,11 +1012,8 @@ inline int box_smem_for(int wmax) { return 2 * ((kBoxTile + wmax + 8 + 3) & ~3) 
 // uint16 stage 2: two even-copy slots, one odd-copy slot, address table
 inline int stage2_u16_smem_for(int slot, int sc) { return (3 * slot + kStage2MaxGroup * sc) * 4; }
 
-// Warps per fine DM for the uint16 stage 2: enough to fill 32 warps.
-inline int stage2_split(const tx_plan* p) {
-  if (p->nw2 != 512) return 1;
-  return p->group <= 4 ? 8 : p->group <= 8 ? 4 : p->group <= 16 ? 2 : 1;
-}
+// Warps per fine DM of the uint16 stage 2 (the plan's tile choice).
+inline int stage2_split(const tx_plan* p) { return p->split2; }
 
 inline int stage2_threads(const tx_plan* p) { return std::min(p->group, kStage2MaxGroup) * 32 * stage2_split(p); }
 

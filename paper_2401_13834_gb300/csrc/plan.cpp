@@ -185,7 +185,13 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   // A sub-band's staged window starts at the tile start + emin rounded down to
   // 8 elements (16 bytes) and spans the tile, the group's delay spread and
   // that alignment: sww2 32-bit words.
-  p->nw2 = G <= 16 ? 512 : 256;  // 512-word tiles split over 2-8 warps per fine DM; 256 for larger groups
+  // 512-word tiles shared by 2-8 warps per fine DM, or 256-word tiles with one
+  int split = d->tile_split2;
+  if (split == 0) split = G <= 4 ? 8 : G <= 8 ? 4 : G <= 16 ? 2 : 1;
+  if (split != 1 && split != 2 && split != 4 && split != 8) { set_error("tile_split2 must be 0, 1, 2, 4 or 8"); return TX_ERR_INVALID_ARG; }
+  if (std::min(G, kStage2MaxGroup) * split > 32) { set_error("min(group, 32) * tile_split2 must be <= 32 (group %d)", G); return TX_ERR_INVALID_ARG; }
+  p->split2 = split;
+  p->nw2 = split == 1 ? 256 : 512;
   const int64_t tt2 = 2 * (int64_t)p->nw2;
   p->ntile2 = (int32_t)((p->Td + tt2 - 1) / tt2);
   p->sww2 = (int32_t)round_up(p->nw2 + (span2 + 7 + 2) / 2 + 6, 4);
@@ -210,6 +216,11 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   // quarter length q1: the largest of 256/128/64/32 whose staged words, raw
   // prefetch buffer and address table fit in shared memory
   int q1 = 256;
+  if (d->tile_q1) {
+    if (d->tile_q1 != 32 && d->tile_q1 != 64 && d->tile_q1 != 128 && d->tile_q1 != 256) { set_error("tile_q1 must be 0, 32, 64, 128 or 256"); return TX_ERR_INVALID_ARG; }
+    q1 = d->tile_q1;
+    if (stage1_smem_bytes(m, q1) > kSmemMax) { set_error("tile_q1 %d does not fit shared memory with %d channels per sub-band", q1, m); return TX_ERR_UNSUPPORTED; }
+  }
   while (q1 > 32 && stage1_smem_bytes(m, q1) > kSmemMax) q1 /= 2;
   if (stage1_smem_bytes(m, q1) > kSmemMax) { set_error("too many channels per sub-band for stage 1 (%d)", m); return TX_ERR_UNSUPPORTED; }
   p->q1 = q1;
@@ -279,7 +290,7 @@ using namespace tx;
 
 extern "C" {
 
-int32_t tx_version(void) { return 100; }
+int32_t tx_version(void) { return 200; }
 
 int32_t tx_last_error(char* buf, size_t size) {
   const std::string& e = g_last_error;
@@ -319,6 +330,8 @@ int32_t tx_plan_get_info(const tx_plan* p, tx_plan_info* info) {
   info->block_bytes = (int64_t)p->nchan * p->T;
   info->ring_len = p->R;
   info->ring_head0 = p->head0;
+  info->tile_q1 = p->q1;
+  info->tile_split2 = p->split2;
   return TX_OK;
 }
 

@@ -102,6 +102,7 @@ struct tx_plan {
   int32_t span1_max = 256;        // staged delay spread limit of stage 1
   int32_t span2_max = 0;          // max stage-2 delay spread within a group
   int32_t nw2 = 512;              // stage-2 tile words (2 * nw2 outputs)
+  int32_t split2 = 2;             // stage-2 warps per fine DM (uint16 path)
   int32_t ntile2 = 0;             // stage-2 tiles over the series
   int32_t sww2 = 0;               // stage-2 staged words per sub-band (uint16 path)
   int32_t sw2_i32 = 0;            // stage-2 staged elements per sub-band (int32 path)

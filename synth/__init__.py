@@ -16,6 +16,10 @@ Workloads (the paper's benchmark simulates MMGPS-L-like data at 153 us, Sec. 3):
 * ``meerkat_l``  -- 4096 channels over 856-1712 MHz, 153.12 us, 65536-sample
   blocks, 4096 DMs over 0-2000 in four segments whose step doubles, 64
   sub-bands, widths 1..256, twenty pulses.
+* ``batched``    -- 64 beams of uneven shape on the same band and sampling:
+  channels in {1024, 2048, 4096}, blocks in {32768, 65536, 131072} samples,
+  {1024, 4096, 8192} DM trials over 0-3000 (four doubling-step segments),
+  widths 1..256, a few pulses per beam; drawn with a fixed seed.
 """
 from __future__ import annotations
 
@@ -130,6 +134,33 @@ def tiny_workload(nchan=32, nsub=4, ndm=12, nsamp=300, dm_max=60.0, widths=(1, 2
     )
 
 
+def batched_workloads(nbeams: int = 64, seed: int = 3, dm_max: float = 3000.0) -> list:
+    """Beams of uneven shape sharing the MeerKAT-L band and sampling time.
+
+    Each beam draws its channel count, block length and DM-trial count
+    independently and uniformly from the three values of each; the sub-band
+    count defaults to 64 channels per sub-band (an autotuner may change it).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nbeams):
+        nchan = int(rng.choice([1024, 2048, 4096]))
+        nsamp = int(rng.choice([32768, 65536, 131072]))
+        ndm = int(rng.choice([1024, 4096, 8192]))
+        out.append(Workload(
+            name=f"beam{i}-{nchan}ch-{ndm}dm-T{nsamp}",
+            freqs_mhz=channel_centres(856.0, 1712.0, nchan),
+            tsamp_s=153.12e-6,
+            dms=meerkat_dm_grid(ndm, dm_max),
+            nsub=nchan // 64,
+            widths=geometric_widths(256),
+            nsamp=nsamp,
+            noise_mean=128.0,
+            noise_std=12.0,
+        ))
+    return out
+
+
 WORKLOADS = {"small": small_workload, "meerkat_l": meerkat_l_workload}
 
 
@@ -212,6 +243,64 @@ def add_pulse(x: np.ndarray, p: Pulse, freqs: np.ndarray, tsamp: float, f_top=No
             continue
         rel = np.arange(t0, t1, dtype=np.float64) - centres[c]
         x[c, t0:t1] += (p.amp * spec[c] * np.interp(rel, lat, prof, left=0.0, right=0.0)).astype(x.dtype)
+
+
+def pulse_points(p: Pulse, freqs: np.ndarray, tsamp: float, nsamp: int, f_top=None, f_mid=None):
+    """The (channel, sample, value) points ``add_pulse`` adds, as flat arrays.
+
+    Same window per channel (max(floor(c) - half, 0) .. min(ceil(c) + half + 1,
+    nsamp), c the continuous arrival) and the same interpolated values, for
+    adders that work on other array types.
+    """
+    f_top = float(freqs.max()) if f_top is None else f_top
+    f_mid = 0.5 * (float(freqs.min()) + f_top) if f_mid is None else f_mid
+    centres = p.t_arr + sky_delay_samples(p.dm, freqs, f_top, tsamp)
+    spec = (freqs / f_mid) ** (-p.alpha)
+    half = _pulse_half_span(p)
+    lat = np.arange(-half - 1, half + 1 + 1e-9, 1.0 / 16.0)
+    prof = pulse_profile(lat, p.fwhm, p.tau_s)
+    lo = np.floor(centres).astype(np.int64) - half
+    hi = np.ceil(centres).astype(np.int64) + half + 1
+    tt = lo[:, None] + np.arange(2 * half + 2, dtype=np.int64)[None, :]
+    keep = (tt < hi[:, None]) & (tt >= 0) & (tt < nsamp)
+    rel = tt - centres[:, None]
+    vals = (p.amp * spec[:, None] * np.interp(rel, lat, prof, left=0.0, right=0.0)).astype(np.float32)
+    chan = np.broadcast_to(np.arange(freqs.size, dtype=np.int64)[:, None], tt.shape)
+    return chan[keep], tt[keep], vals[keep]
+
+
+def device_spectrum(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0, device="cuda"):
+    """uint8 [nchan, nsamp_total] torch tensor drawn on a CUDA device.
+
+    clip(round(N(mean, std) + pulses), 0, 255) like ``make_spectrum``, with the
+    noise from torch's counter-based generator on the device (seeded; the same
+    seed, shape and device type give the same values) so that volumes of many
+    GB need no host work. Pulses are added as ``pulse_points`` gives them.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    x = torch.randn((wl.nchan, nsamp_total), generator=g, device=device, dtype=torch.float32)
+    x.mul_(float(wl.noise_std)).add_(float(wl.noise_mean))
+    for p in pulses:
+        c, t, v = pulse_points(p, wl.freqs_mhz, wl.tsamp_s, nsamp_total)
+        if c.size:
+            x.index_put_((torch.from_numpy(c).to(device), torch.from_numpy(t).to(device)),
+                         torch.from_numpy(v).to(device), accumulate=True)
+    return x.round_().clamp_(0.0, 255.0).to(torch.uint8)
+
+
+def batched_pulses(wl: Workload, n: int = 4, seed: int = 0) -> list:
+    """Pulses of one batched beam: DM U(0, DM_max), FWHM logU(0.3, 20) ms, S/N U(8, 50), flat spectrum, no scattering."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        fwhm = math.exp(rng.uniform(math.log(0.3e-3), math.log(20e-3))) / wl.tsamp_s
+        p = Pulse(dm=float(rng.uniform(0.0, float(wl.dms.max()))), t_arr=float(rng.uniform(0.05, 0.95) * wl.nsamp),
+                  fwhm=fwhm)
+        p.amp = amplitude_for_snr(float(rng.uniform(8.0, 50.0)), wl, p)
+        out.append(p)
+    return out
 
 
 def quantise(values: np.ndarray) -> np.ndarray:

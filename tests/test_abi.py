@@ -95,6 +95,9 @@ def test_geometric_widths_match_ladder(tx):
     (dict(tsamp=0.0), -1),
     (dict(nsamp=0), -1),
     (dict(output="cands", max_cands=0), -1),
+    (dict(tile_q1=48), -1),
+    (dict(tile_split2=3), -1),
+    (dict(group=8, tile_split2=8), -1),        # 8 DMs x 8 warps > 32 warps
 ])
 def test_invalid_plans_rejected(tx, kw, code):
     wl = synth.tiny_workload(nchan=32, nsub=4)
@@ -114,4 +117,23 @@ def test_too_many_channels_per_subband_unsupported(tx):
     wl = synth.tiny_workload(nchan=520, nsub=2)
     with pytest.raises(tx.TxError) as e:
         _plan(tx, wl)
+    assert e.value.code == -8
+
+
+def test_tile_knobs_reported(tx):
+    wl = synth.tiny_workload(nchan=64, nsub=4, ndm=40)
+    auto = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 4, wl.widths, wl.nsamp, group=4)
+    assert auto.tile_q1 == 256 and auto.tile_split2 == 8          # groups of <= 4 DMs: 8 warps each
+    p = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 4, wl.widths, wl.nsamp, group=4, tile_q1=64, tile_split2=1)
+    assert p.tile_q1 == 64 and p.tile_split2 == 1
+    # the tile shapes change neither the tables nor the overlap
+    assert p.overlap == auto.overlap
+    for k in ("d1", "d2", "coarse_of_fine", "coarse_dm"):
+        assert np.array_equal(p.tables()[k], auto.tables()[k])
+
+
+def test_tile_q1_that_does_not_fit_is_unsupported(tx):
+    wl = synth.tiny_workload(nchan=257, nsub=1, ndm=8)
+    with pytest.raises(tx.TxError) as e:
+        tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 1, wl.widths, wl.nsamp, tile_q1=256)
     assert e.value.code == -8

@@ -68,7 +68,7 @@ def same(a, b):
     return np.array_equal(a, b)
 
 
-def run_pair(tx, specs, graph, budget):
+def run_pair(tx, specs, graph, budget, profile=False):
     plans = [make_plan(tx, s) for s in specs]
     rng = np.random.default_rng(11)
     streams = [rng.integers(0, 256, size=(p.nchan, p.overlap + NSTEPS * p.nsamp), dtype=np.uint8) for p in plans]
@@ -78,7 +78,7 @@ def run_pair(tx, specs, graph, budget):
         tail = torch.from_numpy(to_layout(X[:, :p.overlap], p.layout)).cuda()
         b1.prime(tail)
         b2.prime(tail)
-    batch = tx.Batch(plans, mixed, workspace_budget=budget, graph=graph)
+    batch = tx.Batch(plans, mixed, workspace_budget=budget, graph=graph, profile=profile)
     ws = batch.alloc_workspace()
     outs = batch.alloc_outs()
     solo_ws = [p.alloc_workspace() for p in plans]
@@ -115,6 +115,13 @@ def test_batch_in_waves_under_budget(tx):
     assert batch.workspace_bytes <= budget
 
 
+def test_batch_profile_times_every_phase(tx):
+    batch, _ = run_pair(tx, BEAMS, graph=False, budget=0, profile=True)
+    ms, n = batch.read_profile()
+    assert n == NSTEPS
+    assert all(v > 0.0 for v in ms.values()), ms
+
+
 def test_batch_rejects_what_it_cannot_run(tx):
     p16 = make_plan(tx, BEAMS[0])
     spec = dict(BEAMS[0], interm="i32")
@@ -129,3 +136,6 @@ def test_batch_rejects_what_it_cannot_run(tx):
     with pytest.raises(tx.TxError) as e:
         tx.Batch([p16], [b16], workspace_budget=max(1, p16.workspace_bytes // 2))
     assert e.value.code == -7                        # one beam over the budget
+    with pytest.raises(tx.TxError) as e:
+        tx.Batch([p16], [b16], graph=True, profile=True)
+    assert e.value.code == -1                        # profiling needs direct launches

@@ -337,3 +337,17 @@ def test_boxcar_width_sets(tx, widths, output):
     else:
         s, w = tx.plane_view(plan, out)
         _check_plane(s.cpu().numpy(), w.cpu().numpy(), snr)
+
+
+@pytest.mark.parametrize("q1", [32, 64, 128, 256])
+@pytest.mark.parametrize("split", [1, 2, 4, 8])
+def test_tile_shapes_do_not_change_results(tx, q1, split):
+    """Every stage-1 tile length and stage-2 warp split gives the oracle's series."""
+    wl = synth.tiny_workload(nchan=128, nsub=16, ndm=64, nsamp=5000, dm_max=400.0, tsamp=128e-6, group=4)
+    plan = make_plan(tx, wl, output="series", tile_q1=q1, tile_split2=split)
+    assert (plan.tile_q1, plan.tile_split2) == (q1, split)
+    op = oracle_plan(wl)
+    X = rand_stream(wl.nchan, plan.overlap + wl.nsamp, seed=77)
+    (out, _, _), = run_blocks(tx, plan, X)[0]
+    got = tx.series_view(plan, out).cpu().numpy()
+    assert np.array_equal(got, O.subband_dedisperse(X, op, plan.series_len))

@@ -131,6 +131,8 @@ typedef struct tx_plan_info {
   int64_t ring_head0;       /* where a fresh beam's first block lands in it        */
   int32_t tile_q1;          /* the stage-1 tile chosen (see tx_plan_desc)           */
   int32_t tile_split2;      /* the stage-2 warps per fine DM chosen                 */
+  int64_t workspace_bytes_compact;   /* d_workspace of an execute on a compact beam */
+  int64_t compact_beam_state_bytes;  /* device memory one compact beam holds        */
 } tx_plan_info;
 
 /* One candidate of TX_OUT_CANDS: a DM-time plane point with S/N >= threshold. */
@@ -189,6 +191,15 @@ void tx_plan_destroy(tx_plan* plan);
    Synchronous. Errors: INVALID_ARG, OOM, CUDA. */
 int32_t tx_beam_create(const tx_plan* plan, tx_beam** out);
 
+/* A compact beam keeps only the carried tail (nchan * L bytes) and the
+   running statistics resident; each execute borrows its circular buffer
+   from the workspace (info.workspace_bytes_compact instead of
+   info.workspace_bytes), copying the tail in before the block lands and the
+   new tail out after. The results are those of a full beam; the cost is two
+   copies of the tail per block. Everything else that takes a beam takes a
+   compact one. Errors as tx_beam_create. */
+int32_t tx_beam_create_compact(const tx_plan* plan, tx_beam** out);
+
 /* Zeroes the carried tail and the running statistics (enqueued on `stream`). */
 int32_t tx_beam_reset(const tx_plan* plan, tx_beam* beam, void* stream);
 
@@ -213,7 +224,8 @@ void tx_beam_destroy(tx_beam* beam);
      d_ncand     int64 [1], TX_OUT_CANDS only (else may be NULL): set to the number
                  of candidates found; records beyond max_cands are dropped, so a
                  value above max_cands means the buffer overflowed
-     d_workspace info.workspace_bytes bytes of device scratch (not kept)
+     d_workspace info.workspace_bytes bytes of device scratch (not kept);
+                 info.workspace_bytes_compact for a compact beam
    All kernels go on `stream`; the call returns once they are enqueued. */
 int32_t tx_execute(const tx_plan* plan, tx_beam* beam, const uint8_t* d_block, void* d_out,
                    int64_t* d_ncand, void* d_workspace, void* stream);
@@ -278,10 +290,12 @@ void tx_timer_destroy(tx_timer* timer);
    results are exactly those tx_execute would give for the same block, and
    its beam state (tail, running statistics, block count) advances the same way.
 
-   Waves: with workspace_budget > 0 the beams are split, in order, into waves
-   whose summed per-beam workspace (tx_plan_info.workspace_bytes) fits the
-   budget; waves run one after another in the same workspace. With
-   workspace_budget <= 0 all beams form one wave.
+   Waves: the beams are split, in order, into waves of at most 96 beams
+   whose summed per-beam workspace (tx_plan_info.workspace_bytes, or
+   workspace_bytes_compact for a compact beam) fits workspace_budget when it
+   is > 0; waves run one after another in the same workspace. At most two
+   batches may exist per device at a time (their per-beam arguments live in
+   one of two constant-memory slots; a third create returns TX_ERR_BUDGET).
 
    TX_BATCH_GRAPH: the first two steps are captured (on a private stream) as
    CUDA graphs, one per argument buffer, and later steps replay them; without

@@ -44,6 +44,7 @@ class _Info(C.Structure):
         ("workspace_bytes", C.c_int64), ("beam_state_bytes", C.c_int64), ("out_bytes", C.c_int64),
         ("export_bytes", C.c_int64), ("block_bytes", C.c_int64), ("ring_len", C.c_int64),
         ("ring_head0", C.c_int64), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32),
+        ("workspace_bytes_compact", C.c_int64), ("compact_beam_state_bytes", C.c_int64),
     ]
 
 
@@ -79,6 +80,7 @@ def _load():
         "tx_plan_stage1_layout": (I32, [P, C.POINTER(I64), C.POINTER(I64), VP]),
         "tx_plan_destroy": (None, [P]),
         "tx_beam_create": (I32, [P, C.POINTER(P)]),
+        "tx_beam_create_compact": (I32, [P, C.POINTER(P)]),
         "tx_beam_reset": (I32, [P, P, VP]),
         "tx_beam_prime": (I32, [P, P, VP, VP]),
         "tx_beam_export": (I32, [P, P, VP, I64]),
@@ -202,9 +204,11 @@ class Plan:
         _check(lib.tx_plan_stage1_layout(self._h, C.byref(off), C.byref(pitch), base.ctypes.data_as(C.c_void_p)))
         return int(off.value), int(pitch.value), base
 
-    def alloc_workspace(self, device=None):
+    def alloc_workspace(self, device=None, compact=False):
+        """Workspace of one execute (on a compact beam: with room for its borrowed ring)."""
         import torch
-        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device or "cuda")
+        n = self.workspace_bytes_compact if compact else self.workspace_bytes
+        return torch.empty(n, dtype=torch.uint8, device=device or "cuda")
 
     def alloc_out(self, device=None):
         import torch
@@ -222,12 +226,18 @@ class Plan:
 
 
 class Beam:
-    """Per-beam device state: the carried tail (two rings) and running statistics."""
+    """Per-beam device state: the carried tail and running statistics.
 
-    def __init__(self, plan: Plan):
+    A full beam keeps a circular buffer of L + T samples per channel resident;
+    a compact beam (``compact=True``) only the L-sample tail, and borrows the
+    buffer from each execute's workspace (``plan.alloc_workspace(compact=True)``).
+    """
+
+    def __init__(self, plan: Plan, compact: bool = False):
         self.plan = plan
+        self.compact = bool(compact)
         h = C.c_void_p()
-        _check(lib.tx_beam_create(plan.handle, C.byref(h)))
+        _check((lib.tx_beam_create_compact if compact else lib.tx_beam_create)(plan.handle, C.byref(h)))
         self._h = h
 
     @property
@@ -273,7 +283,7 @@ def execute(plan: Plan, beam: Beam, block, out=None, ncand=None, workspace=None,
     if out is None:
         out, ncand = plan.alloc_out(block.device)
     if workspace is None:
-        workspace = plan.alloc_workspace(block.device)
+        workspace = plan.alloc_workspace(block.device, compact=beam.compact)
     assert block.is_cuda and block.numel() == plan.nchan * plan.nsamp and block.is_contiguous()
     _check(lib.tx_execute(plan.handle, beam.handle, _ptr(block), _ptr(out), _ptr(ncand), _ptr(workspace),
                           _stream_ptr(stream)))

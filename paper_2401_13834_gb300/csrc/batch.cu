@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "kernels.cuh"
@@ -54,9 +55,15 @@ struct SlotArgs {
 std::mutex g_slot_mu;
 bool g_slot_used[kMaxDevices][kArgSlots] = {};
 
-// A launch's kind is the phase it belongs to (TX_PHASE_* order).
+// Launch kinds: the first five are the phases (TX_PHASE_* order); the compact
+// beams' tail copies count as ingest.
 enum LaunchKind { kIngest = TX_PHASE_INGEST, kStage1 = TX_PHASE_STAGE1, kStage2 = TX_PHASE_STAGE2,
-                  kStats = TX_PHASE_STATS, kBoxcar = TX_PHASE_BOXCAR };
+                  kStats = TX_PHASE_STATS, kBoxcar = TX_PHASE_BOXCAR, kTailIn = 5, kTailOut = 6 };
+
+int phase_of(int kind) { return kind == kTailIn || kind == kTailOut ? TX_PHASE_INGEST : kind; }
+
+// Workspace of one execute on beam b of plan p.
+int64_t beam_ws(const tx_plan* p, const tx_beam* b) { return b->compact ? p->ws_bytes_compact : p->ws_bytes; }
 
 // One persistent launch of a step over the units of its member beams.
 struct BatchLaunch {
@@ -64,9 +71,8 @@ struct BatchLaunch {
   int wave = 0;
   int q1 = 0, split = 0, nwc = 0, mode = 0;  // template selectors
   int grid = 0, threads = 0, smem = 0;
-  int nmem = 0, nunits = 0;                  // member beams, units (stage 1: work items)
+  int nmem = 0, nunits = 0;                  // member beams, work units (stage 1: the plans' items)
   int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
-  int64_t items = 0;                         // stage 1: offset of its work items
   int layout = 0;                            // stage 1 mL, stage 2 slot words, boxcar wmaxL
 };
 
@@ -85,7 +91,6 @@ struct tx_batch {
   std::vector<BatchLaunch> launches;  // wave by wave
   BeamArgs* d_slot = nullptr;    // device address of the batch's constant-memory slot
   int32_t* d_tab = nullptr;      // unit offsets and member lists of every launch
-  Stage1Item* d_items = nullptr; // stage-1 work items of every stage-1 launch, pad0 = member
   BeamArgs* h_args[2] = {nullptr, nullptr};  // pinned, alternating between steps
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool used[2] = {false, false};
@@ -105,6 +110,8 @@ namespace {
 const void* launch_kernel(const BatchLaunch& L) {
   switch (L.kind) {
     case kIngest: return (const void*)k_ingest_batch<SlotArgs>;
+    case kTailIn:
+    case kTailOut: return (const void*)k_tail<SlotArgs>;
     case kStage1:
       switch (L.q1) {
         case 256: return (const void*)k_stage1<256, uint16_t, SlotArgs>;
@@ -131,7 +138,7 @@ int build_batch(tx_batch* B, int64_t budget) {
   B->wave_first.assign(1, 0);
   int64_t cur = 0;
   for (int i = 0; i < n; ++i) {
-    const int64_t need = B->plans[i]->ws_bytes;
+    const int64_t need = beam_ws(B->plans[i], B->beams[i]);
     if (budget > 0 && need > budget) {
       set_error("beam %d needs %lld workspace bytes, more than the budget %lld", i, (long long)need, (long long)budget);
       return TX_ERR_BUDGET;
@@ -150,7 +157,6 @@ int build_batch(tx_batch* B, int64_t budget) {
   B->nwaves = (int)B->wave_first.size() - 1;
 
   std::vector<int32_t> tab;
-  std::vector<Stage1Item> items;
   // unit offsets and member list (wave-local indices) of one launch
   auto add_members = [&](BatchLaunch& L, const std::vector<int>& mem, int first, auto units_of) -> int {
     L.nmem = (int)mem.size();
@@ -174,6 +180,25 @@ int build_batch(tx_batch* B, int64_t budget) {
     const int first = B->wave_first[wv];
     std::vector<int> mem;
     for (int i = first; i < B->wave_first[wv + 1]; ++i) mem.push_back(i);
+    // ---- compact beams: tails into their borrowed rings ---------------------------
+    std::vector<int> compact;
+    for (int b : mem)
+      if (B->beams[b]->compact && B->plans[b]->L > 0) compact.push_back(b);
+    auto tail_launch = [&](int kind) -> int {
+      BatchLaunch L;
+      L.kind = kind;
+      L.wave = wv;
+      const int r = add_members(L, compact, first, [&](int b) -> int64_t {
+        const tx_plan* p = B->plans[b];
+        return (int64_t)p->nchan * ((p->tail_pitch + 4095) / 4096);
+      });
+      if (r) return r;
+      L.threads = 256;
+      L.grid = std::min(L.nunits, nsm * 8);
+      if (L.nunits > 0) B->launches.push_back(L);
+      return TX_OK;
+    };
+    if (!compact.empty() && (rc = tail_launch(kTailIn))) return rc;
     // ---- ingest: every beam of the wave ------------------------------------------
     {
       BatchLaunch L;
@@ -189,39 +214,35 @@ int build_batch(tx_batch* B, int64_t budget) {
       L.grid = std::min(L.nunits, nsm * 8);
       if (L.nunits > 0) B->launches.push_back(L);
     }
-    // ---- stage 1, one launch per tile length q1 ----------------------------------
-    std::map<int, std::vector<int>> by_q;
-    for (int b : mem) by_q[B->plans[b]->q1].push_back(b);
+    // ---- compact beams: the new tails out ------------------------------------------
+    if (!compact.empty() && (rc = tail_launch(kTailOut))) return rc;
+    // ---- stage 1, one launch per (tile length, channels per sub-band): the shared
+    // memory of a launch is laid out for its largest sub-band, and a mix would
+    // take carve-out from L1 for the smaller ones
+    std::map<std::pair<int, int>, std::vector<int>> by_q;
+    for (int b : mem) by_q[{B->plans[b]->q1, B->plans[b]->m}].push_back(b);
     for (auto& kv : by_q) {
       BatchLaunch L;
       L.kind = kStage1;
       L.wave = wv;
-      L.q1 = kv.first;
-      L.items = (int64_t)items.size();
-      int mL = 0;
-      for (int b : kv.second) {
-        const tx_plan* p = B->plans[b];
-        mL = std::max(mL, p->m);
-        for (Stage1Item it : p->items1) {
-          it.pad0 = b - first;
-          items.push_back(it);
-        }
-      }
-      const int64_t nit = (int64_t)items.size() - L.items;
-      if (nit >= INT32_MAX) { set_error("too many stage-1 items in one batched launch"); return TX_ERR_UNSUPPORTED; }
-      L.nunits = (int)nit;
-      L.layout = mL;
+      L.q1 = kv.first.first;
+      if ((rc = add_members(L, kv.second, first, [&](int b) -> int64_t { return (int64_t)B->plans[b]->items1.size(); })))
+        return rc;
+      L.layout = kv.first.second;  // channels per sub-band of every member
+      const int mL = L.layout;
       L.smem = (int)stage1_smem_bytes(mL, L.q1);
       if (L.smem > kSmemMax) { set_error("stage-1 shared memory for %d channels per sub-band exceeds the limit", mL); return TX_ERR_UNSUPPORTED; }
       L.threads = kStage1Warps * 32;
       L.grid = std::min(L.nunits, nsm);
       if (L.nunits > 0) B->launches.push_back(L);
     }
-    // ---- stage 2, one launch per warp split (tile width follows) -------------------
+    // ---- stage 2, one launch per (warp split, sub-bands per chunk, block size) -------
     // Shared memory is laid out for the largest staged chunk and table of the
-    // launch; a split class whose mix would not fit is launched per chunk size.
-    std::map<int, std::vector<int>> by_split;
-    for (int b : mem) by_split[stage2_split(B->plans[b])].push_back(b);
+    // launch (which the plans size to fit, with room for the static sums); a
+    // block as large as its largest group would idle warps of smaller groups.
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_split;
+    for (int b : mem)
+      by_split[{stage2_split(B->plans[b]), B->plans[b]->nsub_chunk2, stage2_threads(B->plans[b])}].push_back(b);
     auto s2_smem = [&](const std::vector<int>& g) {
       int slot = 0, sc = 0;
       for (int b : g) {
@@ -231,15 +252,7 @@ int build_batch(tx_batch* B, int64_t budget) {
       return std::make_pair(slot, stage2_u16_smem_for(slot, sc));
     };
     std::vector<std::pair<int, std::vector<int>>> s2groups;
-    for (auto& kv : by_split) {
-      if (s2_smem(kv.second).second <= kSmemMax - 1024) {  // room for the static sums
-        s2groups.push_back(kv);
-        continue;
-      }
-      std::map<int, std::vector<int>> by_sc;
-      for (int b : kv.second) by_sc[B->plans[b]->nsub_chunk2].push_back(b);
-      for (auto& kc : by_sc) s2groups.push_back({kv.first, kc.second});
-    }
+    for (auto& kv : by_split) s2groups.push_back({std::get<0>(kv.first), kv.second});
     for (auto& kv : s2groups) {
       BatchLaunch L;
       L.kind = kStage2;
@@ -310,9 +323,6 @@ int build_batch(tx_batch* B, int64_t budget) {
   B->d_slot = static_cast<BeamArgs*>(sym) + (size_t)B->slot * kArgSlotBeams;
   TX_CUDA(cudaMalloc((void**)&B->d_tab, std::max<size_t>(tab.size(), 1) * 4));
   if (!tab.empty()) TX_CUDA(cudaMemcpy(B->d_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice));
-  TX_CUDA(cudaMalloc((void**)&B->d_items, std::max<size_t>(items.size(), 1) * sizeof(Stage1Item)));
-  if (!items.empty())
-    TX_CUDA(cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(Stage1Item), cudaMemcpyHostToDevice));
   for (int i = 0; i < 2; ++i) {
     TX_CUDA(cudaHostAlloc((void**)&B->h_args[i], (size_t)n * sizeof(BeamArgs), cudaHostAllocDefault));
     std::memset(B->h_args[i], 0, (size_t)n * sizeof(BeamArgs));
@@ -333,7 +343,7 @@ int collect_profile(tx_batch* B) {
   for (size_t i = 0; i < B->launches.size(); ++i) {
     float ms = 0.f;
     TX_CUDA(cudaEventElapsedTime(&ms, B->prof_ev[i], B->prof_ev[i + 1]));
-    B->prof_ms[B->launches[i].kind] += ms;
+    B->prof_ms[phase_of(B->launches[i].kind)] += ms;
   }
   ++B->prof_steps;
   B->prof_pending = false;
@@ -360,10 +370,14 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
       case kIngest:
         k_ingest_batch<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, off, mem, L.nmem, L.nunits);
         break;
+      case kTailIn:
+      case kTailOut:
+        k_tail<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, L.kind == kTailOut, off, mem, L.nmem, L.nunits);
+        break;
       case kStage1: {
-        const Stage1Item* it = B->d_items + L.items;
-#define TX_B1(Q) \
-  k_stage1<Q, uint16_t, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, it, L.nunits, L.layout, 1u)
+#define TX_B1(Q)                                                                                          \
+  k_stage1<Q, uint16_t, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits, L.layout, \
+                                                                     1u)
         switch (L.q1) {
           case 256: TX_B1(256); break;
           case 128: TX_B1(128); break;
@@ -535,7 +549,7 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
   ++B->nsteps;
   for (int i = 0; i < B->n; ++i) {
     tx_beam* b = B->beams[i];
-    b->head = mod64(b->head + B->plans[i]->T, B->plans[i]->R);
+    if (!b->compact) b->head = mod64(b->head + B->plans[i]->T, B->plans[i]->R);
     ++b->nblocks;
   }
   return TX_OK;
@@ -566,7 +580,6 @@ void tx_batch_destroy(tx_batch* B) {
   for (auto e : B->prof_ev)
     if (e) cudaEventDestroy(e);
   cudaFree(B->d_tab);
-  cudaFree(B->d_items);
   if (B->slot >= 0 && B->device >= 0) {
     std::lock_guard<std::mutex> g(g_slot_mu);
     g_slot_used[B->device][B->slot] = false;

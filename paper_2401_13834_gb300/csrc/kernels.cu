@@ -103,7 +103,7 @@ void launch_stage1(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
   const int nitems = (int)p->items1.size();
   const int grid = std::min(nitems, std::max(p->dev.num_sms, 1));
   k_stage1<Q, PT, OneBeam><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
-      OneBeam{a}, p->dev.items1, nitems, p->m, 1u);
+      OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u);
 }
 
 int check_beam(const tx_plan* p, const tx_beam* b) {
@@ -143,11 +143,20 @@ int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64
   return TX_OK;
 }
 
-// Copies the carried tail (the L samples before `head`, per channel) between
-// the ring and a host buffer [nchan][L].
+// Copies the carried tail (the L samples before `head`, per channel; a
+// compact beam's tail store) between the beam and a host buffer [nchan][L].
 int copy_tail(const tx_plan* p, const tx_beam* b, uint8_t* host, bool to_host) {
   const int64_t L = p->L, R = p->R;
   if (L <= 0) return TX_OK;
+  if (b->compact) {
+    uint8_t* t = b->tail + p->tail_pad;
+    const size_t pitch = (size_t)p->tail_pitch;
+    if (to_host)
+      TX_CUDA(cudaMemcpy2D(host, (size_t)L, t, pitch, (size_t)L, (size_t)p->nchan, cudaMemcpyDeviceToHost));
+    else
+      TX_CUDA(cudaMemcpy2D(t, pitch, host, (size_t)L, (size_t)L, (size_t)p->nchan, cudaMemcpyHostToDevice));
+    return TX_OK;
+  }
   const int64_t a = mod(b->head - L, R);
   const int64_t first = std::min(L, R - a);
   if (to_host) {
@@ -194,7 +203,11 @@ void tx_plan_destroy(tx_plan* p) {
   delete p;
 }
 
-int32_t tx_beam_create(const tx_plan* p, tx_beam** out) {
+}  // extern "C"
+
+namespace {
+
+int beam_create(const tx_plan* p, tx_beam** out, int compact) {
   if (!p || !out) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
   *out = nullptr;
   int rc = tx_upload_plan(p);
@@ -202,8 +215,10 @@ int32_t tx_beam_create(const tx_plan* p, tx_beam** out) {
   tx_beam* b = new (std::nothrow) tx_beam();
   if (!b) { set_error("out of host memory"); return TX_ERR_OOM; }
   b->plan = p;
+  b->compact = compact;
   cudaGetDevice(&b->device);
-  cudaError_t e = cudaMalloc((void**)&b->ring, (size_t)p->nchan * p->R);
+  cudaError_t e = compact ? cudaMalloc((void**)&b->tail, std::max<size_t>((size_t)p->nchan * p->tail_pitch, 16))
+                          : cudaMalloc((void**)&b->ring, (size_t)p->nchan * p->R);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->run, (size_t)p->ndm * 2 * sizeof(double));
   if (e != cudaSuccess) {
     set_error("beam allocation failed: %s", cudaGetErrorString(e));
@@ -220,11 +235,22 @@ int32_t tx_beam_create(const tx_plan* p, tx_beam** out) {
   return TX_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int32_t tx_beam_create(const tx_plan* p, tx_beam** out) { return beam_create(p, out, 0); }
+
+int32_t tx_beam_create_compact(const tx_plan* p, tx_beam** out) { return beam_create(p, out, 1); }
+
 int32_t tx_beam_reset(const tx_plan* p, tx_beam* b, void* stream) {
   int rc = check_beam(p, b);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  TX_CUDA(cudaMemsetAsync(b->ring, 0, (size_t)p->nchan * p->R, st));
+  if (b->compact)
+    TX_CUDA(cudaMemsetAsync(b->tail, 0, (size_t)p->nchan * p->tail_pitch, st));
+  else
+    TX_CUDA(cudaMemsetAsync(b->ring, 0, (size_t)p->nchan * p->R, st));
   TX_CUDA(cudaMemsetAsync(b->run, 0, (size_t)p->ndm * 2 * sizeof(double), st));
   k_fill_run<<<(p->ndm + 255) / 256, 256, 0, st>>>(b->run, p->ndm);
   TX_CUDA(cudaGetLastError());
@@ -237,6 +263,21 @@ int32_t tx_beam_prime(const tx_plan* p, tx_beam* b, const uint8_t* d_tail, void*
   int rc = check_beam(p, b);
   if (rc) return rc;
   if (!d_tail && p->L > 0) { set_error("null tail"); return TX_ERR_INVALID_ARG; }
+  if (b->compact) {
+    if (p->L <= 0) return TX_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t* t = b->tail + p->tail_pad;
+    if (p->layout == TX_LAYOUT_TF) {
+      const int vec = (p->tail_pad % 16 == 0) && (p->nchan % 16 == 0) && (((uintptr_t)d_tail & 15) == 0);
+      dim3 grid((unsigned)((p->L + 63) / 64), (unsigned)((p->nchan + 63) / 64));
+      k_ingest_tf<<<grid, 256, 0, st>>>(d_tail, 0, p->L, p->nchan, b->tail, p->tail_pitch, p->tail_pad, vec);
+      TX_CUDA(cudaGetLastError());
+    } else {
+      TX_CUDA(cudaMemcpy2DAsync(t, (size_t)p->tail_pitch, d_tail, (size_t)p->L, (size_t)p->L, (size_t)p->nchan,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    return TX_OK;
+  }
   // the tail sits in the L positions before the next block
   return ingest(p, d_tail, p->L, b->ring, b->head - p->L, (cudaStream_t)stream);
 }
@@ -282,6 +323,7 @@ void tx_beam_destroy(tx_beam* b) {
   cudaGetDevice(&prev);
   if (b->device >= 0) cudaSetDevice(b->device);
   cudaFree(b->ring);
+  cudaFree(b->tail);
   cudaFree(b->run);
   cudaSetDevice(prev);
   delete b;
@@ -313,10 +355,21 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   TX_MARK(0);
 
   // Sec. 2.3 data flow: the block lands behind the carried tail (steps 1, 2, 4)
-  if ((rc = ingest(p, d_block, p->T, b->ring, b->head, st))) return rc;
   const int64_t start = mod(b->head - p->L, p->R);
   const BeamArgs a = make_args(p, b, d_block, d_out, d_ncand, d_workspace, b->head, start);
-  b->head = mod(b->head + p->T, p->R);
+  if (b->compact) {
+    // tail into the borrowed ring, the block behind it, the new tail back out
+    const int nunits = p->nchan * (int)((p->tail_pitch + 4095) / 4096);
+    const int tgrid = std::min(nunits, std::max(p->dev.num_sms, 1) * 8);
+    if (nunits > 0) k_tail<OneBeam><<<tgrid, 256, 0, st>>>(OneBeam{a}, 0, nullptr, nullptr, 1, nunits);
+    TX_CUDA(cudaGetLastError());
+    if ((rc = ingest(p, d_block, p->T, a.ring, a.head, st))) return rc;
+    if (nunits > 0) k_tail<OneBeam><<<tgrid, 256, 0, st>>>(OneBeam{a}, 1, nullptr, nullptr, 1, nunits);
+    TX_CUDA(cudaGetLastError());
+  } else {
+    if ((rc = ingest(p, d_block, p->T, b->ring, b->head, st))) return rc;
+    b->head = mod(b->head + p->T, p->R);
+  }
   TX_MARK(1);
 
   // stage 1
@@ -581,6 +634,7 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   a.d1 = d1;
   a.abase = abase;
   a.e2 = e2;
+  a.items = items;
   a.R = ld;
   a.start = 0;
   a.T = p->T;
@@ -604,7 +658,8 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
 #define TX_NA_S1(Q)                                                                                               \
   do {                                                                                                            \
     TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, uint16_t, OneBeam>, smem1));                           \
-    k_stage1<Q, uint16_t, OneBeam><<<grid1, kStage1Warps * 32, smem1, st>>>(OneBeam{a}, items, nitems, p->m, 1u); \
+    k_stage1<Q, uint16_t, OneBeam><<<grid1, kStage1Warps * 32, smem1, st>>>(OneBeam{a}, nullptr, nullptr, 1, nitems, \
+                                                                            p->m, 1u);                        \
   } while (0)
   switch (p->q1) {
     case 256: TX_NA_S1(256); break;

@@ -54,14 +54,17 @@ struct BeamArgs {
   const int32_t* abase;          // [nk][nsub]
   const int32_t* e2;             // [ndm][nsub]
   const int32_t* widths;         // [nw]
+  const Stage1Item* items;       // stage-1 work items of the plan
   float* outf;                   // cube / plane S/N
   uint8_t* outw;                 // plane best-width index
   tx_cand* cands;                // candidate records
   unsigned long long* ncand;     // candidate counter
+  uint8_t* tail;                 // compact beams: [nchan][tail_pitch] carried tail
   int64_t R, head, start, T, Pp, Dp, Td, max_cands;
+  int64_t L, tail_pitch;
   double lam, gamma;
   int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
-  int32_t layout, ingest_vec, running, output;
+  int32_t layout, ingest_vec, running, output, compact, tail_pad;
 };
 
 // Where a kernel finds a beam's arguments (the Src template parameter).
@@ -152,10 +155,11 @@ __global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t src_pitch, 
   }
 }
 
-// Loads a 64-time x 64-channel byte tile of a time-major block [t][nchan]
-// (times t0.., channels c0..) into tile[time][channel]; 256 threads.
-__device__ __forceinline__ void tf_load_tile(uint8_t (*tile)[80], const uint8_t* __restrict__ src, int64_t t0,
-                                             int64_t n, int c0, int nchan, int vec) {
+// This thread's 16 bytes of the 64-time x 64-channel byte tile (times t0..,
+// channels c0..) of a time-major block [t][nchan]: time t0 + tid / 4,
+// channels c0 + 16 (tid % 4) ..; zero outside the block. 256 threads.
+__device__ __forceinline__ uint4 tf_tile_chunk(const uint8_t* __restrict__ src, int64_t t0, int64_t n, int c0,
+                                               int nchan, int vec) {
   const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
   const int64_t t = t0 + r;
   const int c = c0 + 16 * q;
@@ -171,7 +175,14 @@ __device__ __forceinline__ void tf_load_tile(uint8_t (*tile)[80], const uint8_t*
       v = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
-  *reinterpret_cast<uint4*>(&tile[r][16 * q]) = v;
+  return v;
+}
+
+// Loads such a tile into tile[time][channel].
+__device__ __forceinline__ void tf_load_tile(uint8_t (*tile)[80], const uint8_t* __restrict__ src, int64_t t0,
+                                             int64_t n, int c0, int nchan, int vec) {
+  *reinterpret_cast<uint4*>(&tile[threadIdx.x >> 2][16 * (threadIdx.x & 3)]) =
+      tf_tile_chunk(src, t0, n, c0, nchan, vec);
 }
 
 // Column cc of a tile, times 16 pq .. 16 pq + 15, as four little-endian words.
@@ -218,7 +229,18 @@ template <typename Src>
 __global__ void __launch_bounds__(256) k_ingest_batch(const Src src, const int32_t* __restrict__ uoff,
                                                       const int32_t* __restrict__ umem, int nmem, int nunits) {
   __shared__ __align__(16) uint8_t tile[64][80];
-  MemberCursor cur;
+  MemberCursor cur, nxt;
+  // time-major tiles: this thread's 16 bytes of the block's next tile are loaded
+  // while the current tile is transposed and stored
+  uint4 pre = make_uint4(0u, 0u, 0u, 0u);
+  auto tf_fetch = [&](int u) {
+    nxt.seek(uoff, umem, nmem, u);
+    const BeamArgs b = src.get(nxt.beam);
+    if (b.layout != TX_LAYOUT_TF) return;
+    const int lu = u - nxt.lo, nct = (b.nchan + 63) >> 6;
+    pre = tf_tile_chunk(b.block, (int64_t)(lu / nct) * 64, b.T, (lu % nct) * 64, b.nchan, b.ingest_vec);
+  };
+  if ((int)blockIdx.x < nunits) tf_fetch(blockIdx.x);
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     cur.seek(uoff, umem, nmem, u);
     const int lu = u - cur.lo;
@@ -228,7 +250,8 @@ __global__ void __launch_bounds__(256) k_ingest_batch(const Src src, const int32
       const int64_t t0 = (int64_t)(lu / nct) * 64;
       const int c0 = (lu % nct) * 64;
       __syncthreads();  // the previous tile's readers are done with `tile`
-      tf_load_tile(tile, a.block, t0, a.T, c0, a.nchan, a.ingest_vec);
+      *reinterpret_cast<uint4*>(&tile[threadIdx.x >> 2][16 * (threadIdx.x & 3)]) = pre;
+      if (u + (int)gridDim.x < nunits) tf_fetch(u + gridDim.x);
       __syncthreads();
       const int cc = threadIdx.x & 63, pq = threadIdx.x >> 6;
       const int c = c0 + cc;
@@ -251,6 +274,7 @@ __global__ void __launch_bounds__(256) k_ingest_batch(const Src src, const int32
         }
       }
     } else {
+      if (u + (int)gridDim.x < nunits) tf_fetch(u + gridDim.x);
       const int nchunk = (int)((a.T + 4095) >> 12);
       const int c = lu / nchunk;
       const int64_t t = (int64_t)(lu - c * nchunk) * 4096 + 16 * threadIdx.x;
@@ -269,6 +293,48 @@ __global__ void __launch_bounds__(256) k_ingest_batch(const Src src, const int32
           }
         }
       }
+    }
+  }
+}
+
+// Compact beams: the carried tail moves between the beam's tail store
+// [nchan][tail_pitch] (samples at tail_pad + i) and the borrowed ring, where
+// it sits just before the block (ring positions head - L .. head - 1, head a
+// multiple of 64; the store and the ring share the 16-byte phase).
+//   dir 0, in:  ring[c][head - L - pad + j] = store[c][j], j < tail_pitch (the
+//               pad bytes land before the window, where nothing reads them
+//               into a sum);
+//   dir 1, out: store[c][pad + i] = ring[c][head - L + T + i], i < L: the last
+//               L samples of the buffer, the next block's tail.
+// 16-byte chunks throughout, except dir 1 when T is not a multiple of 16.
+// Units: (channel, 4096-byte chunk) of every member in turn; 256 threads.
+template <typename Src>
+__global__ void __launch_bounds__(256) k_tail(const Src src, int dir, const int32_t* __restrict__ uoff,
+                                              const int32_t* __restrict__ umem, int nmem, int nunits) {
+  MemberCursor cur;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    int lu = u;
+    BeamArgs a;
+    if constexpr (Src::kBatch) {
+      cur.seek(uoff, umem, nmem, u);
+      lu = u - cur.lo;
+      a = src.get(cur.beam);
+    } else {
+      a = src.get(0);
+    }
+    const int nchunk = (int)((a.tail_pitch + 4095) >> 12);
+    const int c = lu / nchunk;
+    const int64_t j = (int64_t)(lu - c * nchunk) * 4096 + 16 * threadIdx.x;
+    uint8_t* store = a.tail + (int64_t)c * a.tail_pitch;
+    uint8_t* ring = a.ring + (int64_t)c * a.R + (a.head - a.L - a.tail_pad);
+    if (j >= a.tail_pitch) continue;
+    if (dir == 0) {
+      *reinterpret_cast<uint4*>(ring + j) = *reinterpret_cast<const uint4*>(store + j);
+    } else if (a.T % 16 == 0) {
+      *reinterpret_cast<uint4*>(store + j) = *reinterpret_cast<const uint4*>(ring + a.T + j);
+    } else {
+      for (int64_t i = j; i < j + 16; ++i)
+        if (i >= a.tail_pad) store[i] = ring[a.T + i];
     }
   }
 }
@@ -342,8 +408,8 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 }
 
 // Persistent blocks walk the work items (sub-band s, coarse DMs [kb, ke),
-// absolute times [tau0, tau0 + 4Q)); in a batch, item field pad0 names the
-// beam. For each item the channels' input windows (from 16-byte aligned ring
+// absolute times [tau0, tau0 + 4Q)) of the plan, or in a batch the members'
+// items in turn (unit u of member j is item u - off[j] of its plan). For each item the channels' input windows (from 16-byte aligned ring
 // positions) are copied with cp.async into a raw buffer while the previous
 // item is being summed, then rearranged so that shared word S[c][j] holds
 // channel c's samples at raw offsets j + qQ in byte q (q = 0..3). For coarse
@@ -359,7 +425,8 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 // staged words or table.
 template <int Q, typename PT, typename Src>
 __global__ void __launch_bounds__(kStage1Warps * 32, 1)
-k_stage1(const Src src, const Stage1Item* __restrict__ items, int nitems, int mL, uint32_t unit) {
+k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nitems,
+         int mL, uint32_t unit) {
   extern __shared__ __align__(16) uint8_t smem1[];
   constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
@@ -376,9 +443,23 @@ k_stage1(const Src src, const Stage1Item* __restrict__ items, int nitems, int mL
     while (p >= a.R) p -= a.R;
     return (int)p;
   };
+  MemberCursor cur_c, cur_i;  // items being summed / being prefetched
+  auto locate = [&](MemberCursor& c, int u, Stage1Item& it) -> BeamArgs {
+    int lu = u;
+    BeamArgs a;
+    if constexpr (Src::kBatch) {
+      c.seek(uoff, umem, nmem, u);
+      lu = u - c.lo;
+      a = src.get(c.beam);
+    } else {
+      a = src.get(0);
+    }
+    it = a.items[lu];
+    return a;
+  };
   auto issue = [&](int idx) {
-    const Stage1Item it = items[idx];
-    const BeamArgs a = src.get(it.pad0);
+    Stage1Item it;
+    const BeamArgs a = locate(cur_i, idx, it);
     const int R = (int)a.R;
     for (int c = warp; c < a.m; c += kStage1Warps) {
       const int pa = wstart(a, it, c) & ~15;
@@ -396,8 +477,8 @@ k_stage1(const Src src, const Stage1Item* __restrict__ items, int nitems, int mL
   int idx = blockIdx.x;
   if (idx < nitems) issue(idx);
   while (idx < nitems) {
-    const Stage1Item it = items[idx];
-    const BeamArgs a = src.get(it.pad0);
+    Stage1Item it;
+    const BeamArgs a = locate(cur_c, idx, it);
     const int m = a.m;
     const int TS = (m + 3) & ~3;                 // offset-table row stride (16-byte aligned quads)
     const int c0 = it.s * m;
@@ -510,11 +591,8 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       return src.get(0);
     }
   };
-  auto issue = [&](int u, int ch, int buf) {
-    int lu;
-    const BeamArgs a = locate(cur_i, u, lu);
-    const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
-    const int64_t t0 = (int64_t)tile * 2 * NW;
+  // copies sub-band chunk ch of unit (k, tile) of beam a into even-copy buffer buf
+  auto issue_chunk = [&](const BeamArgs& a, int k, int64_t t0, int ch, int buf) {
     const int s0 = ch * a.SC, ns = min(a.SC, a.nsub - s0);
     const int nq = a.SWW >> 2;
     const uint16_t* P = static_cast<const uint16_t*>(a.P);
@@ -528,117 +606,124 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
     }
     cp_async_commit();
   };
+  auto issue_unit = [&](int u, int buf) {  // first chunk of unit u
+    int lu;
+    const BeamArgs a = locate(cur_i, u, lu);
+    const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
+    issue_chunk(a, k, (int64_t)tile * 2 * NW, 0, buf);
+  };
 
   uint32_t aw[VW], ah[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
-  int u = blockIdx.x, ch = 0, buf = 0;
-  if (u < nunits) issue(u, 0, 0);
-  while (u < nunits) {
+  int buf = 0;
+  if ((int)blockIdx.x < nunits) issue_unit(blockIdx.x, 0);
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     int lu;
-    const BeamArgs a = locate(cur_c, u, lu);
+    const BeamArgs a = locate(cur_c, u, lu);  // once per unit
     const int SC = a.SC, SWW = a.SWW, nsub = a.nsub;
     const int nchunk = (nsub + SC - 1) / SC;
     const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
     const int64_t t0 = (int64_t)tile * 2 * NW;
     const int dfirst = k * a.G;
     const int nd = min(a.G, a.ndm - dfirst);
-    const int s0 = ch * SC, ns = min(SC, nsub - s0);
-    uint32_t* cur = Se + (size_t)buf * slot;
-    cp_async_wait_all();
-    __syncthreads();
-    // odd copy: So[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged base
-    for (int ss = warp; ss < ns; ss += nwarps) {
-      const uint32_t* r = cur + (size_t)ss * SWW;
-      uint32_t* o = So + (size_t)ss * SWW;
-      for (int j = 4 * lane; j < SWW - 4; j += 128) {
-        const uint4 x = *reinterpret_cast<const uint4*>(r + j);
-        const uint32_t y = r[j + 4];
-        *reinterpret_cast<uint4*>(o + j) =
-            make_uint4(__funnelshift_r(x.x, x.y, 16), __funnelshift_r(x.y, x.z, 16), __funnelshift_r(x.z, x.w, 16),
-                       __funnelshift_r(x.w, y, 16));
+    for (int ch = 0; ch < nchunk; ++ch, buf ^= 1) {
+      const int s0 = ch * SC, ns = min(SC, nsub - s0);
+      uint32_t* cur = Se + (size_t)buf * slot;
+      cp_async_wait_all();
+      __syncthreads();
+      // odd copy: So[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged base
+      for (int ss = warp; ss < ns; ss += nwarps) {
+        const uint32_t* r = cur + (size_t)ss * SWW;
+        uint32_t* o = So + (size_t)ss * SWW;
+        for (int j = 4 * lane; j < SWW - 4; j += 128) {
+          const uint4 x = *reinterpret_cast<const uint4*>(r + j);
+          const uint32_t y = r[j + 4];
+          *reinterpret_cast<uint4*>(o + j) =
+              make_uint4(__funnelshift_r(x.x, x.y, 16), __funnelshift_r(x.y, x.z, 16), __funnelshift_r(x.z, x.w, 16),
+                         __funnelshift_r(x.w, y, 16));
+        }
       }
-    }
-    for (int gg = warp; gg < nd; gg += nwarps) {
-      for (int ss = lane; ss < ns; ss += 32) {
-        const int s = s0 + ss;
-        const int32_t emin = a.e2[(size_t)dfirst * nsub + s];
-        const int off = a.e2[(size_t)(dfirst + gg) * nsub + s] - emin + (int)((t0 + emin) & 7);
-        const uint32_t* base = (off & 1) ? So : cur;
-        tab[gg * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
+      for (int gg = warp; gg < nd; gg += nwarps) {
+        for (int ss = lane; ss < ns; ss += 32) {
+          const int s = s0 + ss;
+          const int32_t emin = a.e2[(size_t)dfirst * nsub + s];
+          const int off = a.e2[(size_t)(dfirst + gg) * nsub + s] - emin + (int)((t0 + emin) & 7);
+          const uint32_t* base = (off & 1) ? So : cur;
+          tab[gg * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
+        }
       }
-    }
-    __syncthreads();
-    int nu = u, nch = ch + 1;
-    if (nch == nchunk) { nu = u + gridDim.x; nch = 0; }
-    if (nu < nunits) issue(nu, nch, buf ^ 1);
+      __syncthreads();
+      // prefetch the next chunk: of this unit, else the first of the block's next unit
+      if (ch + 1 < nchunk) {
+        issue_chunk(a, k, t0, ch + 1, buf ^ 1);
+      } else if (u + (int)gridDim.x < nunits) {
+        issue_unit(u + gridDim.x, buf ^ 1);
+      }
 
-    if (g < nd) {
-      const uint32_t* t = tab + g * SC;
-      const uint32_t* Sl = smem2 + jbase + lane;
-      int ss = 0;
-#pragma unroll 2
-      for (; ss + 1 < ns; ss += 2) {
-        const uint32_t* r0 = Sl + t[ss];
-        const uint32_t* r1 = Sl + t[ss + 1];
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
-          aw[v] += w0 + w1;
-          madd_hi16(ah[v], w0);
-          madd_hi16(ah[v], w1);
-        }
-      }
-      if (ss < ns) {
-        const uint32_t* r0 = Sl + t[ss];
-#pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          const uint32_t w0 = r0[32 * v];
-          aw[v] += w0;
-          madd_hi16(ah[v], w0);
-        }
-      }
-    }
-    if (ch == nchunk - 1) {
-      long long s1 = 0;
-      unsigned long long s2 = 0;
       if (g < nd) {
-        const int d = dfirst + g;
-        int32_t* drow = a.D + (size_t)d * a.Dp;
+        const uint32_t* t = tab + g * SC;
+        const uint32_t* Sl = smem2 + jbase + lane;
+        int ss = 0;
+#pragma unroll 2
+        for (; ss + 1 < ns; ss += 2) {
+          const uint32_t* r0 = Sl + t[ss];
+          const uint32_t* r1 = Sl + t[ss + 1];
 #pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          const int64_t ta = t0 + 2 * (jbase + lane + 32 * v);
-          const uint32_t lo = aw[v] - (ah[v] << 16), hi = ah[v];
-          if (ta + 1 < a.Td && (a.Dp & 1) == 0) {
-            *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
-          } else {
-            if (ta < a.Td) drow[ta] = (int32_t)lo;
-            if (ta + 1 < a.Td) drow[ta + 1] = (int32_t)hi;
+          for (int v = 0; v < VW; ++v) {
+            const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+            aw[v] += w0 + w1;
+            madd_hi16(ah[v], w0);
+            madd_hi16(ah[v], w1);
           }
-          if (ta < a.T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
-          if (ta + 1 < a.T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
         }
-      }
+        if (ss < ns) {
+          const uint32_t* r0 = Sl + t[ss];
 #pragma unroll
-      for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
-      warp_sum_stats(s1, s2);
-      if (SPLIT == 1) {
-        if (g < nd && lane == 0) a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(s1, (long long)s2);
-      } else {
-        // combine the parts of each fine DM in a fixed order (deterministic sums)
-        if (lane == 0) { st1[warp] = s1; st2[warp] = s2; }
-        __syncthreads();
-        if (part_i == 0 && g < nd && lane == 0) {
-          long long x = 0;
-          unsigned long long y = 0;
-          for (int i = 0; i < SPLIT; ++i) { x += st1[warp + i]; y += st2[warp + i]; }
-          a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(x, (long long)y);
+          for (int v = 0; v < VW; ++v) {
+            const uint32_t w0 = r0[32 * v];
+            aw[v] += w0;
+            madd_hi16(ah[v], w0);
+          }
         }
       }
     }
-    u = nu;
-    ch = nch;
-    buf ^= 1;
+    // the unit's sums are complete: store the series and the tile's exact sums
+    long long s1 = 0;
+    unsigned long long s2 = 0;
+    if (g < nd) {
+      const int d = dfirst + g;
+      int32_t* drow = a.D + (size_t)d * a.Dp;
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        const int64_t ta = t0 + 2 * (jbase + lane + 32 * v);
+        const uint32_t lo = aw[v] - (ah[v] << 16), hi = ah[v];
+        if (ta + 1 < a.Td && (a.Dp & 1) == 0) {
+          *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
+        } else {
+          if (ta < a.Td) drow[ta] = (int32_t)lo;
+          if (ta + 1 < a.Td) drow[ta + 1] = (int32_t)hi;
+        }
+        if (ta < a.T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
+        if (ta + 1 < a.T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+    warp_sum_stats(s1, s2);
+    if (SPLIT == 1) {
+      if (g < nd && lane == 0) a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(s1, (long long)s2);
+    } else {
+      // combine the parts of each fine DM in a fixed order (deterministic sums)
+      if (lane == 0) { st1[warp] = s1; st2[warp] = s2; }
+      __syncthreads();
+      if (part_i == 0 && g < nd && lane == 0) {
+        long long x = 0;
+        unsigned long long y = 0;
+        for (int i = 0; i < SPLIT; ++i) { x += st1[warp + i]; y += st2[warp + i]; }
+        a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(x, (long long)y);
+      }
+    }
   }
 }
 
@@ -1018,7 +1103,8 @@ inline int stage2_split(const tx_plan* p) { return p->split2; }
 inline int stage2_threads(const tx_plan* p) { return std::min(p->group, kStage2MaxGroup) * 32 * stage2_split(p); }
 
 // The arguments of one execute of plan p on beam b: the block lands at ring
-// position `head`, buffer time 0 sits at `start`; ws is the execute's
+// position `head`, buffer time 0 sits at `start` (a compact beam uses its
+// borrowed ring instead: head0 and head0 - L); ws is the execute's
 // workspace; out / ncand as tx_execute.
 inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* block, void* out, int64_t* ncand,
                           void* ws_ptr, int64_t head, int64_t start) {
@@ -1027,6 +1113,16 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   BeamArgs a{};
   a.block = block;
   a.ring = b->ring;
+  if (b->compact) {  // a fresh linear window in the workspace: tail, then the block at head0
+    a.ring = ws + p->ws_ring;
+    head = p->head0;
+    start = p->head0 - p->L;
+    a.tail = b->tail;
+    a.compact = 1;
+  }
+  a.L = p->L;
+  a.tail_pitch = p->tail_pitch;
+  a.tail_pad = (int32_t)p->tail_pad;
   a.P = ws + p->ws_P;
   a.D = series ? static_cast<int32_t*>(out) : reinterpret_cast<int32_t*>(ws + p->ws_D);
   a.part = reinterpret_cast<longlong2*>(ws + p->ws_part);
@@ -1036,6 +1132,7 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.abase = p->dev.abase;
   a.e2 = p->dev.e2;
   a.widths = p->dev.widths;
+  a.items = p->dev.items1;
   a.outf = static_cast<float*>(out);
   a.outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(out) + (size_t)p->ndm * p->T * 4 : nullptr;
   a.cands = static_cast<tx_cand*>(out);

@@ -280,6 +280,11 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
     default: p->out_bytes = (int64_t)ndm * p->Td * 4; break;
   }
   p->beam_bytes = (int64_t)nchan * p->R + (int64_t)ndm * 16 + 16;
+  p->tail_pad = (16 - p->L % 16) % 16;
+  p->tail_pitch = p->L + p->tail_pad;
+  p->ws_ring = p->ws_bytes;
+  p->ws_bytes_compact = round_up(p->ws_ring + (int64_t)nchan * p->R, 256);
+  p->compact_beam_bytes = (int64_t)nchan * p->tail_pitch + (int64_t)ndm * 16 + 16;
   p->export_bytes = 64 + (int64_t)nchan * p->L + (int64_t)ndm * 16;
   return TX_OK;
 }
@@ -332,6 +337,8 @@ int32_t tx_plan_get_info(const tx_plan* p, tx_plan_info* info) {
   info->ring_head0 = p->head0;
   info->tile_q1 = p->q1;
   info->tile_split2 = p->split2;
+  info->workspace_bytes_compact = p->ws_bytes_compact;
+  info->compact_beam_state_bytes = p->compact_beam_bytes;
   return TX_OK;
 }
 

@@ -113,6 +113,10 @@ struct tx_plan {
   // ---- workspace carve-up (bytes) -------------------------------------------
   int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_bytes = 0;
   int64_t out_bytes = 0, beam_bytes = 0, export_bytes = 0;
+  // compact beams: the tail lives in [nchan][tail_pitch] (samples at
+  // tail_pad.. so that they share the ring's 16-byte phase); an execute
+  // borrows the ring from the workspace at ws_ring
+  int64_t tail_pad = 0, tail_pitch = 0, ws_ring = 0, ws_bytes_compact = 0, compact_beam_bytes = 0;
 
   // ---- device copy, uploaded once ------------------------------------------
   std::once_flag dev_once;
@@ -123,7 +127,9 @@ struct tx_plan {
 struct tx_beam {
   const tx_plan* plan = nullptr;
   int device = -1;
-  uint8_t* ring = nullptr;        // [nchan][R] circular
+  int compact = 0;                // tail store instead of a resident ring
+  uint8_t* ring = nullptr;        // [nchan][R] circular (full beams)
+  uint8_t* tail = nullptr;        // [nchan][tail_pitch] carried tail (compact beams)
   int64_t head = 0;               // where the next block lands
   double* run = nullptr;          // [ndm][2] running (mu, var); var < 0 = unset
   int64_t nblocks = 0;

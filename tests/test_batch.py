@@ -68,12 +68,14 @@ def same(a, b):
     return np.array_equal(a, b)
 
 
-def run_pair(tx, specs, graph, budget, profile=False):
+def run_pair(tx, specs, graph, budget, profile=False, compact=()):
+    """Beams in the batch (compact ones at the indices in `compact`) against
+    full beams run alone, block by block."""
     plans = [make_plan(tx, s) for s in specs]
     rng = np.random.default_rng(11)
     streams = [rng.integers(0, 256, size=(p.nchan, p.overlap + NSTEPS * p.nsamp), dtype=np.uint8) for p in plans]
     solo = [tx.Beam(p) for p in plans]
-    mixed = [tx.Beam(p) for p in plans]
+    mixed = [tx.Beam(p, compact=i in compact) for i, p in enumerate(plans)]
     for p, X, b1, b2 in zip(plans, streams, solo, mixed):
         tail = torch.from_numpy(to_layout(X[:, :p.overlap], p.layout)).cuda()
         b1.prime(tail)
@@ -113,6 +115,13 @@ def test_batch_in_waves_under_budget(tx):
     batch, _ = run_pair(tx, BEAMS, graph=True, budget=budget)
     assert batch.nwaves > 1
     assert batch.workspace_bytes <= budget
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_with_compact_beams(tx, graph):
+    """Compact beams (tail resident, buffer borrowed from the batch workspace)
+    mixed with full ones give the full beams' results."""
+    run_pair(tx, BEAMS, graph, budget=0, compact=(1, 2, 4, 6))
 
 
 def test_batch_profile_times_every_phase(tx):

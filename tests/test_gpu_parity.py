@@ -351,3 +351,58 @@ def test_tile_shapes_do_not_change_results(tx, q1, split):
     (out, _, _), = run_blocks(tx, plan, X)[0]
     got = tx.series_view(plan, out).cpu().numpy()
     assert np.array_equal(got, O.subband_dedisperse(X, op, plan.series_len))
+
+
+@pytest.mark.parametrize("layout", ["ft", "tf"])
+@pytest.mark.parametrize("cfg", [TINY[2], TINY[3], TINY[7], dict(nchan=64, nsub=8, ndm=20, nsamp=4096, dm_max=90.0)])
+def test_compact_beam_equals_full_beam(tx, cfg, layout):
+    """A compact beam (tail resident, buffer borrowed from the workspace) gives
+    exactly the full beam's outputs, block after block; odd L and T exercise
+    the tail store's padding and its byte-wise copy."""
+    wl = synth.tiny_workload(**cfg)
+    for output in ("series", "cands"):
+        plan = make_plan(tx, wl, output=output, layout=layout, snr_threshold=3.0)
+        L, T = plan.overlap, plan.nsamp
+        X = rand_stream(wl.nchan, L + 3 * T, seed=91)
+        full, comp = tx.Beam(plan), tx.Beam(plan, compact=True)
+        tail = torch.from_numpy(to_layout(X[:, :L], layout)).cuda()
+        full.prime(tail)
+        comp.prime(tail)
+        wsf, wsc = plan.alloc_workspace(), plan.alloc_workspace(compact=True)
+        for b in range(3):
+            blk = torch.from_numpy(to_layout(X[:, L + b * T:L + (b + 1) * T], layout)).cuda()
+            res = []
+            for beam, ws in ((full, wsf), (comp, wsc)):
+                out, nc = plan.alloc_out()
+                tx.execute(plan, beam, blk, out=out, ncand=nc, workspace=ws)
+                torch.cuda.synchronize()
+                if output == "cands":
+                    rec, n = tx.cands_view(plan, out, nc)
+                    res.append((n, np.sort(rec, order=("dm_index", "t"))))
+                else:
+                    res.append(out.cpu().numpy())
+            if output == "cands":
+                assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1]), f"block {b}"
+            else:
+                assert np.array_equal(res[0], res[1]), f"block {b}"
+        # the checkpoint of a compact beam is the full beam's
+        assert full.export() == comp.export()
+
+
+def test_compact_beam_checkpoint_restore(tx):
+    wl = synth.tiny_workload(nchan=64, nsub=8, ndm=20, nsamp=1000, dm_max=90.0)
+    plan = make_plan(tx, wl, output="series")
+    L, T = plan.overlap, plan.nsamp
+    X = rand_stream(wl.nchan, L + 3 * T, seed=92)
+    a = tx.Beam(plan, compact=True)
+    a.prime(torch.from_numpy(np.ascontiguousarray(X[:, :L])).cuda())
+    ws = plan.alloc_workspace(compact=True)
+    blk = [torch.from_numpy(np.ascontiguousarray(X[:, L + i * T:L + (i + 1) * T])).cuda() for i in range(3)]
+    tx.execute(plan, a, blk[0], workspace=ws)
+    state = a.export()
+    ref = [tx.execute(plan, a, blk[i], workspace=ws).cpu().numpy() for i in (1, 2)]
+    b = tx.Beam(plan, compact=True)
+    b.import_(state)
+    got = [tx.execute(plan, b, blk[i], workspace=ws).cpu().numpy() for i in (1, 2)]
+    assert all(np.array_equal(x, y) for x, y in zip(ref, got))
+    assert b.nblocks == 3

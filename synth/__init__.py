@@ -20,6 +20,8 @@ Workloads (the paper's benchmark simulates MMGPS-L-like data at 153 us, Sec. 3):
   channels in {1024, 2048, 4096}, blocks in {32768, 65536, 131072} samples,
   {1024, 4096, 8192} DM trials over 0-3000 (four doubling-step segments),
   widths 1..256, a few pulses per beam; drawn with a fixed seed.
+* ``serving``    -- 480 beams, every other one MeerKAT-L-like and the rest
+  drawn like the batched beams.
 """
 from __future__ import annotations
 
@@ -158,6 +160,17 @@ def batched_workloads(nbeams: int = 64, seed: int = 3, dm_max: float = 3000.0) -
             noise_mean=128.0,
             noise_std=12.0,
         ))
+    return out
+
+
+def serving_workloads(nbeams: int = 480, seed: int = 4) -> list:
+    """Beams of a served stream: half MeerKAT-L-like, half drawn like the batched beams."""
+    drawn = batched_workloads(nbeams - nbeams // 2, seed=seed)
+    out = []
+    for i in range(nbeams):
+        wl = meerkat_l_workload() if i % 2 == 0 else drawn[i // 2]
+        wl.name = f"beam{i}-" + wl.name.split("-", 1)[-1] if i % 2 else f"beam{i}-{wl.name}"
+        out.append(wl)
     return out
 
 

@@ -164,21 +164,23 @@ class ClockSampler:
 
 
 def kernels_sha():
+    """Hash of the kernel sources (kernels.cuh) and the single-beam launcher (kernels.cu)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2401_13834_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
+    for f in ("kernels.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2401_13834_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if taken on this kernels.cu."""
+    """DRAM bytes per launch from a committed ncu summary, if taken on these kernel sources."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"dram_bytes_per_launch:\s*([\d.eE+]+)", txt)
-    s = re.search(r"kernels_cu_sha256_16:\s*([0-9a-f]+)", txt)
+    s = re.search(r"kernels_src_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or not s or s.group(1) != kernels_sha():
         return None
     return float(m.group(1))

@@ -74,7 +74,13 @@ enum tx_layout { TX_LAYOUT_FT = 0,   /* block is channel-major  uint8 [nchan][T]
                                         Sec. 2.3 data-flow step 2)                   */
 enum tx_interm { TX_INTERM_U16 = 0,  /* stage-1 sums stored as uint16 (exact for
                                         nchan/nsub <= 257)                          */
-                 TX_INTERM_I32 = 1 };/* stored as int32                              */
+                 TX_INTERM_I32 = 1,  /* stored as int32                              */
+                 TX_INTERM_F16 = 2 };/* stored as FP16 after subtracting an integer
+                                        offset per sub-band (the sum of its channels'
+                                        rounded block means), rounded to nearest even
+                                        and saturated at +-65504; stage 2 sums the
+                                        halves in FP32 and adds the offsets back.
+                                        Exact while |sum - offset| <= 2048.         */
 enum tx_output { TX_OUT_CANDS  = 0,  /* tx_cand records, S/N >= snr_threshold        */
                  TX_OUT_PLANE  = 1,  /* float32 [ndm][T] best S/N, then uint8 [ndm][T]
                                         index of the best width                      */

@@ -215,6 +215,48 @@ def subband_dedisperse(X: np.ndarray, plan: SubbandPlan, nout: int, dm_indices=N
     return D
 
 
+def half_offsets(X: np.ndarray, plan: SubbandPlan, block: slice) -> np.ndarray:
+    """Integer offset per sub-band for half-precision stage-1 storage:
+    o_s = sum over the channels c of s of rnd(mean of X[c] over the block's
+    samples), each mean rounded half up (an integer, so subtracting it and
+    adding it back is exact). Returns int64 [nsub]."""
+    Xb = np.asarray(X[:, block], dtype=np.int64)
+    T = Xb.shape[1]
+    sums = Xb.sum(axis=1)
+    means = (2 * sums + T) // (2 * T)           # rnd(sum / T), half up, for sum >= 0
+    return means.reshape(plan.nsub, plan.m).sum(axis=1)
+
+
+def subband_dedisperse_f16(X: np.ndarray, plan: SubbandPlan, nout: int, block: slice, dm_indices=None):
+    """The sub-band scheme of Sec. 2.3 with the stage-1 sums kept at half
+    precision (the FP16 form): P'[k][s] = P[k][s] - o_s (o_s from
+    half_offsets over `block`) rounded to the nearest FP16 (ties to even),
+    saturated at +-65504; stage 2 adds the halves in float64 and then the
+    offsets back: D = sum_s (half(P') + o_s). Returns float64 [len(dm)][nout]
+    (integer-valued: every FP16 value of an integer is an integer)."""
+    if dm_indices is None:
+        dm_indices = range(plan.ndm)
+    dm_indices = list(dm_indices)
+    off = half_offsets(X, plan, block)
+    D = np.zeros((len(dm_indices), nout), dtype=np.float64)
+    cache = {}
+    for i, d in enumerate(dm_indices):
+        k = int(plan.coarse_of_fine[d])
+        if k not in cache:
+            ds = list(plan.fine_dms_of(k))
+            cache.clear()
+            cache[k] = []
+            for s in range(plan.nsub):
+                P = stage1(X, plan, k, s, nout + int(plan.d2[ds, s].max())).astype(np.float64)
+                h = np.clip(P - float(off[s]), -65504.0, 65504.0).astype(np.float16)
+                cache[k].append(h.astype(np.float64))
+        for s in range(plan.nsub):
+            o = int(plan.d2[d, s])
+            D[i] += cache[k][s][o:o + nout]
+        D[i] += float(off.sum())
+    return D
+
+
 # ----------------------------------------------------------------------------
 # Boxcar matched filter, Sec. 2.4 and Eq. 5
 # ----------------------------------------------------------------------------

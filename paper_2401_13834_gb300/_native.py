@@ -10,7 +10,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_lib", "libtransientx_gb300.so")
 
 LAYOUTS = {"ft": 0, "tf": 1}
-INTERMS = {"u16": 0, "i32": 1}
+INTERMS = {"u16": 0, "i32": 1, "f16": 2}
 OUTPUTS = {"cands": 0, "plane": 1, "cube": 2, "series": 3}
 STATS = {"block": 0, "running": 1}
 

@@ -58,9 +58,12 @@ bool g_slot_used[kMaxDevices][kArgSlots] = {};
 // Launch kinds: the first five are the phases (TX_PHASE_* order); the compact
 // beams' tail copies count as ingest.
 enum LaunchKind { kIngest = TX_PHASE_INGEST, kStage1 = TX_PHASE_STAGE1, kStage2 = TX_PHASE_STAGE2,
-                  kStats = TX_PHASE_STATS, kBoxcar = TX_PHASE_BOXCAR, kTailIn = 5, kTailOut = 6 };
+                  kStats = TX_PHASE_STATS, kBoxcar = TX_PHASE_BOXCAR, kTailIn = 5, kTailOut = 6, kOffsets = 7 };
 
-int phase_of(int kind) { return kind == kTailIn || kind == kTailOut ? TX_PHASE_INGEST : kind; }
+// compact beams' tail copies count as ingest, half intermediates' offsets as stage 1
+int phase_of(int kind) {
+  return kind == kTailIn || kind == kTailOut ? TX_PHASE_INGEST : kind == kOffsets ? TX_PHASE_STAGE1 : kind;
+}
 
 // Workspace of one execute on beam b of plan p.
 int64_t beam_ws(const tx_plan* p, const tx_beam* b) { return b->compact ? p->ws_bytes_compact : p->ws_bytes; }
@@ -69,7 +72,7 @@ int64_t beam_ws(const tx_plan* p, const tx_beam* b) { return b->compact ? p->ws_
 struct BatchLaunch {
   int kind = 0;
   int wave = 0;
-  int q1 = 0, split = 0, nwc = 0, mode = 0;  // template selectors
+  int q1 = 0, split = 0, nwc = 0, mode = 0, half = 0;  // template selectors
   int grid = 0, threads = 0, smem = 0;
   int nmem = 0, nunits = 0;                  // member beams, work units (stage 1: the plans' items)
   int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
@@ -112,20 +115,27 @@ const void* launch_kernel(const BatchLaunch& L) {
     case kIngest: return (const void*)k_ingest_batch<SlotArgs>;
     case kTailIn:
     case kTailOut: return (const void*)k_tail<SlotArgs>;
+    case kOffsets: return (const void*)k_offsets<SlotArgs>;
     case kStage1:
+#define TX_K1(Q) (L.half ? (const void*)k_stage1<Q, uint16_t, SlotArgs, true> : (const void*)k_stage1<Q, uint16_t, SlotArgs>)
       switch (L.q1) {
-        case 256: return (const void*)k_stage1<256, uint16_t, SlotArgs>;
-        case 128: return (const void*)k_stage1<128, uint16_t, SlotArgs>;
-        case 64: return (const void*)k_stage1<64, uint16_t, SlotArgs>;
-        default: return (const void*)k_stage1<32, uint16_t, SlotArgs>;
+        case 256: return TX_K1(256);
+        case 128: return TX_K1(128);
+        case 64: return TX_K1(64);
+        default: return TX_K1(32);
       }
+#undef TX_K1
     case kStage2:
+#define TX_K2(NW, SP)                                                        \
+  (L.half ? (const void*)k_stage2_u16<NW, 32, SP, SlotArgs, true>            \
+          : (const void*)k_stage2_u16<NW, 32, SP, SlotArgs, false>)
       switch (L.split) {
-        case 8: return (const void*)k_stage2_u16<512, 32, 8, SlotArgs>;
-        case 4: return (const void*)k_stage2_u16<512, 32, 4, SlotArgs>;
-        case 2: return (const void*)k_stage2_u16<512, 32, 2, SlotArgs>;
-        default: return (const void*)k_stage2_u16<256, 32, 1, SlotArgs>;
+        case 8: return TX_K2(512, 8);
+        case 4: return TX_K2(512, 4);
+        case 2: return TX_K2(512, 2);
+        default: return TX_K2(256, 1);
       }
+#undef TX_K2
     case kStats: return (const void*)k_stats<SlotArgs>;
     default: return (const void*)box_kernel<SlotArgs>(L.nwc, L.mode);
   }
@@ -216,19 +226,36 @@ int build_batch(tx_batch* B, int64_t budget) {
     }
     // ---- compact beams: the new tails out ------------------------------------------
     if (!compact.empty() && (rc = tail_launch(kTailOut))) return rc;
+    // ---- half intermediates: the block's per-sub-band offsets (ingest zeroed them) ----
+    {
+      std::vector<int> hm;
+      for (int b : mem)
+        if (B->plans[b]->interm == TX_INTERM_F16) hm.push_back(b);
+      if (!hm.empty()) {
+        BatchLaunch L;
+        L.kind = kOffsets;
+        L.wave = wv;
+        if ((rc = add_members(L, hm, first, [&](int b) -> int64_t { return B->plans[b]->nchan; }))) return rc;
+        L.threads = 256;
+        L.grid = std::min(L.nunits, nsm * 8);
+        B->launches.push_back(L);
+      }
+    }
     // ---- stage 1, one launch per (tile length, channels per sub-band): the shared
     // memory of a launch is laid out for its largest sub-band, and a mix would
     // take carve-out from L1 for the smaller ones
-    std::map<std::pair<int, int>, std::vector<int>> by_q;
-    for (int b : mem) by_q[{B->plans[b]->q1, B->plans[b]->m}].push_back(b);
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_q;
+    for (int b : mem)
+      by_q[{B->plans[b]->q1, B->plans[b]->m, B->plans[b]->interm == TX_INTERM_F16}].push_back(b);
     for (auto& kv : by_q) {
       BatchLaunch L;
       L.kind = kStage1;
       L.wave = wv;
-      L.q1 = kv.first.first;
+      L.q1 = std::get<0>(kv.first);
+      L.half = std::get<2>(kv.first);
       if ((rc = add_members(L, kv.second, first, [&](int b) -> int64_t { return (int64_t)B->plans[b]->items1.size(); })))
         return rc;
-      L.layout = kv.first.second;  // channels per sub-band of every member
+      L.layout = std::get<1>(kv.first);  // channels per sub-band of every member
       const int mL = L.layout;
       L.smem = (int)stage1_smem_bytes(mL, L.q1);
       if (L.smem > kSmemMax) { set_error("stage-1 shared memory for %d channels per sub-band exceeds the limit", mL); return TX_ERR_UNSUPPORTED; }
@@ -240,9 +267,10 @@ int build_batch(tx_batch* B, int64_t budget) {
     // Shared memory is laid out for the largest staged chunk and table of the
     // launch (which the plans size to fit, with room for the static sums); a
     // block as large as its largest group would idle warps of smaller groups.
-    std::map<std::tuple<int, int, int>, std::vector<int>> by_split;
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_split;
     for (int b : mem)
-      by_split[{stage2_split(B->plans[b]), B->plans[b]->nsub_chunk2, stage2_threads(B->plans[b])}].push_back(b);
+      by_split[{stage2_split(B->plans[b]), B->plans[b]->nsub_chunk2, stage2_threads(B->plans[b]),
+                B->plans[b]->interm == TX_INTERM_F16}].push_back(b);
     auto s2_smem = [&](const std::vector<int>& g) {
       int slot = 0, sc = 0;
       for (int b : g) {
@@ -251,13 +279,12 @@ int build_batch(tx_batch* B, int64_t budget) {
       }
       return std::make_pair(slot, stage2_u16_smem_for(slot, sc));
     };
-    std::vector<std::pair<int, std::vector<int>>> s2groups;
-    for (auto& kv : by_split) s2groups.push_back({std::get<0>(kv.first), kv.second});
-    for (auto& kv : s2groups) {
+    for (auto& kv : by_split) {
       BatchLaunch L;
       L.kind = kStage2;
       L.wave = wv;
-      L.split = kv.first;
+      L.split = std::get<0>(kv.first);
+      L.half = std::get<3>(kv.first);
       if ((rc = add_members(L, kv.second, first,
                             [&](int b) -> int64_t { return (int64_t)B->plans[b]->nk * B->plans[b]->ntile2; })))
         return rc;
@@ -374,10 +401,19 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
       case kTailOut:
         k_tail<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, L.kind == kTailOut, off, mem, L.nmem, L.nunits);
         break;
+      case kOffsets:
+        k_offsets<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, off, mem, L.nmem, L.nunits);
+        break;
       case kStage1: {
-#define TX_B1(Q)                                                                                          \
-  k_stage1<Q, uint16_t, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits, L.layout, \
-                                                                     1u)
+#define TX_B1(Q)                                                                                                \
+  do {                                                                                                           \
+    if (L.half)                                                                                                  \
+      k_stage1<Q, uint16_t, SlotArgs, true><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits,   \
+                                                                               L.layout, 1u);                    \
+    else                                                                                                         \
+      k_stage1<Q, uint16_t, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits,         \
+                                                                         L.layout, 1u);                          \
+  } while (0)
         switch (L.q1) {
           case 256: TX_B1(256); break;
           case 128: TX_B1(128); break;
@@ -388,9 +424,15 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
         break;
       }
       case kStage2:
-#define TX_B2(NW, SP)                                                                                     \
-  k_stage2_u16<NW, 32, SP, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits, \
-                                                                        L.layout)
+#define TX_B2(NW, SP)                                                                                          \
+  do {                                                                                                         \
+    if (L.half)                                                                                                \
+      k_stage2_u16<NW, 32, SP, SlotArgs, true><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem,       \
+                                                                                  L.nunits, L.layout);         \
+    else                                                                                                       \
+      k_stage2_u16<NW, 32, SP, SlotArgs, false><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem,      \
+                                                                                   L.nunits, L.layout);        \
+  } while (0)
         switch (L.split) {
           case 8: TX_B2(512, 8); break;
           case 4: TX_B2(512, 4); break;
@@ -443,7 +485,7 @@ int32_t tx_batch_create(int32_t n, const tx_plan* const* plans, tx_beam* const* 
     if (!p || !b) { set_error("null plan or beam at %d", i); return TX_ERR_INVALID_ARG; }
     if (b->plan != p) { set_error("beam %d was created for another plan", i); return TX_ERR_INVALID_ARG; }
     if (b->device != dev) { set_error("beam %d lives on device %d, current device is %d", i, b->device, dev); return TX_ERR_INVALID_ARG; }
-    if (p->interm != TX_INTERM_U16) { set_error("batched execute needs uint16 intermediates (beam %d)", i); return TX_ERR_UNSUPPORTED; }
+    if (p->interm == TX_INTERM_I32) { set_error("batched execute needs 16-bit intermediates (beam %d)", i); return TX_ERR_UNSUPPORTED; }
     for (int j = 0; j < i; ++j)
       if (beams[j] == b) { set_error("beam %d appears twice in the batch", i); return TX_ERR_INVALID_ARG; }
     int rc = tx_upload_plan(p);

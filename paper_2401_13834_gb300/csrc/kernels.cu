@@ -36,23 +36,34 @@ int upload(T** dst, const std::vector<T>& v) {
   return TX_OK;
 }
 
+// 16-bit intermediates (uint16 or half) share the staging kernels
+bool is16(const tx_plan* p) { return p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16; }
+
 int stage2_smem(const tx_plan* p) {
-  if (p->interm == TX_INTERM_U16) return stage2_u16_smem_for(p->nsub_chunk2 * p->sww2, p->nsub_chunk2);
+  if (is16(p)) return stage2_u16_smem_for(p->nsub_chunk2 * p->sww2, p->nsub_chunk2);
   return p->nsub_chunk2 * p->sw2_i32 * 4;
 }
 
 int box_smem(const tx_plan* p) { return box_smem_for(p->wmax); }
 
-template <int Q, typename PT>
+template <int Q, typename PT, bool HALF = false>
 int set_stage1_attr(int bytes) {
-  TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, PT, OneBeam>, bytes));
+  TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, PT, OneBeam, HALF>, bytes));
   return TX_OK;
 }
 
 template <int NW, int MAXWARPS, int SPLIT>
 int set_stage2_attr(int bytes) {
-  TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, MAXWARPS, SPLIT, OneBeam>, bytes));
+  TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, MAXWARPS, SPLIT, OneBeam, false>, bytes));
+  TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, MAXWARPS, SPLIT, OneBeam, true>, bytes));
   return TX_OK;
+}
+
+template <int Q>
+int set_stage1_attr_for(const tx_plan* p, int bytes) {
+  if (p->interm == TX_INTERM_F16) return set_stage1_attr<Q, uint16_t, true>(bytes);
+  if (p->interm == TX_INTERM_U16) return set_stage1_attr<Q, uint16_t>(bytes);
+  return set_stage1_attr<Q, int32_t>(bytes);
 }
 
 int do_upload(tx_plan* p) {
@@ -67,16 +78,15 @@ int do_upload(tx_plan* p) {
   if ((rc = upload(&p->dev.widths, p->widths))) return rc;
   if ((rc = upload(&p->dev.items1, p->items1))) return rc;
   const int s1 = (int)stage1_smem_bytes(p->m, p->q1);
-  const bool u16 = p->interm == TX_INTERM_U16;
   switch (p->q1) {
-    case 256: rc = u16 ? set_stage1_attr<256, uint16_t>(s1) : set_stage1_attr<256, int32_t>(s1); break;
-    case 128: rc = u16 ? set_stage1_attr<128, uint16_t>(s1) : set_stage1_attr<128, int32_t>(s1); break;
-    case 64: rc = u16 ? set_stage1_attr<64, uint16_t>(s1) : set_stage1_attr<64, int32_t>(s1); break;
-    default: rc = u16 ? set_stage1_attr<32, uint16_t>(s1) : set_stage1_attr<32, int32_t>(s1); break;
+    case 256: rc = set_stage1_attr_for<256>(p, s1); break;
+    case 128: rc = set_stage1_attr_for<128>(p, s1); break;
+    case 64: rc = set_stage1_attr_for<64>(p, s1); break;
+    default: rc = set_stage1_attr_for<32>(p, s1); break;
   }
   if (rc) return rc;
   const int s2 = stage2_smem(p);
-  if (u16) {
+  if (is16(p)) {
     switch (stage2_split(p)) {
       case 8: rc = set_stage2_attr<512, 32, 8>(s2); break;
       case 4: rc = set_stage2_attr<512, 32, 4>(s2); break;
@@ -98,12 +108,19 @@ int do_upload(tx_plan* p) {
   return TX_OK;
 }
 
-template <int Q, typename PT>
-void launch_stage1(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
+template <int Q, typename PT, bool HALF = false>
+void launch_stage1_t(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
   const int nitems = (int)p->items1.size();
   const int grid = std::min(nitems, std::max(p->dev.num_sms, 1));
-  k_stage1<Q, PT, OneBeam><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
+  k_stage1<Q, PT, OneBeam, HALF><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
       OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u);
+}
+
+template <int Q>
+void launch_stage1(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
+  if (p->interm == TX_INTERM_F16) launch_stage1_t<Q, uint16_t, true>(p, a, st);
+  else if (p->interm == TX_INTERM_U16) launch_stage1_t<Q, uint16_t>(p, a, st);
+  else launch_stage1_t<Q, int32_t>(p, a, st);
 }
 
 int check_beam(const tx_plan* p, const tx_beam* b) {
@@ -372,13 +389,21 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   }
   TX_MARK(1);
 
+  // half intermediates: the per-sub-band offsets of this block
+  const bool half = p->interm == TX_INTERM_F16;
+  if (half) {
+    TX_CUDA(cudaMemsetAsync(a.hoff, 0, (size_t)(p->nsub + 1) * 4, st));
+    k_offsets<OneBeam><<<std::min(p->nchan, std::max(p->dev.num_sms, 1) * 8), 256, 0, st>>>(OneBeam{a}, nullptr,
+                                                                                           nullptr, 1, p->nchan);
+    TX_CUDA(cudaGetLastError());
+  }
+
   // stage 1
-  const bool u16 = p->interm == TX_INTERM_U16;
   switch (p->q1) {
-    case 256: u16 ? launch_stage1<256, uint16_t>(p, a, st) : launch_stage1<256, int32_t>(p, a, st); break;
-    case 128: u16 ? launch_stage1<128, uint16_t>(p, a, st) : launch_stage1<128, int32_t>(p, a, st); break;
-    case 64: u16 ? launch_stage1<64, uint16_t>(p, a, st) : launch_stage1<64, int32_t>(p, a, st); break;
-    default: u16 ? launch_stage1<32, uint16_t>(p, a, st) : launch_stage1<32, int32_t>(p, a, st); break;
+    case 256: launch_stage1<256>(p, a, st); break;
+    case 128: launch_stage1<128>(p, a, st); break;
+    case 64: launch_stage1<64>(p, a, st); break;
+    default: launch_stage1<32>(p, a, st); break;
   }
   TX_CUDA(cudaGetLastError());
   TX_MARK(2);
@@ -386,13 +411,19 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   // stage 2 (+ exact per-tile sums)
   const bool series = p->output == TX_OUT_SERIES;
   {
-    if (u16) {
+    if (is16(p)) {
       const int nunits = p->nk * p->ntile2;
       const int grid = std::min(nunits, std::max(p->dev.num_sms, 1));
       const int slot = p->nsub_chunk2 * p->sww2;
-#define TX_S2(NW, SP)                                                                                       \
-  k_stage2_u16<NW, 32, SP, OneBeam><<<grid, stage2_threads(p), stage2_smem(p), st>>>(OneBeam{a}, nullptr, nullptr, \
-                                                                                     1, nunits, slot)
+#define TX_S2(NW, SP)                                                                                          \
+  do {                                                                                                         \
+    if (half)                                                                                                  \
+      k_stage2_u16<NW, 32, SP, OneBeam, true><<<grid, stage2_threads(p), stage2_smem(p), st>>>(                \
+          OneBeam{a}, nullptr, nullptr, 1, nunits, slot);                                                      \
+    else                                                                                                       \
+      k_stage2_u16<NW, 32, SP, OneBeam, false><<<grid, stage2_threads(p), stage2_smem(p), st>>>(               \
+          OneBeam{a}, nullptr, nullptr, 1, nunits, slot);                                                      \
+  } while (0)
       switch (stage2_split(p)) {
         case 8: TX_S2(512, 8); break;
         case 4: TX_S2(512, 4); break;

@@ -24,6 +24,7 @@
 // member's arguments from constant memory).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,11 +61,12 @@ struct BeamArgs {
   tx_cand* cands;                // candidate records
   unsigned long long* ncand;     // candidate counter
   uint8_t* tail;                 // compact beams: [nchan][tail_pitch] carried tail
+  int32_t* hoff;                 // half intermediates: per-sub-band offsets [nsub], then their sum
   int64_t R, head, start, T, Pp, Dp, Td, max_cands;
   int64_t L, tail_pitch;
   double lam, gamma;
   int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
-  int32_t layout, ingest_vec, running, output, compact, tail_pad;
+  int32_t layout, ingest_vec, running, output, compact, tail_pad, half;
 };
 
 // Where a kernel finds a beam's arguments (the Src template parameter).
@@ -245,6 +247,8 @@ __global__ void __launch_bounds__(256) k_ingest_batch(const Src src, const int32
     cur.seek(uoff, umem, nmem, u);
     const int lu = u - cur.lo;
     const BeamArgs a = src.get(cur.beam);
+    if (a.half && lu == 0)  // k_offsets accumulates into these next
+      for (int i = threadIdx.x; i <= a.nsub; i += blockDim.x) a.hoff[i] = 0;
     if (a.layout == TX_LAYOUT_TF) {
       const int nct = (a.nchan + 63) >> 6;
       const int64_t t0 = (int64_t)(lu / nct) * 64;
@@ -339,15 +343,86 @@ __global__ void __launch_bounds__(256) k_tail(const Src src, int dir, const int3
   }
 }
 
+// Half intermediates: the integer offset of sub-band s is
+//   o_s = sum_{c in s} rnd(sum_t X[c][t] / T)
+// over the block's T new samples (ring positions head .. head + T - 1 mod R),
+// rnd rounding half up. hoff[s] = o_s and hoff[nsub] = sum_s o_s accumulate
+// with integer atomics (order-free) from zero (set by the ingest). Units:
+// channels of every member in turn; 256 threads read 16-byte aligned chunks
+// of the ring and count only the bytes inside the block.
+__device__ __forceinline__ uint32_t byte_sum(uint32_t w) { return __dp4a(w, 0x01010101u, 0u); }
+
+template <typename Src>
+__global__ void __launch_bounds__(256) k_offsets(const Src src, const int32_t* __restrict__ uoff,
+                                                 const int32_t* __restrict__ umem, int nmem, int nunits) {
+  __shared__ unsigned long long red[8];
+  MemberCursor cur;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    int lu = u;
+    BeamArgs a;
+    if constexpr (Src::kBatch) {
+      cur.seek(uoff, umem, nmem, u);
+      lu = u - cur.lo;
+      a = src.get(cur.beam);
+    } else {
+      a = src.get(0);
+    }
+    const int c = lu;
+    const uint8_t* row = a.ring + (int64_t)c * a.R;
+    unsigned long long part = 0;
+    // the block's samples: [head, head + T) of the ring, in at most two ranges
+    const int64_t e0 = a.head + a.T;
+    for (int r = 0; r < 2; ++r) {
+      const int64_t b = r == 0 ? a.head : 0;
+      const int64_t e = r == 0 ? (e0 < a.R ? e0 : a.R) : (e0 > a.R ? e0 - a.R : 0);
+      for (int64_t q = (b & ~(int64_t)15) + 16 * (int64_t)threadIdx.x; q < e; q += 16 * (int64_t)blockDim.x) {
+        const uint4 w = *reinterpret_cast<const uint4*>(row + q);
+        if (q >= b && q + 16 <= e) {
+          part += byte_sum(w.x) + byte_sum(w.y) + byte_sum(w.z) + byte_sum(w.w);
+        } else {
+          const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+          for (int i = 0; i < 16; ++i)
+            if (q + i >= b && q + i < e) part += (ws[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) part += __shfl_xor_sync(0xffffffffu, part, k);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+      const int mean = (int)((2 * tot + (unsigned long long)a.T) / (2 * (unsigned long long)a.T));
+      atomicAdd(a.hoff + c / a.m, mean);
+      atomicAdd(a.hoff + a.nsub, mean);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // stage 1 (Sec. 2.3: de-disperse each sub-band on the coarse DM grid)
 // ---------------------------------------------------------------------------
 // Sums one coarse DM over the sub-band's m channels for VW words per lane,
 // starting at word jbase of the tile, and stores the 4 * VW * 32 outputs.
-template <int Q, int VW, typename PT>
+// Stored form of an exact stage-1 sum v: itself (uint16 or int32), or with
+// HALF the FP16 bits of v - off (off the sub-band's integer offset), rounded
+// to nearest even and saturated at +-65504.
+template <typename PT, bool HALF>
+__device__ __forceinline__ PT stage1_store(uint32_t v, int off) {
+  if constexpr (HALF) {
+    const float x = fminf(fmaxf((float)((int)v - off), -65504.f), 65504.f);
+    return (PT)__half_as_ushort(__float2half_rn(x));
+  } else {
+    return (PT)v;
+  }
+}
+
+template <int Q, int VW, typename PT, bool HALF>
 __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const uint32_t* __restrict__ t, int m,
                                            uint32_t one, int lane, int jbase, PT* __restrict__ prow, int rel0,
-                                           int64_t Pp) {
+                                           int64_t Pp, int off) {
   uint32_t aw[VW], ah[VW];
 #pragma unroll
   for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
@@ -386,7 +461,8 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 #pragma unroll
     for (int v = 0; v < VW; ++v) {
       const uint32_t lo = aw[v] - (ah[v] << 8);
-      const PT v0 = (PT)(lo & 0xFFFFu), v1 = (PT)(ah[v] & 0xFFFFu), v2 = (PT)(lo >> 16), v3 = (PT)(ah[v] >> 16);
+      const PT v0 = stage1_store<PT, HALF>(lo & 0xFFFFu, off), v1 = stage1_store<PT, HALF>(ah[v] & 0xFFFFu, off);
+      const PT v2 = stage1_store<PT, HALF>(lo >> 16, off), v3 = stage1_store<PT, HALF>(ah[v] >> 16, off);
       o[32 * v] = v0;
       o[32 * v + Q] = v1;
       o[32 * v + 2 * Q] = v2;
@@ -401,7 +477,7 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint32_t u = (uint32_t)(r + j + q * Q);
-        if (u < (uint64_t)Pp) prow[u] = (PT)val[q];
+        if (u < (uint64_t)Pp) prow[u] = stage1_store<PT, HALF>(val[q], off);
       }
     }
   }
@@ -423,7 +499,7 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 // or 8 warps. Shared memory is laid out for mL channels (the largest sub-band
 // of the launch), so an item's prefetch never overlaps the previous item's
 // staged words or table.
-template <int Q, typename PT, typename Src>
+template <int Q, typename PT, typename Src, bool HALF = false>
 __global__ void __launch_bounds__(kStage1Warps * 32, 1)
 k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nitems,
          int mL, uint32_t unit) {
@@ -517,6 +593,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const int next = idx + gridDim.x;
     if (next < nitems) issue(next);
 
+    const int off = HALF ? a.hoff[it.s] : 0;   // the sub-band's offset (half intermediates)
     // tasks: (coarse DM, part of the tile); split the tile when coarse DMs are few
     int split = 1;
     while (split < V && nkk * split * 2 <= kStage1Warps) split *= 2;
@@ -529,13 +606,13 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       const int rel0 = (int)((int64_t)it.tau0 - ab);  // |rel0| < 2^30
       const uint32_t* t = tab + kk * TS;
       if (split == 1) {
-        stage1_sum<Q, V, PT>(S, t, m, unit, lane, 0, prow, rel0, a.Pp);
+        stage1_sum<Q, V, PT, HALF>(S, t, m, unit, lane, 0, prow, rel0, a.Pp, off);
       } else if (split == 2) {
-        if constexpr (V >= 2) stage1_sum<Q, V / 2, PT>(S, t, m, unit, lane, part * (Q / 2), prow, rel0, a.Pp);
+        if constexpr (V >= 2) stage1_sum<Q, V / 2, PT, HALF>(S, t, m, unit, lane, part * (Q / 2), prow, rel0, a.Pp, off);
       } else if (split == 4) {
-        if constexpr (V >= 4) stage1_sum<Q, V / 4, PT>(S, t, m, unit, lane, part * (Q / 4), prow, rel0, a.Pp);
+        if constexpr (V >= 4) stage1_sum<Q, V / 4, PT, HALF>(S, t, m, unit, lane, part * (Q / 4), prow, rel0, a.Pp, off);
       } else {
-        if constexpr (V >= 8) stage1_sum<Q, V / 8, PT>(S, t, m, unit, lane, part * (Q / 8), prow, rel0, a.Pp);
+        if constexpr (V >= 8) stage1_sum<Q, V / 8, PT, HALF>(S, t, m, unit, lane, part * (Q / 8), prow, rel0, a.Pp, off);
       }
     }
     __syncthreads();
@@ -564,7 +641,7 @@ __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long
 // exact because every stage-2 sum is below 2^32. Shared memory holds two
 // even-copy slots and one odd-copy slot of `slot` words (the largest
 // SC * SWW of the launch) and the address table.
-template <int NW, int MAXWARPS, int SPLIT, typename Src>
+template <int NW, int MAXWARPS, int SPLIT, typename Src, bool HALF = false>
 __global__ void __launch_bounds__(MAXWARPS * 32, 1)
 k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
              int slot) {
@@ -613,9 +690,13 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
     issue_chunk(a, k, (int64_t)tile * 2 * NW, 0, buf);
   };
 
-  uint32_t aw[VW], ah[VW];
+  uint32_t aw[VW], ah[VW];   // uint16 pairs: sum of words, sum of high lanes
+  float fl[VW], fh[VW];      // half pairs: FP32 sums of the low and high halves
 #pragma unroll
-  for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+  for (int v = 0; v < VW; ++v) {
+    aw[v] = ah[v] = 0u;
+    fl[v] = fh[v] = 0.f;
+  }
   int buf = 0;
   if ((int)blockIdx.x < nunits) issue_unit(blockIdx.x, 0);
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
@@ -671,19 +752,32 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
           const uint32_t* r1 = Sl + t[ss + 1];
 #pragma unroll
           for (int v = 0; v < VW; ++v) {
-            const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
-            aw[v] += w0 + w1;
-            madd_hi16(ah[v], w0);
-            madd_hi16(ah[v], w1);
+            if constexpr (HALF) {
+              const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(r0 + 32 * v));
+              const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(r1 + 32 * v));
+              fl[v] += f0.x + f1.x;
+              fh[v] += f0.y + f1.y;
+            } else {
+              const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+              aw[v] += w0 + w1;
+              madd_hi16(ah[v], w0);
+              madd_hi16(ah[v], w1);
+            }
           }
         }
         if (ss < ns) {
           const uint32_t* r0 = Sl + t[ss];
 #pragma unroll
           for (int v = 0; v < VW; ++v) {
-            const uint32_t w0 = r0[32 * v];
-            aw[v] += w0;
-            madd_hi16(ah[v], w0);
+            if constexpr (HALF) {
+              const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(r0 + 32 * v));
+              fl[v] += f0.x;
+              fh[v] += f0.y;
+            } else {
+              const uint32_t w0 = r0[32 * v];
+              aw[v] += w0;
+              madd_hi16(ah[v], w0);
+            }
           }
         }
       }
@@ -694,10 +788,19 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
     if (g < nd) {
       const int d = dfirst + g;
       int32_t* drow = a.D + (size_t)d * a.Dp;
+      const int O = HALF ? a.hoff[a.nsub] : 0;   // the offsets taken out in stage 1, added back
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         const int64_t ta = t0 + 2 * (jbase + lane + 32 * v);
-        const uint32_t lo = aw[v] - (ah[v] << 16), hi = ah[v];
+        uint32_t lo, hi;
+        if constexpr (HALF) {
+          // the halves hold integers and their FP32 sums stay below 2^24: exact
+          lo = (uint32_t)((int)fl[v] + O);
+          hi = (uint32_t)((int)fh[v] + O);
+        } else {
+          lo = aw[v] - (ah[v] << 16);
+          hi = ah[v];
+        }
         if (ta + 1 < a.Td && (a.Dp & 1) == 0) {
           *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
         } else {
@@ -709,7 +812,10 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       }
     }
 #pragma unroll
-    for (int v = 0; v < VW; ++v) aw[v] = ah[v] = 0u;
+    for (int v = 0; v < VW; ++v) {
+      aw[v] = ah[v] = 0u;
+      fl[v] = fh[v] = 0.f;
+    }
     warp_sum_stats(s1, s2);
     if (SPLIT == 1) {
       if (g < nd && lane == 0) a.part[(size_t)(dfirst + g) * a.ntile2 + tile] = make_longlong2(s1, (long long)s2);
@@ -1127,6 +1233,8 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.D = series ? static_cast<int32_t*>(out) : reinterpret_cast<int32_t*>(ws + p->ws_D);
   a.part = reinterpret_cast<longlong2*>(ws + p->ws_part);
   a.cst = reinterpret_cast<SnrConst*>(ws + p->ws_const);
+  a.hoff = reinterpret_cast<int32_t*>(ws + p->ws_hoff);
+  a.half = p->interm == TX_INTERM_F16;
   a.run = b->run;
   a.d1 = p->dev.d1;
   a.abase = p->dev.abase;

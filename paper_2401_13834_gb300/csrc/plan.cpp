@@ -94,7 +94,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   if (d->nsamp < 1) { set_error("nsamp must be >= 1"); return TX_ERR_INVALID_ARG; }
   if (d->group < 0) { set_error("group must be >= 0"); return TX_ERR_INVALID_ARG; }
   if (d->layout != TX_LAYOUT_FT && d->layout != TX_LAYOUT_TF) { set_error("bad layout"); return TX_ERR_INVALID_ARG; }
-  if (d->interm != TX_INTERM_U16 && d->interm != TX_INTERM_I32) { set_error("bad interm"); return TX_ERR_INVALID_ARG; }
+  if (d->interm != TX_INTERM_U16 && d->interm != TX_INTERM_I32 && d->interm != TX_INTERM_F16) { set_error("bad interm"); return TX_ERR_INVALID_ARG; }
   if (d->output < TX_OUT_CANDS || d->output > TX_OUT_SERIES) { set_error("bad output mode"); return TX_ERR_INVALID_ARG; }
   if (d->stats != TX_STATS_BLOCK && d->stats != TX_STATS_RUNNING) { set_error("bad stats mode"); return TX_ERR_INVALID_ARG; }
   if (d->stats == TX_STATS_RUNNING && !(d->stats_lambda > 0.0 && d->stats_lambda <= 1.0)) { set_error("stats_lambda must be in (0, 1]"); return TX_ERR_INVALID_ARG; }
@@ -199,7 +199,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   // uint16 path reads [base, base + 2 sww2) with base <= t0 + 15; int32 path
   // reads [t0 + emin, + tt2 + span2 + 16)
   p->Pp = round_up(std::max<int64_t>(last_t0 + 16 + 2 * (int64_t)p->sww2, last_t0 + 16 + tt2 + span2 + 16) + 16, 64);
-  if (p->interm == TX_INTERM_U16) {
+  if (p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16) {
     // double-buffered even copy + odd copy + address table
     const int64_t per_sub = 3 * (int64_t)p->sww2 * 4 + (int64_t)kStage2MaxGroup * 4 + 8;
     p->nsub_chunk2 = (int32_t)std::min<int64_t>(nsub, (kSmemMax - 1024) / per_sub);
@@ -266,12 +266,13 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->head0 = round_up(p->L, 64) % p->R;
 
   // ---- sizes ---------------------------------------------------------------------
-  const int64_t psz = p->interm == TX_INTERM_U16 ? 2 : 4;
+  const int64_t psz = p->interm == TX_INTERM_I32 ? 4 : 2;
   int64_t off = 0;
   p->ws_P = off; off = round_up(off + (int64_t)nk * nsub * p->Pp * psz, 256);
   p->ws_D = off; off = round_up(off + (p->output == TX_OUT_SERIES ? 0 : (int64_t)ndm * p->Dp * 4), 256);
   p->ws_part = off; off = round_up(off + (int64_t)ndm * p->ntile2 * 16, 256);
   p->ws_const = off; off = round_up(off + (int64_t)ndm * p->nw * (int64_t)sizeof(SnrConst), 256);
+  p->ws_hoff = off; off = round_up(off + (p->interm == TX_INTERM_F16 ? (int64_t)(nsub + 1) * 4 : 0), 256);
   p->ws_bytes = off;
   switch (p->output) {
     case TX_OUT_CANDS: p->out_bytes = p->max_cands * (int64_t)sizeof(tx_cand); break;

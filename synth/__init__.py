@@ -282,7 +282,7 @@ def pulse_points(p: Pulse, freqs: np.ndarray, tsamp: float, nsamp: int, f_top=No
     return chan[keep], tt[keep], vals[keep]
 
 
-def device_spectrum(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0, device="cuda"):
+def device_spectrum(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0, device="cuda", rfi: Rfi = None):
     """uint8 [nchan, nsamp_total] torch tensor drawn on a CUDA device.
 
     clip(round(N(mean, std) + pulses), 0, 255) like ``make_spectrum``, with the
@@ -300,6 +300,8 @@ def device_spectrum(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0, de
         if c.size:
             x.index_put_((torch.from_numpy(c).to(device), torch.from_numpy(t).to(device)),
                          torch.from_numpy(v).to(device), accumulate=True)
+    if rfi is not None:
+        add_rfi(x, rfi)
     return x.round_().clamp_(0.0, 255.0).to(torch.uint8)
 
 
@@ -316,19 +318,66 @@ def batched_pulses(wl: Workload, n: int = 4, seed: int = 0) -> list:
     return out
 
 
+@dataclasses.dataclass
+class Rfi:
+    """Interference for the precision workload: narrow-band sinusoids in some
+    channels (amplitude in noise sigmas, period and phase per channel) and
+    zero-DM broadband bursts (every channel at once, no dispersion delay)."""
+    channels: np.ndarray       # int [n]
+    amp: float                 # counts
+    period: np.ndarray         # samples [n]
+    phase: np.ndarray          # radians [n]
+    bursts: list               # (start sample, width, amplitude in counts)
+
+
+def make_rfi(wl: Workload, nsamp_total: int, seed: int = 0, frac: float = 0.05, amp_sigma: float = 50.0,
+             nbursts: int = 4, burst_sigma: float = 3.0) -> Rfi:
+    """5% of channels carrying 50-sigma sinusoids of random period (4..4096 samples) and phase,
+    and a few zero-DM bursts of burst_sigma sigmas lasting 8..256 samples."""
+    rng = np.random.default_rng(seed)
+    n = max(1, int(round(frac * wl.nchan)))
+    ch = np.sort(rng.choice(wl.nchan, size=n, replace=False))
+    period = np.exp(rng.uniform(math.log(4.0), math.log(4096.0), size=n))
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    bursts = []
+    for _ in range(nbursts):
+        w = int(rng.integers(8, 257))
+        bursts.append((int(rng.integers(0, max(1, nsamp_total - w))), w, burst_sigma * wl.noise_std))
+    return Rfi(channels=ch, amp=amp_sigma * wl.noise_std, period=period, phase=phase, bursts=bursts)
+
+
+def add_rfi(x, rfi: Rfi) -> None:
+    """Adds the interference, in place, to a float dynamic spectrum [nchan, nsamp]
+    (a numpy array or a torch tensor)."""
+    nsamp = x.shape[1]
+    if isinstance(x, np.ndarray):
+        t = np.arange(nsamp, dtype=np.float64)
+        for c, P, ph in zip(rfi.channels, rfi.period, rfi.phase):
+            x[c] += (rfi.amp * np.sin(2.0 * math.pi * t / P + ph)).astype(x.dtype)
+    else:
+        import torch
+        t = torch.arange(nsamp, device=x.device, dtype=torch.float64)
+        for c, P, ph in zip(rfi.channels, rfi.period, rfi.phase):
+            x[int(c)] += (rfi.amp * torch.sin(2.0 * math.pi * t / float(P) + float(ph))).to(x.dtype)
+    for t0, w, a in rfi.bursts:
+        x[:, t0:t0 + w] += a
+
+
 def quantise(values: np.ndarray) -> np.ndarray:
     return np.clip(np.rint(values), 0, 255).astype(np.uint8)
 
 
 def make_spectrum(wl: Workload, nsamp_total: int, pulses=(), seed: int = 0,
-                  dtype_noise=np.float32) -> np.ndarray:
-    """uint8 [nchan, nsamp_total] = clip(round(N(mean, std) + pulses), 0, 255)."""
+                  dtype_noise=np.float32, rfi: Rfi = None) -> np.ndarray:
+    """uint8 [nchan, nsamp_total] = clip(round(N(mean, std) + pulses + rfi), 0, 255)."""
     rng = np.random.default_rng(seed)
     x = rng.standard_normal((wl.nchan, nsamp_total), dtype=dtype_noise)
     x *= dtype_noise(wl.noise_std)
     x += dtype_noise(wl.noise_mean)
     for p in pulses:
         add_pulse(x, p, wl.freqs_mhz, wl.tsamp_s)
+    if rfi is not None:
+        add_rfi(x, rfi)
     return quantise(x)
 
 

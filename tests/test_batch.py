@@ -41,6 +41,8 @@ BEAMS = [
          output="cands", layout="tf", stats="running", snr_threshold=3.5),
     dict(wl=dict(nchan=96, nsub=8, ndm=24, nsamp=2048, descending=True), output="plane", layout="tf"),
     dict(wl=None, output="cands", layout="ft", snr_threshold=6.0),   # the 256-channel small workload
+    dict(wl=dict(nchan=257, nsub=1, ndm=20, nsamp=2000, group=32), output="series", layout="tf", interm="f16"),
+    dict(wl=dict(nchan=128, nsub=4, ndm=40, nsamp=2500, dm_max=200.0), output="plane", layout="ft", interm="f16"),
 ]
 
 

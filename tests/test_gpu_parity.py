@@ -406,3 +406,42 @@ def test_compact_beam_checkpoint_restore(tx):
     got = [tx.execute(plan, b, blk[i], workspace=ws).cpu().numpy() for i in (1, 2)]
     assert all(np.array_equal(x, y) for x, y in zip(ref, got))
     assert b.nblocks == 3
+
+
+@pytest.mark.parametrize("cfg", TINY)
+def test_f16_series_bit_exact(tx, cfg):
+    """FP16 stage-1 storage: the series equal the oracle's emulation of the
+    FP16 form exactly (uniform data drives the sums far past 2048, so
+    rounding and, at 257 channels per sub-band, saturation both occur)."""
+    wl = synth.tiny_workload(**cfg)
+    plan = make_plan(tx, wl, output="series", interm="f16")
+    op = oracle_plan(wl)
+    X = rand_stream(wl.nchan, plan.overlap + wl.nsamp, seed=zlib.crc32(str(cfg).encode()) % 997)
+    (out, _, _), = run_blocks(tx, plan, X)[0]
+    got = tx.series_view(plan, out).cpu().numpy()
+    ref = O.subband_dedisperse_f16(X, op, plan.series_len, slice(plan.overlap, plan.overlap + wl.nsamp))
+    assert np.array_equal(got.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("compact", [False, True])
+def test_f16_with_rfi_over_blocks(tx, compact):
+    """64 channels per sub-band with narrow-band RFI and zero-DM bursts (sums
+    beyond 2048 where the bursts are), three blocks through one beam."""
+    wl = synth.tiny_workload(nchan=256, nsub=4, ndm=48, nsamp=3000, dm_max=150.0, tsamp=128e-6)
+    plan = make_plan(tx, wl, output="series", interm="f16")
+    op = oracle_plan(wl)
+    L, T = plan.overlap, plan.nsamp
+    rfi = synth.make_rfi(wl, L + 3 * T, seed=4)
+    X = synth.make_spectrum(wl, L + 3 * T, [], seed=5, rfi=rfi)
+    beam = tx.Beam(plan, compact=compact)
+    beam.prime(torch.from_numpy(np.ascontiguousarray(X[:, :L])).cuda())
+    ws = plan.alloc_workspace(compact=compact)
+    rounded = 0
+    for b in range(3):
+        blk = torch.from_numpy(np.ascontiguousarray(X[:, L + b * T:L + (b + 1) * T])).cuda()
+        got = tx.series_view(plan, tx.execute(plan, beam, blk, workspace=ws)).cpu().numpy()
+        win = X[:, b * T:b * T + L + T]
+        ref = O.subband_dedisperse_f16(win, op, plan.series_len, slice(L, L + T))
+        assert np.array_equal(got.astype(np.float64), ref), f"block {b}"
+        rounded += int((ref != O.subband_dedisperse(win, op, plan.series_len)).sum())
+    assert rounded > 0          # the bursts did push sums past 2048

@@ -468,3 +468,72 @@ def test_detection_probability_symmetry():
     assert float(LS.p_detect(5.0, 5.0)) == pytest.approx(0.5)
     assert float(LS.p_false_alarm(0.0)) == pytest.approx(0.5)
     assert float(LS.p_detect(5.0, 8.0)) > float(LS.p_detect(5.0, 5.0))
+
+
+# ---------------------------------------------------------------------------
+# Half-precision storage of the stage-1 sums (the FP16 form)
+# ---------------------------------------------------------------------------
+def _one_subband_plan(nchan, T):
+    """One sub-band, DM 0 only, width 1: every delay is 0, so D[t] = P[t] = sum_c X[c][t]."""
+    f = synth.channel_centres(1400.0, 1401.0, nchan)
+    return O.SubbandPlan(f, 1e-3, np.array([0.0]), 1, 1, (1,))
+
+
+def test_f16_form_exact_while_offsets_keep_sums_small():
+    """With 8 channels per sub-band every |P - o_s| <= 8 * 255 = 2040 < 2048,
+    and every integer up to 2048 is an FP16 value: the FP16 form is exact."""
+    wl = synth.tiny_workload(nchan=64, nsub=8, ndm=20, nsamp=900, dm_max=80.0)
+    plan = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, 0, wl.widths)
+    X = np.random.default_rng(3).integers(0, 256, size=(64, plan.overlap + 900)).astype(np.uint8)
+    nout = 900 + plan.wmax - 1
+    exact = O.subband_dedisperse(X, plan, nout)
+    f16 = O.subband_dedisperse_f16(X, plan, nout, slice(plan.overlap, plan.overlap + 900))
+    assert np.array_equal(f16, exact.astype(np.float64))
+
+
+def test_f16_form_rounds_to_nearest_even():
+    """Sums placed at 2047, 2049, 3001, 4098 and 4102 on a zero background.
+    FP16 holds the integers up to 2048, every second one in [2048, 4096) and
+    every fourth in [4096, 8192); ties go to the even significand:
+    2049 -> 2048, 3001 -> 3000 (3000 = 1.4648... x 2^11 with significand 476,
+    even), 4098 -> 4096, 4102 -> 4104 (significand 2). The block's channel
+    means round to 0 (at most 1275 counts over 4096 samples), so o_s = 0."""
+    T, m = 4096, 20
+    plan = _one_subband_plan(m, T)
+    X = np.zeros((m, T), dtype=np.uint8)
+    targets = {100: 2047, 700: 2049, 1300: 3001, 2500: 4098, 3900: 4102}
+    for t, v in targets.items():
+        left = v
+        for c in range(m):
+            x = min(255, left)
+            X[c, t] = x
+            left -= x
+        assert left == 0
+    assert np.array_equal(O.half_offsets(X, plan, slice(0, T)), [0])
+    D = O.subband_dedisperse_f16(X, plan, T, slice(0, T))[0]
+    expect = np.zeros(T)
+    expect[[100, 700, 1300, 2500, 3900]] = [2047, 2048, 3000, 4096, 4104]
+    assert np.array_equal(D, expect)
+
+
+def test_f16_form_saturates():
+    """257 channels of 255 sum to 65535, above the largest FP16 value 65504."""
+    T, m = 4096, 257
+    plan = _one_subband_plan(m, T)
+    X = np.zeros((m, T), dtype=np.uint8)
+    X[:, 10] = 255
+    D = O.subband_dedisperse_f16(X, plan, T, slice(0, T))[0]
+    assert D[10] == 65504.0 and D[11] == 0.0
+
+
+def test_half_offsets_definition():
+    """o_s = sum over the sub-band's channels of their block means rounded half up."""
+    wl = synth.tiny_workload(nchan=8, nsub=2, ndm=4, nsamp=10)
+    plan = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 2, 0, wl.widths)
+    X = np.zeros((8, 30), dtype=np.uint8)
+    X[0, 20:30] = 5           # mean 5
+    X[1, 20:25] = 1           # mean 0.5 -> 1 (half up)
+    X[2, 20:24] = 1           # mean 0.4 -> 0
+    X[5, 0:20] = 200          # outside the block: ignored
+    X[6, 20:30] = 255         # mean 255
+    assert list(O.half_offsets(X, plan, slice(20, 30))) == [6, 255]

@@ -54,7 +54,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched", "serving"], default="meerkat_l")
+    ap.add_argument("--workload", choices=sorted(synth.WORKLOADS) + ["batched", "serving", "precision"],
+                    default="meerkat_l")
+    ap.add_argument("--oracle-dms", type=int, default=8, help="precision: DMs checked against the FP64 oracle")
     ap.add_argument("--serve-beams", type=int, default=480, help="serving: number of beams")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: length of the Poisson phase")
     ap.add_argument("--serve-load", type=float, default=1.2, help="serving: arrivals as a multiple of real time")
@@ -68,7 +70,7 @@ def parse_args():
     ap.add_argument("--tune", action="store_true", help="batched: autotune shapes missing from the cache first")
     ap.add_argument("--output", choices=["cands", "plane", "cube"], default="cands")
     ap.add_argument("--layout", choices=["tf", "ft"], default="tf")
-    ap.add_argument("--interm", choices=["u16", "i32"], default="u16")
+    ap.add_argument("--interm", choices=["u16", "i32", "f16"], default="u16")
     ap.add_argument("--gamma", type=float, default=7.0)
     ap.add_argument("--max-cands", type=int, default=1 << 24)
     ap.add_argument("--nsamp", type=int, default=0, help="override T (new samples per block), e.g. for profiling")
@@ -296,6 +298,8 @@ def run_reference(args):
 
 
 def load_workload(args):
+    if args.workload == "precision":
+        return synth.meerkat_l_workload()
     if args.workload == "batched":
         return synth.batched_workloads(args.beams)[0]
     if args.workload == "serving":
@@ -913,6 +917,132 @@ def run_serving(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------
+# precision arm: int32 / uint16 / FP16 intermediates on MeerKAT-L with RFI
+# ----------------------------------------------------------------------------
+def run_precision(args):
+    import torch
+
+    world, rank, dev = init_dist()
+    from paper_2401_13834_gb300 import build as _build
+    _build.build()
+    import paper_2401_13834_gb300 as tx
+    from oracle import dedisp as O
+
+    wl = synth.meerkat_l_workload()
+    wl.name = "meerkat-l-4096ch-4096dm-rfi"
+    mk = dict(layout=args.layout, snr_threshold=args.gamma)
+    probe = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, output="series", **mk)
+    L, T, nw = probe.overlap, probe.nsamp, probe.nwidth
+    rfi = synth.make_rfi(wl, L + T, seed=11)
+    pulses = synth.meerkat_pulses(wl, seed=2)
+    x = synth.device_spectrum(wl, L + T, pulses, seed=17 + rank, device=dev, rfi=rfi)
+    tail, blk = x[:, :L], x[:, L:]
+    if args.layout == "tf":
+        tail, blk = tail.t().contiguous(), blk.t().contiguous()
+    X_host = x.cpu().numpy() if rank == 0 else None
+    del x
+
+    def run(interm, output, reps):
+        p = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, interm=interm, output=output, **mk)
+        ws = p.alloc_workspace(dev)
+        out, nc = p.alloc_out(dev)
+        times = []
+        for r in range(reps + 1):
+            beam = tx.Beam(p)           # the same window every time
+            beam.prime(tail)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tx.execute(p, beam, blk, out=out, ncand=nc, workspace=ws)
+            e1.record()
+            e1.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+            del beam
+        del ws
+        torch.cuda.empty_cache()
+        return p, out, float(np.median(times)) if times else None
+
+    # series: where the FP16 form's integer sums differ from the exact ones
+    ps, d_exact, _ = run("u16", "series", 0)
+    _, d_f16, _ = run("f16", "series", 0)
+    De = d_exact.view(torch.int32)
+    Dh = d_f16.view(torch.int32)
+    dd = (Dh.long() - De.long()).abs()
+    series = {"points": int(De.numel()), "differing": int((dd > 0).sum()), "max_abs_diff": int(dd.max()),
+              "exact_abs_max": int(De.abs().max())}
+    del d_exact, d_f16, De, Dh, dd
+    torch.cuda.empty_cache()
+
+    # S/N cubes and block times of the three intermediates
+    times = {}
+    cubes = {}
+    for im in ("u16", "f16", "i32"):
+        p, out, ms = run(im, "cube", 3)
+        times[im] = ms
+        cubes[im] = out.view(torch.float32).view(p.ndm, nw, T)
+        if im == "i32":
+            same = bool(torch.equal(cubes["i32"], cubes["u16"]))
+            del cubes["i32"], out
+            torch.cuda.empty_cache()
+    ref, f16 = cubes["u16"], cubes["f16"]
+    mx, cnt3, cnt4, tot, hist = 0.0, 0, 0, 0.0, np.zeros(9, dtype=np.int64)
+    for d0 in range(0, ref.shape[0], 256):
+        e = (f16[d0:d0 + 256] - ref[d0:d0 + 256]).abs()
+        mx = max(mx, float(e.max()))
+        cnt3 += int((e > 1e-3).sum())
+        cnt4 += int((e > 1e-4).sum())
+        tot += float(e.double().sum())
+        lg = torch.log10(e.clamp_min(1e-12)).floor().clamp(-9, -1) + 9   # bins 1e-9 .. 1e-1 and above
+        hist += torch.bincount(lg.long().flatten(), minlength=9).cpu().numpy()[:9]
+        del e, lg
+    npts = ref.numel()
+    cube_err = {"points": int(npts), "max_abs": mx, "mean_abs": tot / npts, "count_above_1e-3": cnt3,
+                "count_above_1e-4": cnt4, "frac_above_1e-3": cnt3 / npts,
+                "log10_histogram_bins_1e-9_to_1e-1": hist.tolist(), "int32_cube_equals_uint16_cube": same}
+
+    # against the FP64 oracle on sampled DMs (exact sums, float64 S/N)
+    oracle = None
+    if rank == 0 and args.oracle_dms > 0:
+        op = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, 0, wl.widths)
+        rng = np.random.default_rng(5)
+        pdms = sorted({int(np.argmin(np.abs(wl.dms - pl.dm))) for pl in pulses})[: args.oracle_dms // 2]
+        sel = sorted(set(pdms) | set(rng.choice(wl.ndm, size=args.oracle_dms - len(pdms), replace=False).tolist()))
+        t0 = time.perf_counter()
+        Dx = O.subband_dedisperse(X_host, op, T + op.wmax - 1, sel)
+        _, _, mu, sg = O.block_stats(Dx, T)
+        s64 = O.boxcar_snr(Dx, op.widths, T, mu, sg)
+        Dh = O.subband_dedisperse_f16(X_host, op, T + op.wmax - 1, slice(L, L + T), sel)
+        _, _, mu2, sg2 = O.block_stats(Dh, T)
+        s64h = O.boxcar_snr(Dh, op.widths, T, mu2, sg2)
+        el = time.perf_counter() - t0
+        gu = ref[sel].double().cpu().numpy()
+        gh = f16[sel].double().cpu().numpy()
+        oracle = {"dm_indices": sel, "oracle_seconds": el,
+                  "uint16_path_vs_fp64_max_abs": float(np.abs(gu - s64).max()),
+                  "fp16_path_vs_fp64_max_abs": float(np.abs(gh - s64).max()),
+                  "fp16_form_fp64_vs_exact_fp64_max_abs": float(np.abs(s64h - s64).max()),
+                  "fp16_path_vs_fp16_form_fp64_max_abs": float(np.abs(gh - s64h).max()),
+                  "max_snr": float(np.abs(s64).max())}
+    if rank == 0:
+        units = wl.ndm * T
+        line = {
+            "metric": METRIC, "value": units / (times["f16"] / 1e3), "unit": UNIT, "n_gpus": world, "steps": 3,
+            "warmup": 1, "ms_per_step": times["f16"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8 -> f16 stage-1 storage, f32 stage-2 sums, f32 S/N",
+            "data": "synthetic",
+            "config": dict(workload_config(wl, probe.group, L, args), output="cube", interm="f16",
+                           rfi={"channels": int(len(rfi.channels)), "amp_sigma": 50.0, "bursts": rfi.bursts}),
+            "block_ms": times,
+            "series_fp16_vs_exact": series,
+            "snr_cube_fp16_vs_exact": cube_err,
+            "vs_fp64_oracle": oracle,
+            "notes": "Exact reference: the uint16 path (bit-identical integer sums to the oracle, checked in the "
+                     "GPU tests; its cube equals the int32 path's). value: FP16-intermediate throughput in cube mode.",
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.workload == "serving":
@@ -923,6 +1053,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

@@ -359,6 +359,53 @@ int32_t tx_batch_read_profile(tx_batch* batch, double* h_ms, int32_t* nsteps);
    plans or beams). */
 void tx_batch_destroy(tx_batch* batch);
 
+/* ---- candidate clustering (Sec. 2.5: DBSCAN on the DM-time plane) ----
+   The candidates of a block (tx_cand records, the DM-time plane's points at or
+   above the threshold) are clustered with DBSCAN after DM is converted to the
+   dispersion delay across the band (Eq. 1, lowest to highest channel centre,
+   ms) and time to t * t_samp (ms):
+     core point   more than k other points at Euclidean distance <= radius_ms
+     cluster      core points joined by chains of core neighbours, plus every
+                  non-core point within radius_ms of one of them
+     outlier      any other point (label -1)
+   Points are taken in canonical order, sorted by (dm_index, t); a cluster's id
+   is the canonical index of its first core point; a non-core point next to
+   several clusters joins the one of smallest id. Results do not depend on the
+   order of the input records. The paper searches neighbours with a kd-tree;
+   here a uniform grid of cells of side ~radius_ms does it (section 2.5's
+   prune rules become "only the 3 x 3 cells around a point"). */
+typedef struct tx_cluster {
+  int32_t id;                 /* canonical index of the cluster's first core point     */
+  int32_t dm_index, t, w_index;
+  float   snr;                /* the member of highest S/N (ties: first in canonical
+                                 order), reported for the cluster                        */
+  int32_t members;            /* points in the cluster                                 */
+  int32_t dm_lo, dm_hi;       /* DM-index and time extent of the members               */
+  int32_t t_lo, t_hi;
+} tx_cluster;
+
+typedef struct tx_clusterer tx_clusterer;
+
+/* The delay of each DM trial of a plan as used for clustering: double
+   [ndm], K DM (f_min^-2 - f_max^-2) in ms (f_min, f_max the lowest and highest
+   channel centres). */
+int32_t tx_plan_delay_table(const tx_plan* plan, double* h_delay_ms);
+
+/* Scratch for clustering up to max_points candidates of the plan's blocks on
+   the current device (about 90 bytes per point). Errors: INVALID_ARG, OOM, CUDA. */
+int32_t tx_clusterer_create(const tx_plan* plan, double radius_ms, int32_t k, int64_t max_points,
+                            tx_clusterer** out);
+
+/* Clusters n records at d_cands (device; may be NULL when n is 0). Writes the clusters in id order to
+   d_out (room for n records) and their count to *d_nclusters (device int64);
+   d_labels (may be NULL) receives the cluster id of each point in canonical
+   order (-1: outlier) and d_order (may be NULL) the record index of each
+   canonical position. Enqueued on `stream`; n <= max_points. */
+int32_t tx_cluster_run(tx_clusterer* c, const tx_cand* d_cands, int64_t n, tx_cluster* d_out,
+                       int64_t* d_nclusters, int32_t* d_labels, int32_t* d_order, void* stream);
+
+void tx_clusterer_destroy(tx_clusterer* c);
+
 /* ---- allocation-free de-dispersion (the paper has no counterpart) ----
    For callers that cannot call cudaMalloc: real-time loops that must not take
    the allocator's locks or its implicit synchronisation, hosts that embed the

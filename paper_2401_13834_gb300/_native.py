@@ -17,6 +17,9 @@ STATS = {"block": 0, "running": 1}
 TX_ERR_CAND_OVERFLOW = -6
 
 CAND_DTYPE = np.dtype([("dm_index", np.int32), ("t", np.int32), ("w_index", np.int32), ("snr", np.float32)])
+CLUSTER_DTYPE = np.dtype([("id", np.int32), ("dm_index", np.int32), ("t", np.int32), ("w_index", np.int32),
+                          ("snr", np.float32), ("members", np.int32), ("dm_lo", np.int32), ("dm_hi", np.int32),
+                          ("t_lo", np.int32), ("t_hi", np.int32)])
 
 
 class TxError(RuntimeError):
@@ -99,6 +102,10 @@ def _load():
         "tx_batch_get_info": (I32, [P, C.POINTER(_BatchInfo)]),
         "tx_execute_batch": (I32, [P, VP, VP, VP, VP, VP]),
         "tx_batch_read_profile": (I32, [P, VP, C.POINTER(I32)]),
+        "tx_plan_delay_table": (I32, [P, VP]),
+        "tx_clusterer_create": (I32, [P, C.c_double, I32, I64, C.POINTER(P)]),
+        "tx_cluster_run": (I32, [P, VP, I64, VP, VP, VP, VP, VP]),
+        "tx_clusterer_destroy": (None, [P]),
         "tx_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -197,6 +204,12 @@ class Plan:
         _check(lib.tx_plan_tables(self._h, d1.ctypes.data_as(C.c_void_p), d2.ctypes.data_as(C.c_void_p),
                                   kof.ctypes.data_as(C.c_void_p), cdm.ctypes.data_as(C.c_void_p)))
         return {"d1": d1, "d2": d2, "coarse_of_fine": kof, "coarse_dm": cdm}
+
+    def delay_table(self):
+        """Delay of each DM trial across the band, ms (the clustering axis)."""
+        out = np.zeros(self.ndm, dtype=np.float64)
+        _check(lib.tx_plan_delay_table(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def stage1_layout(self):
         off, pitch = C.c_int64(), C.c_int64()
@@ -433,3 +446,39 @@ class Batch:
         if h is not None and lib is not None:
             lib.tx_batch_destroy(h)
             self._h = None
+
+
+class Clusterer:
+    """DBSCAN of a block's candidates on the GPU (tx_cluster_run)."""
+
+    def __init__(self, plan: Plan, radius_ms: float, k: int, max_points: int):
+        self.plan = plan
+        self.max_points = int(max_points)
+        h = C.c_void_p()
+        _check(lib.tx_clusterer_create(plan.handle, float(radius_ms), int(k), self.max_points, C.byref(h)))
+        self._h = h
+
+    def run(self, cands, n: int, out=None, nclusters=None, labels=None, order=None, stream=None):
+        """cands: the device candidate buffer (records); n: how many. Returns (out, nclusters)
+        device tensors (out holds int32 [n, 10] cluster records)."""
+        import torch
+        dev = cands.device
+        if out is None:
+            out = torch.empty((max(int(n), 1), 10), dtype=torch.int32, device=dev)
+        if nclusters is None:
+            nclusters = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(lib.tx_cluster_run(self._h, _ptr(cands), int(n), _ptr(out), _ptr(nclusters), _ptr(labels),
+                                  _ptr(order), _stream_ptr(stream)))
+        return out, nclusters
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and lib is not None:
+            lib.tx_clusterer_destroy(h)
+            self._h = None
+
+
+def clusters_view(out, nclusters):
+    """Host structured array of the cluster records."""
+    n = int(nclusters.item())
+    return out[:n].contiguous().cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)

@@ -125,6 +125,13 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->f_ref = *std::max_element(p->freq.begin(), p->freq.end());
   p->f_ref_s.resize(nsub);
   for (int s = 0; s < nsub; ++s) p->f_ref_s[s] = *std::max_element(p->freq.begin() + s * m, p->freq.begin() + (s + 1) * m);
+  {
+    // DM as dispersion delay across the band (Sec. 2.5 clustering), ms
+    const double f_lo = *std::min_element(p->freq.begin(), p->freq.end());
+    p->delay_ms.resize(ndm);
+    for (int i = 0; i < ndm; ++i)
+      p->delay_ms[i] = kDispersion * p->dm[i] * (1.0 / (f_lo * f_lo) - 1.0 / (p->f_ref * p->f_ref)) * 1e3;
+  }
   p->kof.resize(ndm);
   for (int i = 0; i < ndm; ++i) p->kof[i] = i / G;
   p->coarse_dm.resize(nk);
@@ -367,6 +374,12 @@ int32_t tx_geometric_widths(double ratio, int32_t wmax, int32_t* h_widths, int32
     w *= ratio;
   }
   return n;
+}
+
+int32_t tx_plan_delay_table(const tx_plan* p, double* h_delay_ms) {
+  if (!p || !h_delay_ms) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  std::memcpy(h_delay_ms, p->delay_ms.data(), p->delay_ms.size() * sizeof(double));
+  return TX_OK;
 }
 
 int32_t tx_plan_stage1_layout(const tx_plan* p, int64_t* p_offset, int64_t* p_pitch, int32_t* h_base) {

@@ -88,6 +88,7 @@ struct tx_plan {
   std::vector<int32_t> d1;        // [nk][nchan]
   std::vector<int32_t> d2;        // [ndm][nsub]
   std::vector<int32_t> kof;       // [ndm]
+  std::vector<double> delay_ms;   // [ndm] Eq. 1 across the band (lowest to highest centre), ms
   int64_t max_delay = 0, L = 0;
 
   // ---- derived layout -----------------------------------------------------

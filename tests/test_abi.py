@@ -137,3 +137,13 @@ def test_tile_q1_that_does_not_fit_is_unsupported(tx):
     with pytest.raises(tx.TxError) as e:
         tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 1, wl.widths, wl.nsamp, tile_q1=256)
     assert e.value.code == -8
+
+
+@pytest.mark.parametrize("mk", [synth.small_workload, synth.meerkat_l_workload])
+def test_delay_table_equals_oracle(tx, mk):
+    """The clustering axis: Eq. 1 across the band, identical to the last bit."""
+    from oracle import cluster as CL
+    wl = mk()
+    plan = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp)
+    ref = CL.delay_ms(wl.dms, float(wl.freqs_mhz.min()), float(wl.freqs_mhz.max()))
+    assert np.array_equal(plan.delay_table(), ref)

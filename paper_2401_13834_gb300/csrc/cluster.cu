@@ -59,6 +59,7 @@ struct tx_clusterer {
   double *x = nullptr, *y = nullptr;    // canonical coordinates
   unsigned long long* ckey = nullptr;   // cell keys sorted
   int32_t* cidx = nullptr;              // canonical index of each sorted cell entry
+  float *xs = nullptr, *ys = nullptr;   // per sorted entry: coordinates relative to its cell corner
   int32_t* core = nullptr;
   int32_t* parent = nullptr;
   int32_t* label = nullptr;
@@ -106,31 +107,58 @@ __device__ __forceinline__ int lower_bound(const unsigned long long* __restrict_
   return lo;
 }
 
-// Calls f(q) for every other point q within r of canonical point j.
+// Calls f(q) for every other point q within r of canonical point j, in cell
+// order; f returns false to stop early. The test is
+//   (x_q - x_j)^2 + (y_q - y_j)^2 <= r^2     in IEEE double,
+// screened first in float on coordinates relative to the cell corner (errors
+// below 1e-6 r^2): only pairs within 1e-5 r^2 of the radius take the double
+// test, so every decision is the double one.
 template <typename F>
 __device__ __forceinline__ void for_neighbours(const tx_clusterer& C, int n, int j, F&& f) {
   const double xj = C.x[j], yj = C.y[j];
   const double r2 = __dmul_rn(C.r, C.r);
+  const float r2f = (float)r2, lo2 = r2f * (1.0f - 1e-5f), hi2 = r2f * (1.0f + 1e-5f);
+  const float cellf = (float)C.cell;
   const long long cx = (long long)floor(xj / C.cell), cy = (long long)floor(yj / C.cell);
+  const float xjl = (float)(xj - (double)cx * C.cell), yjl = (float)(yj - (double)cy * C.cell);
   for (long long dx = -1; dx <= 1; ++dx) {
     if (cx + dx < 0) continue;
     const unsigned long long row = (unsigned long long)(cx + dx) << 32;
     const unsigned long long lo = row | (unsigned long long)(cy > 0 ? cy - 1 : 0);
     const unsigned long long hi = row | (unsigned long long)(cy + 1);
-    for (int e = lower_bound(C.ckey, n, lo); e < n && C.ckey[e] <= hi; ++e) {
+    for (int e = lower_bound(C.ckey, n, lo); e < n; ++e) {
+      const unsigned long long key = C.ckey[e];
+      if (key > hi) break;
+      const float ddx = C.xs[e] - xjl + (float)dx * cellf;
+      const float ddy = C.ys[e] - yjl + (float)((long long)(uint32_t)key - cy) * cellf;
+      const float d2f = ddx * ddx + ddy * ddy;
+      if (d2f > hi2) continue;
       const int q = C.cidx[e];
       if (q == j) continue;
-      const double ddx = __dsub_rn(C.x[q], xj), ddy = __dsub_rn(C.y[q], yj);
-      if (__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) <= r2) f(q);
+      if (d2f >= lo2) {  // near the radius: decide in double
+        const double gx = __dsub_rn(C.x[q], xj), gy = __dsub_rn(C.y[q], yj);
+        if (!(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)) <= r2)) continue;
+      }
+      if (!f(q)) return;
     }
   }
+}
+
+// Cell-relative float coordinates of each sorted entry.
+__global__ void k_cl_local(const tx_clusterer C, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int q = C.cidx[e];
+  const unsigned long long key = C.ckey[e];
+  C.xs[e] = (float)(C.x[q] - (double)(key >> 32) * C.cell);
+  C.ys[e] = (float)(C.y[q] - (double)(uint32_t)key * C.cell);
 }
 
 __global__ void k_cl_core(const tx_clusterer C, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int cnt = 0;
-  for_neighbours(C, n, j, [&](int) { ++cnt; });
+  for_neighbours(C, n, j, [&](int) { return ++cnt <= C.k; });  // stop once core
   C.core[j] = cnt > C.k;
   C.parent[j] = j;
   C.cnt[j] = 0;
@@ -157,8 +185,10 @@ __global__ void k_cl_union(const tx_clusterer C, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n || !C.core[j]) return;
   for_neighbours(C, n, j, [&](int q) {
-    if (q >= j || !C.core[q]) return;  // each core pair once
-    int a = cl_find(C.parent, j), b = cl_find(C.parent, q);
+    if (q >= j || !C.core[q]) return true;  // each core pair once
+    int a = cl_find(C.parent, j);
+    if (((volatile int32_t*)C.parent)[q] == a) return true;  // already joined
+    int b = cl_find(C.parent, q);
     while (a != b) {
       if (a < b) { const int t = a; a = b; b = t; }
       // link the larger root a under the smaller root b
@@ -167,6 +197,7 @@ __global__ void k_cl_union(const tx_clusterer C, int n) {
       a = cl_find(C.parent, a);
       b = cl_find(C.parent, b);
     }
+    return true;
   });
 }
 
@@ -182,6 +213,7 @@ __global__ void k_cl_label_border(const tx_clusterer C, int n) {
   int best = INT32_MAX;
   for_neighbours(C, n, j, [&](int q) {
     if (C.core[q]) best = min(best, C.label[q]);
+    return true;
   });
   C.label[j] = best == INT32_MAX ? -1 : best;
 }
@@ -282,6 +314,8 @@ int32_t tx_clusterer_create(const tx_plan* p, double radius_ms, int32_t k, int64
   if (!rc) rc = dalloc(&C->thi, n);
   if (!rc) rc = dalloc(&C->flag, n);
   if (!rc) rc = dalloc(&C->pos, n);
+  if (!rc) rc = dalloc(&C->xs, n);
+  if (!rc) rc = dalloc(&C->ys, n);
   if (!rc && cudaMemcpy(C->table, p->delay_ms.data(), p->delay_ms.size() * sizeof(double),
                         cudaMemcpyHostToDevice) != cudaSuccess) {
     set_error("delay table upload failed");
@@ -329,6 +363,7 @@ int32_t tx_cluster_run(tx_clusterer* C, const tx_cand* d_cands, int64_t n, tx_cl
   TX_CUDA(cub::DeviceRadixSort::SortPairs(C->temp, tb, C->key_a, ck, C->val_a, ci, ni, 0, 64, st));
   C->ckey = ck;
   C->cidx = ci;
+  k_cl_local<<<grid, kThreads, 0, st>>>(*C, ni);
   // 3-5. core flags, union-find, labels
   k_cl_core<<<grid, kThreads, 0, st>>>(*C, ni);
   k_cl_union<<<grid, kThreads, 0, st>>>(*C, ni);
@@ -357,7 +392,7 @@ void tx_clusterer_destroy(tx_clusterer* C) {
   for (void* q : {(void*)C->table, (void*)C->key_a, (void*)C->key_b, (void*)C->val_a, (void*)C->val_b, (void*)C->x,
                   (void*)C->y, (void*)C->core, (void*)C->parent, (void*)C->label, (void*)C->cnt, (void*)C->rep,
                   (void*)C->dlo, (void*)C->dhi, (void*)C->tlo, (void*)C->thi, (void*)C->flag, (void*)C->pos,
-                  C->temp})
+                  (void*)C->xs, (void*)C->ys, C->temp})
     cudaFree(q);
   cudaSetDevice(prev);
   delete C;

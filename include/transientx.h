@@ -406,6 +406,26 @@ int32_t tx_cluster_run(tx_clusterer* c, const tx_cand* d_cands, int64_t n, tx_cl
 
 void tx_clusterer_destroy(tx_clusterer* c);
 
+/* ---- de-dispersion plans with downsampling (Sec. 2.3, last paragraph) ----
+   At high DM the smearing inside one channel exceeds the sampling time, so
+   the DM range can be split into segments de-dispersed on downsampled data
+   (a plan per segment with sampling time f t_samp and blocks of T / f
+   samples). The paper gives no rule; the library's:
+     h_factor[d] = the largest power of two (at least 1, at most f_max) not
+                   above the Eq. 1 delay of DM d across the lowest-frequency
+                   channel (edges at its centre -+ half the channel spacing),
+                   in samples.
+   Consecutive DMs with the same factor form a segment. */
+int32_t tx_plan_segments(int32_t nchan, const double* freq_mhz, double tsamp_s, int32_t ndm, const double* dm,
+                         int32_t f_max, int32_t* h_factor);
+
+/* Averages `factor` consecutive samples of every channel, rounding half up:
+   out[t'] = (sum_{i<factor} in[factor t' + i] + factor / 2) / factor for
+   t' < nsamp / factor, in the same layout (FT [nchan][n] or TF [n][nchan]).
+   factor is a power of two <= 1024 dividing nsamp. Enqueued on `stream`. */
+int32_t tx_downsample(const uint8_t* d_in, int32_t layout, int32_t nchan, int64_t nsamp, int32_t factor,
+                      uint8_t* d_out, void* stream);
+
 /* ---- allocation-free de-dispersion (the paper has no counterpart) ----
    For callers that cannot call cudaMalloc: real-time loops that must not take
    the allocator's locks or its implicit synchronisation, hosts that embed the

@@ -103,6 +103,8 @@ def _load():
         "tx_execute_batch": (I32, [P, VP, VP, VP, VP, VP]),
         "tx_batch_read_profile": (I32, [P, VP, C.POINTER(I32)]),
         "tx_plan_delay_table": (I32, [P, VP]),
+        "tx_plan_segments": (I32, [I32, VP, C.c_double, I32, VP, I32, VP]),
+        "tx_downsample": (I32, [VP, I32, I32, I64, I32, VP, VP]),
         "tx_clusterer_create": (I32, [P, C.c_double, I32, I64, C.POINTER(P)]),
         "tx_cluster_run": (I32, [P, VP, I64, VP, VP, VP, VP, VP]),
         "tx_clusterer_destroy": (None, [P]),
@@ -482,3 +484,23 @@ def clusters_view(out, nclusters):
     """Host structured array of the cluster records."""
     n = int(nclusters.item())
     return out[:n].contiguous().cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)
+
+
+def segment_factors(freqs_mhz, tsamp_s, dms, f_max: int = 64) -> np.ndarray:
+    """Downsampling factor of every DM trial (tx_plan_segments)."""
+    f = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    d = np.ascontiguousarray(dms, dtype=np.float64)
+    out = np.zeros(d.size, dtype=np.int32)
+    _check(lib.tx_plan_segments(f.size, f.ctypes.data_as(C.c_void_p), float(tsamp_s), d.size,
+                                d.ctypes.data_as(C.c_void_p), int(f_max), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def downsample(x, layout: str, nchan: int, nsamp: int, factor: int, out=None, stream=None):
+    """tx_downsample of a uint8 CUDA tensor; returns the downsampled tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(nchan * (nsamp // factor), dtype=torch.uint8, device=x.device)
+    _check(lib.tx_downsample(_ptr(x), LAYOUTS[layout], int(nchan), int(nsamp), int(factor), _ptr(out),
+                             _stream_ptr(stream)))
+    return out

@@ -563,6 +563,29 @@ int32_t tx_execute_host(const tx_plan* p, tx_beam* b, const uint8_t* h_block, vo
 
 }  // extern "C"
 
+extern "C" {
+
+int32_t tx_downsample(const uint8_t* d_in, int32_t layout, int32_t nchan, int64_t nsamp, int32_t factor,
+                      uint8_t* d_out, void* stream) {
+  if (!d_in || !d_out || nchan < 1 || nsamp < 1 || factor < 1 || factor > 1024 || (factor & (factor - 1))) {
+    set_error("need device buffers, nchan >= 1, nsamp >= 1 and a power-of-two factor <= 1024");
+    return TX_ERR_INVALID_ARG;
+  }
+  if (layout != TX_LAYOUT_FT && layout != TX_LAYOUT_TF) { set_error("bad layout"); return TX_ERR_INVALID_ARG; }
+  if (nsamp % factor) { set_error("nsamp (%lld) is not a multiple of the factor %d", (long long)nsamp, factor); return TX_ERR_NOT_DIVISIBLE; }
+  int dev = 0, nsm = 0;
+  TX_CUDA(cudaGetDevice(&dev));
+  TX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int vec = layout == TX_LAYOUT_TF && nchan % 4 == 0 && ((uintptr_t)d_in & 3) == 0 && ((uintptr_t)d_out & 3) == 0;
+  const int64_t work = (nsamp / factor) * (vec ? nchan / 4 : nchan);
+  const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)std::max(nsm, 1) * 16);
+  k_downsample<<<std::max(grid, 1), 256, 0, (cudaStream_t)stream>>>(d_in, layout, nchan, nsamp, factor, vec, d_out);
+  TX_CUDA(cudaGetLastError());
+  return TX_OK;
+}
+
+}  // extern "C"
+
 // ---------------------------------------------------------------------------
 // Allocation-free de-dispersion
 // ---------------------------------------------------------------------------

@@ -401,6 +401,58 @@ __global__ void __launch_bounds__(256) k_offsets(const Src src, const int32_t* _
   }
 }
 
+// De-dispersion plans (Sec. 2.3, last paragraph): the block averaged over f
+// consecutive samples per channel, rounded half up, so it stays uint8:
+//   out[t'] = (sum_{i<f} in[f t' + i] + f / 2) / f,  t' < n / f.
+// Time-major blocks [t][nchan] are read four channels per 32-bit word when
+// nchan is a multiple of four (vec), byte by byte otherwise; channel-major
+// blocks [nchan][n] one output per thread.
+__global__ void __launch_bounds__(256) k_downsample(const uint8_t* __restrict__ in, int layout, int nchan, int64_t n,
+                                                    int f, int vec, uint8_t* __restrict__ out) {
+  const int64_t nout = n / f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint32_t half = (uint32_t)(f >> 1);
+  if (layout == TX_LAYOUT_TF && vec) {
+    const int nw = nchan >> 2;
+    const int64_t total = nout * nw;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+      const int64_t t = i / nw;
+      const int w = (int)(i - t * nw);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(in + t * f * nchan) + w;
+      uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      for (int k = 0; k < f; ++k) {
+        const uint32_t v = __ldg(src + (int64_t)k * nw);
+        s0 += v & 0xFFu;
+        s1 += (v >> 8) & 0xFFu;
+        s2 += (v >> 16) & 0xFFu;
+        s3 += v >> 24;
+      }
+      const uint32_t o = ((s0 + half) / f) | (((s1 + half) / f) << 8) | (((s2 + half) / f) << 16) |
+                         (((s3 + half) / f) << 24);
+      reinterpret_cast<uint32_t*>(out + t * nchan)[w] = o;
+    }
+  } else if (layout == TX_LAYOUT_TF) {
+    const int64_t total = nout * nchan;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+      const int64_t t = i / nchan;
+      const int c = (int)(i - t * nchan);
+      uint32_t sum = 0;
+      for (int k = 0; k < f; ++k) sum += in[(t * f + k) * nchan + c];
+      out[t * nchan + c] = (uint8_t)((sum + half) / f);
+    }
+  } else {
+    const int64_t total = nout * nchan;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+      const int c = (int)(i / nout);
+      const int64_t t = i - (int64_t)c * nout;
+      const uint8_t* src = in + (int64_t)c * n + t * f;
+      uint32_t sum = 0;
+      for (int k = 0; k < f; ++k) sum += src[k];
+      out[(int64_t)c * nout + t] = (uint8_t)((sum + half) / f);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // stage 1 (Sec. 2.3: de-disperse each sub-band on the coarse DM grid)
 // ---------------------------------------------------------------------------

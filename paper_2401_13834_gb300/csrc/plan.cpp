@@ -376,6 +376,28 @@ int32_t tx_geometric_widths(double ratio, int32_t wmax, int32_t* h_widths, int32
   return n;
 }
 
+int32_t tx_plan_segments(int32_t nchan, const double* freq_mhz, double tsamp_s, int32_t ndm, const double* dm,
+                         int32_t f_max, int32_t* h_factor) {
+  if (nchan < 2 || !freq_mhz || !(tsamp_s > 0.0) || ndm < 1 || !dm || f_max < 1 || !h_factor) {
+    set_error("need >= 2 channels, tsamp > 0, >= 1 DM, f_max >= 1 and an output array");
+    return TX_ERR_INVALID_ARG;
+  }
+  // lowest channel: its centre and the spacing to the next one give its edges
+  std::vector<double> f(freq_mhz, freq_mhz + nchan);
+  std::sort(f.begin(), f.end());
+  const double width = f[1] - f[0];
+  const double lo = f[0] - width / 2.0, hi = f[0] + width / 2.0;
+  if (!(lo > 0.0) || !(width > 0.0)) { set_error("channel frequencies must be distinct and positive"); return TX_ERR_INVALID_ARG; }
+  for (int i = 0; i < ndm; ++i) {
+    // Eq. 1 across the channel, in samples; the largest power of two not above it
+    const double smear = kDispersion * dm[i] * (1.0 / (lo * lo) - 1.0 / (hi * hi)) / tsamp_s;
+    int32_t fac = 1;
+    while ((double)(fac * 2) <= smear && fac * 2 <= f_max) fac *= 2;
+    h_factor[i] = fac;
+  }
+  return TX_OK;
+}
+
 int32_t tx_plan_delay_table(const tx_plan* p, double* h_delay_ms) {
   if (!p || !h_delay_ms) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
   std::memcpy(h_delay_ms, p->delay_ms.data(), p->delay_ms.size() * sizeof(double));

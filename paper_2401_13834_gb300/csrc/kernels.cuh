@@ -701,7 +701,7 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
   constexpr int VW = NW / 32 / SPLIT;                    // words per lane
   uint32_t* Se = smem2;                                  // [2][slot]
   uint32_t* So = Se + 2 * (size_t)slot;                  // [slot]
-  uint32_t* tab = So + (size_t)slot;                     // [kStage2MaxGroup][SC] word offsets from smem2
+  uint32_t* tab = So + (size_t)slot;                     // [kStage2MaxGroup][SC rounded up to even] word offsets
   __shared__ long long st1[MAXWARPS];
   __shared__ unsigned long long st2[MAXWARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -755,6 +755,7 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
     int lu;
     const BeamArgs a = locate(cur_c, u, lu);  // once per unit
     const int SC = a.SC, SWW = a.SWW, nsub = a.nsub;
+    const int SCp = (SC + 1) & ~1;  // table row stride: even, so sub-band pairs load as one uint2
     const int nchunk = (nsub + SC - 1) / SC;
     const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
     const int64_t t0 = (int64_t)tile * 2 * NW;
@@ -783,7 +784,7 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
           const int32_t emin = a.e2[(size_t)dfirst * nsub + s];
           const int off = a.e2[(size_t)(dfirst + gg) * nsub + s] - emin + (int)((t0 + emin) & 7);
           const uint32_t* base = (off & 1) ? So : cur;
-          tab[gg * SC + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
+          tab[gg * SCp + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
         }
       }
       __syncthreads();
@@ -795,13 +796,14 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       }
 
       if (g < nd) {
-        const uint32_t* t = tab + g * SC;
+        const uint32_t* t = tab + g * SCp;
         const uint32_t* Sl = smem2 + jbase + lane;
         int ss = 0;
 #pragma unroll 2
         for (; ss + 1 < ns; ss += 2) {
-          const uint32_t* r0 = Sl + t[ss];
-          const uint32_t* r1 = Sl + t[ss + 1];
+          const uint2 tt = *reinterpret_cast<const uint2*>(t + ss);
+          const uint32_t* r0 = Sl + tt.x;
+          const uint32_t* r1 = Sl + tt.y;
 #pragma unroll
           for (int v = 0; v < VW; ++v) {
             if constexpr (HALF) {
@@ -1253,7 +1255,7 @@ inline cudaError_t raise_smem_limit(const void* k, int bytes) {
 inline int box_smem_for(int wmax) { return 2 * ((kBoxTile + wmax + 8 + 3) & ~3) * 4; }
 
 // uint16 stage 2: two even-copy slots, one odd-copy slot, address table
-inline int stage2_u16_smem_for(int slot, int sc) { return (3 * slot + kStage2MaxGroup * sc) * 4; }
+inline int stage2_u16_smem_for(int slot, int sc) { return (3 * slot + kStage2MaxGroup * ((sc + 1) & ~1)) * 4; }
 
 // Warps per fine DM of the uint16 stage 2 (the plan's tile choice).
 inline int stage2_split(const tx_plan* p) { return p->split2; }

@@ -1123,6 +1123,60 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     }
     __syncthreads();
 
+    if constexpr (NWT > 0 && MODE == TX_OUT_CANDS) {
+      if (n == kBoxTile) {
+        // full tile, candidates: each thread tests outputs tid + 256 r (r < 8)
+        // and keeps its hits in a bit mask; the rare hits are written after,
+        // once per warp that has any
+        constexpr int RR = kBoxTile / kBoxThreads;
+        uint32_t mask = 0;
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          const uint32_t* Ci = C + threadIdx.x + r * kBoxThreads;
+          const uint32_t cl = Ci[0];
+          int32_t mx = INT32_MIN;
+#pragma unroll
+          for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
+          mask |= (uint32_t)(mx >= 0) << r;
+        }
+        if (__any_sync(0xffffffffu, mask != 0u)) {
+          for (int r = 0; r < RR; ++r) {
+            const int i = threadIdx.x + r * kBoxThreads;
+            const bool hit = (mask >> r) & 1u;
+            const unsigned hits = __ballot_sync(0xffffffffu, hit);
+            if (!hits) continue;
+            float best = -INFINITY;
+            int bw = 0;
+            if (hit) {
+              const uint32_t* Ci = C + i;
+              const uint32_t cl = Ci[0];
+              for (int w = 0; w < NR; ++w) {
+                const SnrConst c = cst[w];
+                const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+                if (sv > best) { best = sv; bw = w; }
+              }
+            }
+            const int leader = __ffs(hits) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (hit) {
+              const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+              if (idx < (unsigned long long)a.max_cands) {
+                tx_cand rec;
+                rec.dm_index = d;
+                rec.t = (int32_t)(t0 + i);
+                rec.w_index = bw;
+                rec.snr = best;
+                a.cands[idx] = rec;
+              }
+            }
+          }
+        }
+        continue;
+      }
+    }
+
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const uint32_t* Ci = C + i;
       const uint32_t cl = Ci[0];

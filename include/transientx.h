@@ -350,6 +350,12 @@ int32_t tx_batch_get_info(const tx_batch* batch, tx_batch_info* info);
 int32_t tx_execute_batch(tx_batch* batch, const uint8_t* const* d_blocks, void* const* d_outs,
                          int64_t* const* d_ncands, void* d_workspace, void* stream);
 
+/* Waits, polling, until the batch's last enqueued step has finished on the
+   GPU, at most timeout_us microseconds (< 0: no limit). Returns TX_OK, or
+   TX_ERR_TIMEOUT when the limit ran out first (the step keeps running and
+   can be waited for again), or TX_ERR_CUDA if the step failed. */
+int32_t tx_batch_wait(tx_batch* batch, int64_t timeout_us);
+
 /* TX_BATCH_PROFILE batches: waits for the last step, then writes the summed
    milliseconds of each phase's launches over all steps to h_ms[TX_NPHASES]
    (indexed by TX_PHASE_*) and the step count to *nsteps (may be NULL). */

@@ -14,6 +14,7 @@ INTERMS = {"u16": 0, "i32": 1, "f16": 2}
 OUTPUTS = {"cands": 0, "plane": 1, "cube": 2, "series": 3}
 STATS = {"block": 0, "running": 1}
 
+TX_ERR_TIMEOUT = -5
 TX_ERR_CAND_OVERFLOW = -6
 
 CAND_DTYPE = np.dtype([("dm_index", np.int32), ("t", np.int32), ("w_index", np.int32), ("snr", np.float32)])
@@ -102,6 +103,7 @@ def _load():
         "tx_batch_get_info": (I32, [P, C.POINTER(_BatchInfo)]),
         "tx_execute_batch": (I32, [P, VP, VP, VP, VP, VP]),
         "tx_batch_read_profile": (I32, [P, VP, C.POINTER(I32)]),
+        "tx_batch_wait": (I32, [P, I64]),
         "tx_plan_delay_table": (I32, [P, VP]),
         "tx_plan_segments": (I32, [I32, VP, C.c_double, I32, VP, I32, VP]),
         "tx_downsample": (I32, [VP, I32, I32, I64, I32, VP, VP]),
@@ -435,6 +437,15 @@ class Batch:
         op = (C.c_void_p * n)(*[o.data_ptr() for o, _ in outs])
         cp = (C.c_void_p * n)(*[0 if c is None else c.data_ptr() for _, c in outs])
         _check(lib.tx_execute_batch(self._h, bp, op, cp, _ptr(workspace), _stream_ptr(stream)))
+
+    def wait(self, timeout_s=None) -> bool:
+        """Waits for the last step; False if `timeout_s` ran out first (nothing is cancelled)."""
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        rc = lib.tx_batch_wait(self._h, us)
+        if rc == TX_ERR_TIMEOUT:
+            return False
+        _check(rc)
+        return True
 
     def read_profile(self):
         """(summed ms per phase over the profiled steps, step count)."""

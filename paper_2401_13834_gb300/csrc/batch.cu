@@ -10,10 +10,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -595,6 +597,27 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
     ++b->nblocks;
   }
   return TX_OK;
+}
+
+int32_t tx_batch_wait(tx_batch* B, int64_t timeout_us) {
+  if (!B) { set_error("null batch"); return TX_ERR_INVALID_ARG; }
+  if (!B->nsteps) return TX_OK;
+  const cudaEvent_t ev = B->done[(B->nsteps - 1) & 1];
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return TX_OK;
+    if (e != cudaErrorNotReady) {
+      set_error("waiting for the batch failed: %s", cudaGetErrorString(e));
+      return TX_ERR_CUDA;
+    }
+    const int64_t el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_us >= 0 && el >= timeout_us) {
+      set_error("the batch's last step did not finish within %lld us", (long long)timeout_us);
+      return TX_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 int32_t tx_batch_read_profile(tx_batch* B, double* h_ms, int32_t* nsteps) {

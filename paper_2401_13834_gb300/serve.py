@@ -71,6 +71,7 @@ class Server:
         self.steps = 0
         self.batch_sizes = []
         self.t0 = None
+        self.removed = set()
 
     # ---- set-up ---------------------------------------------------------------
     def add_beam(self, plan, reserve_bytes: Optional[int] = None) -> int:
@@ -85,8 +86,21 @@ class Server:
         self.next_seq.append(0)
         return bid
 
+    def remove_beam(self, beam: int) -> list:
+        """Takes a beam out of service: its blocks not yet admitted are dropped
+        (returned); a block already on the device completes normally."""
+        dropped = [j for j in self.pending if j.beam == beam]
+        self.pending = collections.deque(j for j in self.pending if j.beam != beam)
+        self.removed.add(beam)
+        return dropped
+
     # ---- requests -----------------------------------------------------------------
     def submit(self, beam: int, block, arrival: Optional[float] = None) -> Job:
+        if beam in self.removed or not 0 <= beam < len(self.beams):
+            raise ValueError(f"beam {beam} is not in service")
+        check = getattr(self.engine, "check_block", None)
+        if check is not None:
+            check(self.beams[beam][0], block)      # a malformed block is refused here, not on the GPU
         now = self.clock()
         if self.t0 is None:
             self.t0 = now
@@ -156,9 +170,14 @@ class Server:
     def idle(self) -> bool:
         return not (self.pending or self.ready or self.inflight)
 
-    def drain(self, poll_s: float = 0.0):
+    def drain(self, poll_s: float = 0.0, timeout_s: Optional[float] = None):
+        """Pumps until idle; raises TimeoutError if `timeout_s` (on the server's clock) runs out."""
+        t0 = self.clock()
         while not self.idle():
             self.pump()
+            if timeout_s is not None and self.clock() - t0 > timeout_s:
+                raise TimeoutError(f"{len(self.inflight)} steps still running and {len(self.pending)} blocks "
+                                   f"waiting after {timeout_s} s")
             if poll_s:
                 time.sleep(poll_s)
 
@@ -207,6 +226,13 @@ class TxEngine:
     def reserve_bytes(plan) -> int:
         return int(plan.workspace_bytes_compact + plan.out_bytes + 8)
 
+    def check_block(self, plan, block):
+        torch = self.torch
+        if not (isinstance(block, torch.Tensor) and block.is_cuda and block.dtype == torch.uint8
+                and block.is_contiguous() and block.numel() == plan.nchan * plan.nsamp):
+            raise ValueError(f"a block of this beam is a contiguous uint8 CUDA tensor of {plan.nchan * plan.nsamp} "
+                             "samples")
+
     def add_beam(self, bid, plan):
         self.beams[bid] = (plan, self.tx.Beam(plan, compact=True))
 
@@ -248,12 +274,19 @@ class TxEngine:
 
 class SimEngine:
     """A stand-in engine for testing the scheduling: each launch takes a given
-    time per job on a simulated clock; results are the jobs' sequence numbers."""
+    time per job on a simulated clock; results are the jobs' sequence numbers.
+    `stall` makes every launch from then on never finish (a hung step, made
+    on the host)."""
 
     def __init__(self, cost: Callable[[Any], float], clock):
         self.cost, self.clock = cost, clock
         self.plans = {}
         self.launches = []
+        self.stall = False
+
+    def check_block(self, plan, block):
+        if block is not None and block != plan.get("block", block):
+            raise ValueError("malformed block")
 
     def reserve_bytes(self, plan) -> int:
         return int(plan["reserve"])
@@ -263,7 +296,8 @@ class SimEngine:
 
     def launch(self, jobs, s):
         t = self.clock()
-        h = {"end": t + sum(self.cost(self.plans[j.beam]) for j in jobs), "jobs": list(jobs), "stream": s}
+        end = float("inf") if self.stall else t + sum(self.cost(self.plans[j.beam]) for j in jobs)
+        h = {"end": end, "jobs": list(jobs), "stream": s}
         self.launches.append(h)
         return h
 

@@ -150,3 +150,27 @@ def test_batch_rejects_what_it_cannot_run(tx):
     with pytest.raises(tx.TxError) as e:
         tx.Batch([p16], [b16], graph=True, profile=True)
     assert e.value.code == -1                        # profiling needs direct launches
+
+
+def test_batch_wait_times_out_then_completes(tx):
+    """A bounded wait on a step that cannot have finished returns a timeout
+    (the step is held back by a fixed-length spin enqueued before it: nothing
+    hangs), and an unbounded wait then sees it complete with correct results."""
+    plans = [make_plan(tx, BEAMS[0])]
+    p = plans[0]
+    X = np.random.default_rng(2).integers(0, 256, size=(p.nchan, p.overlap + p.nsamp), dtype=np.uint8)
+    beams = [tx.Beam(p)]
+    beams[0].prime(torch.from_numpy(np.ascontiguousarray(X[:, :p.overlap])).cuda())
+    batch = tx.Batch(plans, beams, graph=False)
+    ws, outs = batch.alloc_workspace(), batch.alloc_outs()
+    blk = torch.from_numpy(np.ascontiguousarray(X[:, p.overlap:])).cuda()
+    torch.cuda.synchronize()
+    torch.cuda._sleep(int(2e9))              # ~1 s of spinning on this stream, then the step
+    batch.execute([blk], outs, ws)
+    assert batch.wait(timeout_s=0.05) is False
+    assert batch.wait() is True
+    ref_beam = tx.Beam(p)
+    ref_beam.prime(torch.from_numpy(np.ascontiguousarray(X[:, :p.overlap])).cuda())
+    ref = tx.execute(p, ref_beam, blk)
+    torch.cuda.synchronize()
+    assert np.array_equal(outs[0][0].cpu().numpy(), ref.cpu().numpy())

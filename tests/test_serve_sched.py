@@ -119,3 +119,46 @@ def test_stats():
     st = srv.stats(data_seconds=lambda j: 10.0)
     assert st["blocks"] == 2 and st["p50_latency_s"] == pytest.approx(2.0)   # one step of two jobs
     assert st["real_time_factor"] == pytest.approx(20.0 / st["span_s"])
+
+
+def test_drain_deadline_on_a_hung_step():
+    """A step that never finishes (made on the host) ends drain() with
+    TimeoutError at the deadline instead of waiting forever."""
+    srv, eng, clk, ids = make(1000, cost=1.0, reserves=(10,))
+    eng.stall = True
+    srv.submit(ids[0], block=None)
+
+    class Tick:  # the server's clock advances as it polls
+        def __call__(self):
+            clk.t += 0.5
+            return clk.t
+    srv.clock = Tick()
+    with pytest.raises(TimeoutError):
+        srv.drain(timeout_s=10.0)
+    assert len(srv.inflight) == 1            # the hung step is still accounted for
+
+
+def test_beam_removed_mid_stream():
+    srv, eng, clk, ids = make(15, cost=1.0, reserves=(10, 10))
+    for k in range(3):
+        srv.submit(ids[0], block=None)
+        srv.submit(ids[1], block=None)
+    srv.pump()                               # beam 0's first block admitted (budget fits one)
+    dropped = srv.remove_beam(ids[1])
+    assert len(dropped) == 3 and all(j.beam == ids[1] for j in dropped)
+    with pytest.raises(ValueError):
+        srv.submit(ids[1], block=None)
+    run(srv, clk)
+    assert sorted(j.seq for j in srv.completed) == [0, 1, 2]
+    assert all(j.beam == ids[0] for j in srv.completed)
+
+
+def test_malformed_block_refused_at_submit():
+    clk = Clock()
+    eng = SimEngine(lambda plan: 1.0, clk)
+    srv = Server(eng, 100, clock=clk)
+    b = srv.add_beam({"reserve": 10, "cost": 1.0, "block": "ok"})
+    srv.submit(b, block="ok")
+    with pytest.raises(ValueError):
+        srv.submit(b, block="short")
+    assert len(srv.pending) == 1

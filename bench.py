@@ -168,25 +168,41 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
-def kernels_sha():
-    """Hash of the kernel sources (kernels.cuh) and the single-beam launcher (kernels.cu)."""
-    h = hashlib.sha256()
-    for f in ("kernels.cuh", "kernels.cu"):
-        with open(os.path.join(ROOT, "paper_2401_13834_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+# section banner of each profiled kernel in kernels.cuh
+KERNEL_SECTIONS = {
+    "k_ingest_tf": "// ingest (",
+    "k_stage1": "// stage 1 (",
+    "k_stage2_u16": "// stage 2 (",
+    "k_boxcar": "// boxcar matched filter",
+}
+
+
+def kernel_sha(kernel):
+    """Hash of one kernel's source: its section of kernels.cuh (banner to next
+    banner) and the constants of tx_internal.h."""
+    csrc = os.path.join(ROOT, "paper_2401_13834_gb300", "csrc")
+    with open(os.path.join(csrc, "kernels.cuh")) as fh:
+        lines = fh.read().split("\n")
+    title = KERNEL_SECTIONS[kernel]
+    i = next(k for k, ln in enumerate(lines) if ln.startswith(title))
+    j = next((k for k in range(i + 2, len(lines)) if lines[k].startswith("// ----") and k + 1 < len(lines)
+              and lines[k + 1].startswith("// ") and not lines[k + 1].startswith("// ----")), len(lines))
+    h = hashlib.sha256("\n".join(lines[i:j]).encode())
+    with open(os.path.join(csrc, "tx_internal.h")) as fh:
+        h.update("\n".join(ln for ln in fh.read().split("\n") if ln.startswith("constexpr")).encode())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if taken on these kernel sources."""
+    """DRAM bytes per launch from a committed ncu summary, if taken on this kernel's source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"dram_bytes_per_launch:\s*([\d.eE+]+)", txt)
-    s = re.search(r"kernels_src_sha256_16:\s*([0-9a-f]+)", txt)
-    if not m or not s or s.group(1) != kernels_sha():
+    s = re.search(r"kernel_src_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernel_sha(kernel):
         return None
     return float(m.group(1))
 

@@ -66,7 +66,7 @@ struct BeamArgs {
   int64_t L, tail_pitch;
   double lam, gamma;
   int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
-  int32_t layout, ingest_vec, running, output, compact, tail_pad, half;
+  int32_t layout, ingest_vec, running, output, compact, tail_pad, half, box_vec;
 };
 
 // Where a kernel finds a beam's arguments (the Src template parameter).
@@ -1083,7 +1083,8 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const int n = (int)min((int64_t)kBoxTile, T - t0);
     const int N = n + a.wmax - 1;
     const SnrConst* cst = a.cst + (size_t)d * nw;
-    uint32_t* C = smb + (size_t)buf * bufw + 3;  // C[0] = P[0] = 0, C[1 + j] = D[j] -> P[1 + j]
+    // series D[j] at C[j] (16-byte aligned); the scan leaves C[k] = D[0] + ... + D[k - 1]
+    uint32_t* C = smb + (size_t)buf * bufw + 4;
     const bool fresh = d != cur_d || j != cur_j;
     if (NWT > 0 && fresh) {
 #pragma unroll
@@ -1100,11 +1101,11 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     }
     cur_d = d;
     cur_j = j;
-    if (threadIdx.x == 0) C[0] = 0u;
     if (u + 1 < u_end) issue(u + 1, buf ^ 1);
-    // inclusive scan of C[1..N] (uint32, wrap-around is harmless: window sums < 2^31)
-    const int E = (N + blockDim.x - 1) / blockDim.x;
-    const int beg = 1 + threadIdx.x * E, end = min(beg + E, N + 1);
+    // exclusive scan of C[0..N] in place (uint32, wrap-around is harmless:
+    // window sums < 2^31); D[N] (possibly not loaded) only enters sums past C[N]
+    const int E = (N + 1 + blockDim.x - 1) / blockDim.x;
+    const int beg = threadIdx.x * E, end = min(beg + E, N + 1);
     uint32_t local = 0;
     for (int i = beg; i < end; ++i) local += C[i];
     uint32_t x = local;
@@ -1118,12 +1119,78 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     uint32_t pre = x - local;
     for (int w = 0; w < warp; ++w) pre += wsum[w];
     for (int i = beg; i < end; ++i) {
-      pre += C[i];
+      const uint32_t v = C[i];
       C[i] = pre;
+      pre += v;
     }
     __syncthreads();
 
     if constexpr (NWT > 0 && MODE == TX_OUT_CANDS) {
+      if (n == kBoxTile && a.box_vec) {
+        // full tile, widths 1, 2 and multiples of 4: each thread tests the
+        // four outputs 4q .. 4q + 3 of quads q = tid + 256 r from aligned
+        // 16-byte loads of C (its own quad and the next for widths 1, 2 and
+        // 4, one more per wider width); hits go to a bit mask as below
+        constexpr int QR = kBoxTile / 4 / kBoxThreads;
+        const uint4* C4 = reinterpret_cast<const uint4*>(C);
+        uint32_t mask = 0;
+#pragma unroll
+        for (int r = 0; r < QR; ++r) {
+          const int q = threadIdx.x + r * kBoxThreads;
+          const uint4 cl = C4[q], nx = C4[q + 1];
+          int32_t m0 = (int32_t)(cl.y - cl.x) - thr[0], m1 = (int32_t)(cl.z - cl.y) - thr[0];
+          int32_t m2 = (int32_t)(cl.w - cl.z) - thr[0], m3 = (int32_t)(nx.x - cl.w) - thr[0];
+          m0 = max(m0, (int32_t)(cl.z - cl.x) - thr[1]);
+          m1 = max(m1, (int32_t)(cl.w - cl.y) - thr[1]);
+          m2 = max(m2, (int32_t)(nx.x - cl.z) - thr[1]);
+          m3 = max(m3, (int32_t)(nx.y - cl.w) - thr[1]);
+#pragma unroll
+          for (int w = 2; w < NR; ++w) {
+            const uint4 cw = C4[q + (Wr[w] >> 2)];
+            m0 = max(m0, (int32_t)(cw.x - cl.x) - thr[w]);
+            m1 = max(m1, (int32_t)(cw.y - cl.y) - thr[w]);
+            m2 = max(m2, (int32_t)(cw.z - cl.z) - thr[w]);
+            m3 = max(m3, (int32_t)(cw.w - cl.w) - thr[w]);
+          }
+          mask |= ((uint32_t)(m0 >= 0) | ((uint32_t)(m1 >= 0) << 1) | ((uint32_t)(m2 >= 0) << 2) |
+                   ((uint32_t)(m3 >= 0) << 3)) << (4 * r);
+        }
+        if (__any_sync(0xffffffffu, mask != 0u)) {
+          for (int r = 0; r < 4 * QR; ++r) {
+            const int i = 4 * (threadIdx.x + (r >> 2) * kBoxThreads) + (r & 3);
+            const bool hit = (mask >> r) & 1u;
+            const unsigned hits = __ballot_sync(0xffffffffu, hit);
+            if (!hits) continue;
+            float best = -INFINITY;
+            int bw = 0;
+            if (hit) {
+              const uint32_t* Ci = C + i;
+              const uint32_t cl = Ci[0];
+              for (int w = 0; w < NR; ++w) {
+                const SnrConst c = cst[w];
+                const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+                if (sv > best) { best = sv; bw = w; }
+              }
+            }
+            const int leader = __ffs(hits) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (hit) {
+              const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+              if (idx < (unsigned long long)a.max_cands) {
+                tx_cand rec;
+                rec.dm_index = d;
+                rec.t = (int32_t)(t0 + i);
+                rec.w_index = bw;
+                rec.snr = best;
+                a.cands[idx] = rec;
+              }
+            }
+          }
+        }
+        continue;
+      }
       if (n == kBoxTile) {
         // full tile, candidates: each thread tests outputs tid + 256 r (r < 8)
         // and keeps its hits in a bit mask; the rare hits are written after,
@@ -1343,6 +1410,7 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.cst = reinterpret_cast<SnrConst*>(ws + p->ws_const);
   a.hoff = reinterpret_cast<int32_t*>(ws + p->ws_hoff);
   a.half = p->interm == TX_INTERM_F16;
+  a.box_vec = p->box_vec;
   a.run = b->run;
   a.d1 = p->dev.d1;
   a.abase = p->dev.abase;

@@ -110,6 +110,8 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->dm.assign(d->dm, d->dm + d->ndm);
   p->widths.assign(d->widths, d->widths + d->nwidth);
   p->wmax = p->widths.back();
+  p->box_vec = p->nw >= 2 && p->widths[0] == 1 && p->widths[1] == 2;
+  for (int w = 2; w < p->nw; ++w) p->box_vec = p->box_vec && p->widths[w] % 4 == 0;
   // window sums (<= wmax * nchan * 255) and W * mu must fit int32
   if ((double)p->wmax * p->nchan * 255.0 >= 2147483647.0) { set_error("wmax * nchan * 255 must be < 2^31"); return TX_ERR_UNSUPPORTED; }
   // exact S2 = sum D^2 in uint64

@@ -75,6 +75,7 @@ int64_t stage1_smem_bytes(int m, int q);
 struct tx_plan {
   // ---- description -------------------------------------------------------
   int32_t nchan = 0, nsub = 0, m = 0, ndm = 0, nk = 0, group = 0, nw = 0, wmax = 0;
+  int32_t box_vec = 0;            // widths 1, 2, then multiples of 4: the boxcar's 4-output test
   int64_t T = 0;
   int32_t layout = 0, interm = 0, output = 0, stats = 0;
   float gamma = 0.f;

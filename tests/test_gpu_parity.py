@@ -321,22 +321,32 @@ def test_meerkat_full_size_sampled(tx, meerkat_case):
     _check_cands(sub, sub.size, snr, gamma, dm_indices=sample)
 
 
-@pytest.mark.parametrize("widths", [(1,), (3, 7), tuple(range(1, 17)), tuple(range(1, 21)), (1, 2, 4, 8, 16, 32, 64, 100, 200, 400, 800, 1000)])
-@pytest.mark.parametrize("output", ["cube", "plane"])
+@pytest.mark.parametrize("widths", [(1,), (3, 7), tuple(range(1, 17)), tuple(range(1, 21)), (1, 2, 4, 8, 16, 32, 64, 100, 200, 400, 800, 1000),
+                                    (1, 2), (1, 2, 8, 20, 64, 252), (2, 4, 8)])
+@pytest.mark.parametrize("output", ["cube", "plane", "cands"])
 def test_boxcar_width_sets(tx, widths, output):
-    """Every width-count code path (exact counts and the generic one) against the oracle."""
+    """Every width-count code path (exact counts and the generic one; for candidates
+    also the four-output test of widths 1, 2 and multiples of 4) against the oracle,
+    on one full 2048-output tile and a ragged one."""
     wl = synth.tiny_workload(nchan=32, nsub=4, ndm=6, nsamp=3000, widths=widths)
-    plan = make_plan(tx, wl, output=output)
+    gamma = 3.0
+    kw = dict(snr_threshold=gamma, max_cands=1 << 16) if output == "cands" else {}
+    plan = make_plan(tx, wl, output=output, **kw)
     op = oracle_plan(wl)
     X = synth.make_spectrum(wl, plan.overlap + wl.nsamp,
                             [synth.Pulse(dm=30.0, t_arr=1200.0, fwhm=12.0, amp=9.0)], seed=11)
-    (out, _, _), = run_blocks(tx, plan, X)[0]
+    (out, nc, _), = run_blocks(tx, plan, X)[0]
     snr, _ = _oracle_snr(X, op, wl.nsamp)
     if output == "cube":
         check_snr(tx.cube_view(plan, out).cpu().numpy(), snr)
-    else:
+    elif output == "plane":
         s, w = tx.plane_view(plan, out)
         _check_plane(s.cpu().numpy(), w.cpu().numpy(), snr)
+    else:
+        got, n = tx.cands_view(plan, out, nc)
+        assert 0 < n < (1 << 16)
+        assert (got["t"] < 2048).any() and (got["t"] >= 2048).any()   # hits in the full tile and the ragged one
+        _check_cands(got, n, snr, gamma)
 
 
 @pytest.mark.parametrize("q1", [32, 64, 128, 256])

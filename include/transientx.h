@@ -248,6 +248,42 @@ int32_t tx_execute_host(const tx_plan* plan, tx_beam* beam, const uint8_t* h_blo
                         void* h_out, int64_t* h_ncand, uint8_t* d_block_staging, void* d_out,
                         int64_t* d_ncand, void* d_workspace, void* stream);
 
+/* ---- pipelined host execution (Sec. 2.3 block flow, overlapped) -------------
+   A stream of one beam's blocks from host memory with up to `depth` (1..4)
+   blocks in flight: tx_pipeline_push copies a block into one of `depth`
+   device staging buffers on a copy stream of the pipeline's own and enqueues
+   its tx_execute on `stream` behind that copy; tx_pipeline_pop waits for the
+   oldest block pushed and copies its results back on a second copy stream.
+   Block k's kernels thus overlap block k + 1's host-to-device copy and block
+   k - 1's results, and a steady stream runs at the kernels' rate when the
+   copies are shorter than the kernels. The pipeline owns its staging, output,
+   counter and workspace buffers (device, about depth * (nchan * T +
+   info.out_bytes) bytes plus one workspace) and its copy streams; plan and
+   beam remain the caller's and must outlive it. One thread at a time. */
+typedef struct tx_pipeline tx_pipeline;
+
+/* The beam must belong to `plan` and live on the current device. */
+int32_t tx_pipeline_create(const tx_plan* plan, tx_beam* beam, int32_t depth, void* stream,
+                           tx_pipeline** out);
+
+/* Enqueues one block: h_block is nchan * T bytes in the plan's layout (pinned
+   host memory for an asynchronous copy), left unchanged by the caller until
+   the block's pop returns. Returns TX_ERR_BUDGET when `depth` blocks are in
+   flight already (pop first); on an error nothing is enqueued. */
+int32_t tx_pipeline_push(tx_pipeline* pipeline, const uint8_t* h_block);
+
+/* Waits, polling, at most timeout_us microseconds (< 0: no limit) for the
+   oldest block in flight and copies its results to host memory:
+     TX_OUT_CANDS: *h_ncand and min(*h_ncand, max_cands) records to h_out
+     other modes:  info.out_bytes bytes to h_out
+   Returns TX_ERR_TIMEOUT when the limit ran out first (the block stays in
+   flight: pop again), TX_ERR_INVALID_ARG when no block is in flight, and
+   TX_ERR_CAND_OVERFLOW (results kept, block popped) as tx_execute_host. */
+int32_t tx_pipeline_pop(tx_pipeline* pipeline, void* h_out, int64_t* h_ncand, int64_t timeout_us);
+
+/* Waits for the blocks in flight, then frees everything the pipeline owns. */
+void tx_pipeline_destroy(tx_pipeline* pipeline);
+
 /* ---- phase timing (CUDA events recorded on the execute's stream) ----
    Phases of one execute, in order:
      TX_PHASE_INGEST  carried tail + new block into the ring (Sec. 2.3 steps 1, 2, 4)

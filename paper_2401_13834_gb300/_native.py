@@ -111,6 +111,10 @@ def _load():
         "tx_cluster_run": (I32, [P, VP, I64, VP, VP, VP, VP, VP]),
         "tx_clusterer_destroy": (None, [P]),
         "tx_batch_destroy": (None, [P]),
+        "tx_pipeline_create": (I32, [P, P, I32, VP, C.POINTER(P)]),
+        "tx_pipeline_push": (I32, [P, VP]),
+        "tx_pipeline_pop": (I32, [P, VP, VP, I64]),
+        "tx_pipeline_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -357,6 +361,67 @@ def execute_host(plan: Plan, beam: Beam, h_block: np.ndarray, h_out: np.ndarray,
     if rc not in (0, TX_ERR_CAND_OVERFLOW):
         _check(rc)
     return int(hn[0]) if plan.output == "cands" else None
+
+
+class Pipeline:
+    """A stream of one beam's host blocks with up to ``depth`` in flight
+    (tx_pipeline_*): ``push`` enqueues a block's copy and kernels, ``pop``
+    returns the oldest block's results. Input blocks should be pinned uint8
+    tensors (or numpy arrays) of nchan * T bytes in the plan's layout, kept
+    unchanged until their pop returns. The plan and beam must outlive it.
+    """
+
+    def __init__(self, plan: Plan, beam: Beam, depth: int = 2, stream=None):
+        import torch
+        self.plan, self.beam, self.depth = plan, beam, int(depth)
+        h = C.c_void_p()
+        _check(lib.tx_pipeline_create(plan.handle, beam.handle, self.depth, _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        self._inflight = []
+        nbytes = plan.max_cands * CAND_DTYPE.itemsize if plan.output == "cands" else plan.out_bytes
+        self.h_out = torch.empty(max(nbytes, 1), dtype=torch.uint8, pin_memory=True)
+        self._hn = np.zeros(1, dtype=np.int64)
+
+    def push(self, h_block):
+        n = self.plan.nchan * self.plan.nsamp
+        if isinstance(h_block, np.ndarray):
+            assert h_block.flags.c_contiguous and h_block.nbytes == n
+            ptr = h_block.ctypes.data
+        else:
+            assert not h_block.is_cuda and h_block.is_contiguous() and h_block.numel() * h_block.element_size() == n
+            ptr = h_block.data_ptr()
+        _check(lib.tx_pipeline_push(self._h, C.c_void_p(ptr)))
+        self._inflight.append(h_block)    # keeps the block alive until its pop
+
+    def pop(self, timeout_s=None):
+        """The oldest block's results, or None if ``timeout_s`` ran out first (pop
+        again). Candidate mode: (records, n) with n the count found (records hold
+        min(n, max_cands)); other modes: the raw output bytes (pinned; copy them
+        before the next pop)."""
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        rc = lib.tx_pipeline_pop(self._h, C.c_void_p(self.h_out.data_ptr()), self._hn.ctypes.data_as(C.c_void_p), us)
+        if rc == TX_ERR_TIMEOUT:
+            return None
+        if rc not in (0, TX_ERR_CAND_OVERFLOW):
+            _check(rc)
+        self._inflight.pop(0)
+        if self.plan.output == "cands":
+            n = int(self._hn[0])
+            k = min(n, self.plan.max_cands)
+            return self.h_out.numpy()[: k * CAND_DTYPE.itemsize].view(CAND_DTYPE).copy(), n
+        return self.h_out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib.tx_pipeline_destroy(self._h)
+            self._h = None
+            self._inflight = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- decoding helpers (views of the raw output, no arithmetic) -------------

@@ -78,6 +78,8 @@ def parse_args():
     ap.add_argument("--e2e-depth", type=int, default=2, help="blocks in flight in the end-to-end pipeline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
+                    help="skip the oracle timing on every host core")
     ap.add_argument("--cluster-r", type=float, nargs="*", default=[4.0, 8.0],
                     help="clustering radii (ms) timed on the last block's candidates")
     ap.add_argument("--cluster-k", type=int, default=2)
@@ -279,10 +281,58 @@ def cpu_baseline(wl, X, gamma, budget_s):
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": ndone * T / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": ndone * T / el, "unit": UNIT, "cores": 1, "kind": "oracle", "per_group_s": el / max(groups, 1),
             "sample": f"{groups} coarse DM groups ({ndone} of {wl.ndm} DM trials, spread over the DM range) "
                       f"of one {wl.nchan}-channel x {T}-sample block: stage 1, stage 2, block statistics, "
                       f"boxcar S/N, best width and candidates; numpy, single thread, {el:.1f} s"}
+
+
+_POOL = {}
+
+
+def _oracle_pool_init(shm_name, shape, wlp, T, gamma):
+    from multiprocessing import shared_memory
+    from oracle import dedisp as O
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _POOL.update(shm=shm, X=np.ndarray(shape, dtype=np.uint8, buffer=shm.buf), op=O.SubbandPlan(*wlp), O=O, T=T,
+                 gamma=gamma)
+
+
+def _oracle_pool_task(k):
+    if k < 0:
+        return 0                                   # start-up probe
+    return oracle_group_step(_POOL["O"], _POOL["X"], _POOL["op"], _POOL["T"], k, _POOL["gamma"])
+
+
+def cpu_baseline_all_cores(wl, X, gamma, per_group_s, budget_s):
+    """The same oracle steps on every host core: one process per core (spawned,
+    the block in shared memory), coarse DM groups spread over the processes;
+    the whole block when it fits the budget, else an evenly spread subset."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    from oracle import dedisp as O
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    op = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, 0, wl.widths)
+    ngroups = int(min(op.nk, max(cores, budget_s * cores / max(per_group_s, 1e-3))))
+    ks = np.linspace(0, op.nk - 1, ngroups).astype(int).tolist()
+    shm = shared_memory.SharedMemory(create=True, size=X.nbytes)
+    try:
+        np.ndarray(X.shape, dtype=np.uint8, buffer=shm.buf)[...] = X
+        wlp = (wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, 0, wl.widths)
+        with mp.get_context("spawn").Pool(cores, _oracle_pool_init, (shm.name, X.shape, wlp, wl.nsamp, gamma)) as pool:
+            limit = 120.0 + 4.0 * budget_s                                 # a stuck pool must not stall the bench
+            pool.map_async(_oracle_pool_task, [-1] * cores, chunksize=1).get(limit)   # every process up
+            t0 = time.perf_counter()
+            ndone = sum(pool.map_async(_oracle_pool_task, ks, chunksize=1).get(limit))
+            el = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+    whole = ngroups == op.nk
+    return {"value": ndone * wl.nsamp / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{'the whole block' if whole else f'{ngroups} coarse DM groups'} ({ndone} of {wl.ndm} DM "
+                       f"trials) of one {wl.nchan}-channel x {wl.nsamp}-sample block, the same oracle steps, one "
+                       f"spawned process per core, {el:.1f} s")}
 
 
 def run_reference(args):
@@ -542,6 +592,13 @@ def run_ours(args):
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(wl, X[:, :L + T], args.gamma, args.cpu_seconds)
+            if args.cpu_all_cores:
+                try:
+                    cpu["all_cores"] = cpu_baseline_all_cores(wl, np.ascontiguousarray(X[:, :L + T]), args.gamma,
+                                                              cpu["per_group_s"], args.cpu_seconds)
+                except Exception as e:                                    # noqa: BLE001 (reported, not fatal)
+                    cpu["all_cores"] = {"value": None, "error": f"{type(e).__name__}: {e}"}
+            cpu.pop("per_group_s", None)
         # ingest is one launch, two when the block wraps the ring's end; then
         # stage 1, stage 2, statistics and the boxcar
         head, launches = plan.ring_head0, 0
@@ -800,6 +857,7 @@ def run_batched(args):
         cpu = None
         if host0 is not None and world == 1:
             cpu = cpu_baseline(wls[0], host0, args.gamma, args.cpu_seconds)
+            cpu.pop("per_group_s", None)
             cpu["sample"] = f"beam 0 ({wls[0].name}): " + cpu["sample"]
         shapes = {}
         for wl in wls:

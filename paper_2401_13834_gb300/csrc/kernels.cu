@@ -77,6 +77,7 @@ int do_upload(tx_plan* p) {
   if ((rc = upload(&p->dev.e2, p->e2))) return rc;
   if ((rc = upload(&p->dev.widths, p->widths))) return rc;
   if ((rc = upload(&p->dev.items1, p->items1))) return rc;
+  if ((rc = upload(&p->dev.tab1, p->tab1))) return rc;
   const int s1 = (int)stage1_smem_bytes(p->m, p->q1);
   switch (p->q1) {
     case 256: rc = set_stage1_attr_for<256>(p, s1); break;
@@ -215,6 +216,7 @@ void tx_plan_destroy(tx_plan* p) {
     cudaFree(p->dev.e2);
     cudaFree(p->dev.widths);
     cudaFree(p->dev.items1);
+    cudaFree(p->dev.tab1);
     cudaSetDevice(prev);
   }
   delete p;

@@ -56,6 +56,7 @@ struct BeamArgs {
   const int32_t* e2;             // [ndm][nsub]
   const int32_t* widths;         // [nw]
   const Stage1Item* items;       // stage-1 work items of the plan
+  const int32_t* tab1;           // their precomputed offset tables (window phase tab1_phase)
   float* outf;                   // cube / plane S/N
   uint8_t* outw;                 // plane best-width index
   tx_cand* cands;                // candidate records
@@ -66,7 +67,7 @@ struct BeamArgs {
   int64_t L, tail_pitch;
   double lam, gamma;
   int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
-  int32_t layout, ingest_vec, running, output, compact, tail_pad, half, box_vec;
+  int32_t layout, ingest_vec, running, output, compact, tail_pad, half, box_vec, tab1_phase;
 };
 
 // Where a kernel finds a beam's arguments (the Src template parameter).
@@ -614,6 +615,15 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const int32_t* d1kb = a.d1 + (size_t)it.kb * a.nchan + c0;
     cp_async_wait_all();
     __syncthreads();
+    // the item's offset table: precomputed for this window phase (copied
+    // while the staging transform runs), else built after it
+    const bool pre = a.tab1 != nullptr && (int)(a.start & 15) == a.tab1_phase;
+    if (pre) {
+      const int nq = nkk * TS / 4;
+      const int32_t* src_t = a.tab1 + it.tab;
+      for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(tab + 4 * q, src_t + 4 * q);
+      cp_async_commit();
+    }
     // raw -> four-quarter words; lane g builds words 4g .. 4g + 3 of a channel
     const int n4 = (Q + it.span + 15 + 3) >> 2;
     for (int c = warp; c < m; c += kStage1Warps) {
@@ -636,10 +646,14 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       }
     }
     // word offset of S[c][a_c + d1[k][c] - d1[kb][c]] for every (k, c)
-    for (int kk = warp; kk < nkk; kk += kStage1Warps) {
-      const int32_t* d1k = a.d1 + (size_t)(it.kb + kk) * a.nchan + c0;
-      for (int c = lane; c < m; c += 32)
-        tab[kk * TS + c] = (uint32_t)(c * SW + (wstart(a, it, c) & 15) + d1k[c] - d1kb[c]);
+    if (pre) {
+      cp_async_wait_all();
+    } else {
+      for (int kk = warp; kk < nkk; kk += kStage1Warps) {
+        const int32_t* d1k = a.d1 + (size_t)(it.kb + kk) * a.nchan + c0;
+        for (int c = lane; c < m; c += 32)
+          tab[kk * TS + c] = (uint32_t)(c * SW + (wstart(a, it, c) & 15) + d1k[c] - d1kb[c]);
+      }
     }
     __syncthreads();
     const int next = idx + gridDim.x;
@@ -1411,6 +1425,8 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.hoff = reinterpret_cast<int32_t*>(ws + p->ws_hoff);
   a.half = p->interm == TX_INTERM_F16;
   a.box_vec = p->box_vec;
+  a.tab1 = p->dev.tab1;
+  a.tab1_phase = p->tab1_phase;
   a.run = b->run;
   a.d1 = p->dev.d1;
   a.abase = p->dev.abase;

@@ -235,6 +235,11 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->q1 = q1;
   p->span1_max = q1 - 16;
   const int64_t tt1 = 4 * (int64_t)q1;
+  // every window start of an execute is (head - L) mod R with head a multiple
+  // of 64 plus a multiple of T, and R a multiple of 64
+  p->tab1_phase = (int32_t)((16 - p->L % 16) % 16);
+  const int TS1 = (m + 3) & ~3, SW1 = kStage1StagedWords(q1);
+  p->tab1.clear();
   for (int s = 0; s < nsub; ++s) {
     int kb = 0;
     while (kb < nk) {
@@ -253,8 +258,15 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
         lo = std::min<int64_t>(lo, p->abase[(size_t)k * nsub + s]);
         hi = std::max<int64_t>(hi, (int64_t)p->abase[(size_t)k * nsub + s] + p->Pp);
       }
+      const int32_t toff = (int32_t)p->tab1.size();
+      for (int kk = 0; kk < ke - kb; ++kk)
+        for (int c = 0; c < TS1; ++c) {
+          if (c >= m) { p->tab1.push_back(0); continue; }
+          const int32_t d0 = p->d1[(size_t)kb * nchan + s * m + c];
+          p->tab1.push_back(c * SW1 + ((p->tab1_phase + d0) & 15) + p->d1[(size_t)(kb + kk) * nchan + s * m + c] - d0);
+        }
       for (int64_t t0 = floor_div(lo, tt1) * tt1; t0 < hi; t0 += tt1)
-        p->items1.push_back(Stage1Item{s, kb, ke, (int32_t)t0, span, 0, 0, 0});
+        p->items1.push_back(Stage1Item{s, kb, ke, (int32_t)t0, span, toff, 0, 0});
       kb = ke;
     }
   }

@@ -41,9 +41,11 @@ constexpr int kMaxWidths = 32;
 constexpr int kMaxWidth = 4096;
 
 // Stage-1 work item: sub-band s, coarse DMs [kb, ke), times [tau0, tau0 + 4 q1),
-// span = max over the sub-band's channels of d1[ke-1][c] - d1[kb][c].
+// span = max over the sub-band's channels of d1[ke-1][c] - d1[kb][c]; tab =
+// word offset of the item's precomputed offset table in the plan's tab1
+// (shared by the items of one (s, kb, ke) at every time).
 struct Stage1Item {
-  int32_t s, kb, ke, tau0, span, pad0, pad1, pad2;
+  int32_t s, kb, ke, tau0, span, tab, pad1, pad2;
 };
 
 // Per (fine DM, width) constants of the S/N normalisation (Eq. 5):
@@ -65,6 +67,7 @@ struct DevicePlan {
   int32_t* e2 = nullptr;         // [ndm][nsub]
   int32_t* widths = nullptr;     // [nw]
   Stage1Item* items1 = nullptr;  // [n_items1]
+  int32_t* tab1 = nullptr;       // stage-1 offset tables of the item groups
 };
 
 void set_error(const char* fmt, ...);
@@ -111,6 +114,12 @@ struct tx_plan {
   int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
   int32_t ntile3 = 0;             // boxcar tiles over [0, T)
   std::vector<tx::Stage1Item> items1;
+  // stage-1 offset tables, per (s, kb, ke): rows kk < ke - kb of (m + 3) & ~3
+  // words, word c = c * staged words + ((tab1_phase + d1[kb][c]) & 15) +
+  // d1[kb + kk][c] - d1[kb][c]; valid for executes whose window start has
+  // tab1_phase as its residue mod 16 (every block when T is a multiple of 16)
+  std::vector<int32_t> tab1;
+  int32_t tab1_phase = 0;
 
   // ---- workspace carve-up (bytes) -------------------------------------------
   int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_hoff = 0, ws_bytes = 0;

@@ -136,6 +136,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -538,20 +541,28 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 
 // Persistent blocks walk the work items (sub-band s, coarse DMs [kb, ke),
 // absolute times [tau0, tau0 + 4Q)) of the plan, or in a batch the members'
-// items in turn (unit u of member j is item u - off[j] of its plan). For each item the channels' input windows (from 16-byte aligned ring
-// positions) are copied with cp.async into a raw buffer while the previous
-// item is being summed, then rearranged so that shared word S[c][j] holds
-// channel c's samples at raw offsets j + qQ in byte q (q = 0..3). For coarse
-// DM k the output word j is sum_c S[c][j + a_c + d1[k][c] - d1[kb][c]] (a_c
-// the window's misalignment): four outputs per 32-bit load whatever the
-// delays. Sums use the byte-lane identity
+// items in turn (unit u of member j is item u - off[j] of its plan). For each
+// item the channels' input windows (from 16-byte aligned ring positions) are
+// copied with cp.async into a raw buffer while the previous item is being
+// summed, then rearranged so that shared word S[c][j] holds channel c's
+// samples at raw offsets j + qQ in byte q (q = 0..3). For coarse DM k the
+// output word j is sum_c S[c][j + a_c + d1[k][c] - d1[kb][c]] (a_c the
+// window's misalignment): four outputs per 32-bit load whatever the delays.
+// Sums use the byte-lane identity
 //   sum w = sum(lo lanes) + 256 * sum(hi lanes)  (mod 2^32)
 // with the hi lanes (bytes 1, 3) accumulated separately as 16-bit lanes,
 // exact for up to 257 channels per sub-band. Warps take (coarse DM, part of
 // the tile) tasks; a chunk with few coarse DMs splits each tile between 2, 4
 // or 8 warps. Shared memory is laid out for mL channels (the largest sub-band
 // of the launch), so an item's prefetch never overlaps the previous item's
-// staged words or table.
+// staged words or table. Nothing an item needs is fetched by a dependent
+// global load between barriers: a block's k-th item is blockIdx.x + k *
+// gridDim.x; its descriptor is copied to shared memory two items ahead and
+// its channels' delays d1[kb][c] one item ahead (both with cp.async), so that
+// the next item's windows are issued from shared memory; the offset table
+// and the P-row bases of the item's coarse DMs come precomputed with the
+// plan (copied in during the staging transform) whenever the window phase
+// matches, else they are built after the transform.
 template <int Q, typename PT, typename Src, bool HALF = false>
 __global__ void __launch_bounds__(kStage1Warps * 32, 1)
 k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nitems,
@@ -561,37 +572,54 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
   constexpr int NCH = RB / 16;
   constexpr int V = Q / 32;
+  const int TSL = (mL + 3) & ~3;
   uint32_t* S = reinterpret_cast<uint32_t*>(smem1);
   uint8_t* raw = smem1 + (size_t)mL * SW * 4;
-  uint32_t* tab = reinterpret_cast<uint32_t*>(raw + (size_t)mL * RB);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(raw + (size_t)mL * RB);   // [kStage1MaxCoarse][TS] offsets
+  int32_t* tabase = reinterpret_cast<int32_t*>(tab + (size_t)kStage1MaxCoarse * TSL);  // P-row base per coarse DM
+  Stage1Item* iq = reinterpret_cast<Stage1Item*>(tabase + kStage1MaxCoarse);          // items k, k+1, k+2
+  int32_t* wrow = reinterpret_cast<int32_t*>(iq + 3);                                  // [2][TSL] d1[kb][c]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // physical ring position of channel c's first wanted sample for an item
-  auto wstart = [&](const BeamArgs& a, const Stage1Item& it, int c) -> int {
-    int64_t p = a.start + it.tau0 + a.d1[(size_t)it.kb * a.nchan + it.s * a.m + c];
-    while (p >= a.R) p -= a.R;
-    return (int)p;
-  };
-  MemberCursor cur_c, cur_i;  // items being summed / being prefetched
-  auto locate = [&](MemberCursor& c, int u, Stage1Item& it) -> BeamArgs {
-    int lu = u;
-    BeamArgs a;
+  MemberCursor cur_c, cur_n, cur_f;  // items being summed / next (prefetched) / two ahead
+  auto locate = [&](MemberCursor& c, int u, int& lu) -> BeamArgs {
     if constexpr (Src::kBatch) {
       c.seek(uoff, umem, nmem, u);
       lu = u - c.lo;
-      a = src.get(c.beam);
+      return src.get(c.beam);
     } else {
-      a = src.get(0);
+      lu = u;
+      return src.get(0);
     }
-    it = a.items[lu];
-    return a;
   };
-  auto issue = [&](int idx) {
-    Stage1Item it;
-    const BeamArgs a = locate(cur_i, idx, it);
+  // descriptor of item u into slot sl
+  auto fetch_item = [&](int u, int sl) {
+    if (u >= nitems) return;
+    int lu;
+    const BeamArgs a = locate(cur_f, u, lu);
+    if (threadIdx.x < 2)
+      cp_async16(reinterpret_cast<uint8_t*>(iq + sl) + 16 * threadIdx.x,
+                 reinterpret_cast<const uint8_t*>(a.items + lu) + 16 * threadIdx.x);
+  };
+  // delays d1[kb][c] of item u (descriptor in slot sl) into row w
+  auto fetch_row = [&](int u, int sl, int w) {
+    if (u >= nitems) return;
+    int lu;
+    const BeamArgs a = locate(cur_n, u, lu);
+    const Stage1Item& it = iq[sl];
+    const int32_t* d1kb = a.d1 + (size_t)it.kb * a.nchan + it.s * a.m;
+    for (int c = threadIdx.x; c < a.m; c += blockDim.x) cp_async4(wrow + w * TSL + c, d1kb + c);
+  };
+  // input windows of item u (descriptor in slot sl, delays in row w)
+  auto issue = [&](int u, int sl, int w) {
+    int lu;
+    const BeamArgs a = locate(cur_n, u, lu);
+    const Stage1Item& it = iq[sl];
     const int R = (int)a.R;
     for (int c = warp; c < a.m; c += kStage1Warps) {
-      const int pa = wstart(a, it, c) & ~15;
+      int64_t p = a.start + it.tau0 + wrow[w * TSL + c];
+      while (p >= R) p -= R;
+      const int pa = (int)p & ~15;
       const uint8_t* row = a.ring + (size_t)(it.s * a.m + c) * R;
       uint8_t* dst = raw + (size_t)c * RB;
       for (int ch = lane; ch < NCH; ch += 32) {
@@ -603,27 +631,43 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     cp_async_commit();
   };
 
-  int idx = blockIdx.x;
-  if (idx < nitems) issue(idx);
-  while (idx < nitems) {
-    Stage1Item it;
-    const BeamArgs a = locate(cur_c, idx, it);
+  const int G = gridDim.x;
+  const int u0 = blockIdx.x;
+  if (u0 >= nitems) return;
+  fetch_item(u0, 0);
+  fetch_item(u0 + G, 1);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  fetch_row(u0, 0, 0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  issue(u0, 0, 0);
+  for (int k = 0, u = u0; u < nitems; ++k, u += G) {
+    const int sl = k % 3, sl1 = (k + 1) % 3, sl2 = (k + 2) % 3;
+    int lu;
+    const BeamArgs a = locate(cur_c, u, lu);
+    cp_async_wait_all();
+    __syncthreads();  // this item's windows, descriptor and delays landed; the previous item is done
+    const Stage1Item it = iq[sl];
     const int m = a.m;
     const int TS = (m + 3) & ~3;                 // offset-table row stride (16-byte aligned quads)
     const int c0 = it.s * m;
     const int nkk = it.ke - it.kb;
-    const int32_t* d1kb = a.d1 + (size_t)it.kb * a.nchan + c0;
-    cp_async_wait_all();
-    __syncthreads();
-    // the item's offset table: precomputed for this window phase (copied
-    // while the staging transform runs), else built after it
+    // one group: this item's precomputed table and row bases, the descriptor
+    // two items ahead, the delays of the next item
     const bool pre = a.tab1 != nullptr && (int)(a.start & 15) == a.tab1_phase;
     if (pre) {
       const int nq = nkk * TS / 4;
       const int32_t* src_t = a.tab1 + it.tab;
       for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(tab + 4 * q, src_t + 4 * q);
-      cp_async_commit();
+      const int32_t* src_b = src_t + nkk * TS;
+      for (int q = threadIdx.x; q < (nkk + 3) / 4; q += blockDim.x) cp_async16(tabase + 4 * q, src_b + 4 * q);
     }
+    fetch_item(u + 2 * G, sl2);
+    fetch_row(u + G, sl1, (k + 1) & 1);
+    cp_async_commit();
     // raw -> four-quarter words; lane g builds words 4g .. 4g + 3 of a channel
     const int n4 = (Q + it.span + 15 + 3) >> 2;
     for (int c = warp; c < m; c += kStage1Warps) {
@@ -645,19 +689,21 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         *reinterpret_cast<uint4*>(srow + j) = w;
       }
     }
-    // word offset of S[c][a_c + d1[k][c] - d1[kb][c]] for every (k, c)
-    if (pre) {
-      cp_async_wait_all();
-    } else {
+    if (!pre) {
+      // word offset of S[c][a_c + d1[k][c] - d1[kb][c]] for every (k, c), and the row bases
+      const int32_t* d1kb = wrow + (k & 1) * TSL;
       for (int kk = warp; kk < nkk; kk += kStage1Warps) {
         const int32_t* d1k = a.d1 + (size_t)(it.kb + kk) * a.nchan + c0;
-        for (int c = lane; c < m; c += 32)
-          tab[kk * TS + c] = (uint32_t)(c * SW + (wstart(a, it, c) & 15) + d1k[c] - d1kb[c]);
+        for (int c = lane; c < m; c += 32) {
+          const int32_t wa = (int32_t)((a.start + it.tau0 + d1kb[c]) & 15);
+          tab[kk * TS + c] = (uint32_t)(c * SW + wa + d1k[c] - d1kb[c]);
+        }
       }
+      for (int kk = threadIdx.x; kk < nkk; kk += blockDim.x) tabase[kk] = a.abase[(size_t)(it.kb + kk) * a.nsub + it.s];
     }
+    cp_async_wait_all();
     __syncthreads();
-    const int next = idx + gridDim.x;
-    if (next < nitems) issue(next);
+    if (u + G < nitems) issue(u + G, sl1, (k + 1) & 1);
 
     const int off = HALF ? a.hoff[it.s] : 0;   // the sub-band's offset (half intermediates)
     // tasks: (coarse DM, part of the tile); split the tile when coarse DMs are few
@@ -665,10 +711,10 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     while (split < V && nkk * split * 2 <= kStage1Warps) split *= 2;
     for (int task = warp; task < nkk * split; task += kStage1Warps) {
       const int kk = task / split, part = task - kk * split;
-      const int k = it.kb + kk;
-      const int64_t ab = a.abase[(size_t)k * a.nsub + it.s];
+      const int k1 = it.kb + kk;
+      const int64_t ab = tabase[kk];
       if ((int64_t)it.tau0 + 4 * Q <= ab || (int64_t)it.tau0 >= ab + a.Pp) continue;
-      PT* prow = static_cast<PT*>(a.P) + ((size_t)k * a.nsub + it.s) * a.Pp;
+      PT* prow = static_cast<PT*>(a.P) + ((size_t)k1 * a.nsub + it.s) * a.Pp;
       const int rel0 = (int)((int64_t)it.tau0 - ab);  // |rel0| < 2^30
       const uint32_t* t = tab + kk * TS;
       if (split == 1) {
@@ -681,8 +727,6 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         if constexpr (V >= 8) stage1_sum<Q, V / 8, PT, HALF>(S, t, m, unit, lane, part * (Q / 8), prow, rel0, a.Pp, off);
       }
     }
-    __syncthreads();
-    idx = next;
   }
 }
 

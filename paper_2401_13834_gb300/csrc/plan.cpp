@@ -32,8 +32,11 @@ static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // Shared memory of the stage-1 kernel: staged words, raw prefetch buffer and
 // the offset table (rows padded to a multiple of four entries).
 int64_t stage1_smem_bytes(int m, int q) {
+  // staged words, raw windows, offset table, P-row bases, three item
+  // descriptors and two rows of delays
   return (int64_t)m * kStage1StagedWords(q) * 4 + (int64_t)m * kStage1RawBytes(q) +
-         (int64_t)kStage1MaxCoarse * ((m + 3) & ~3) * 4;
+         (int64_t)kStage1MaxCoarse * ((m + 3) & ~3) * 4 + (int64_t)kStage1MaxCoarse * 4 +
+         3 * (int64_t)sizeof(Stage1Item) + 2 * (int64_t)((m + 3) & ~3) * 4;
 }
 
 static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -265,6 +268,8 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
           const int32_t d0 = p->d1[(size_t)kb * nchan + s * m + c];
           p->tab1.push_back(c * SW1 + ((p->tab1_phase + d0) & 15) + p->d1[(size_t)(kb + kk) * nchan + s * m + c] - d0);
         }
+      for (int kk = 0; kk < ((ke - kb + 3) & ~3); ++kk)   // the coarse DMs' P-row bases
+        p->tab1.push_back(kk < ke - kb ? p->abase[(size_t)(kb + kk) * nsub + s] : 0);
       for (int64_t t0 = floor_div(lo, tt1) * tt1; t0 < hi; t0 += tt1)
         p->items1.push_back(Stage1Item{s, kb, ke, (int32_t)t0, span, toff, 0, 0});
       kb = ke;

@@ -116,8 +116,9 @@ struct tx_plan {
   std::vector<tx::Stage1Item> items1;
   // stage-1 offset tables, per (s, kb, ke): rows kk < ke - kb of (m + 3) & ~3
   // words, word c = c * staged words + ((tab1_phase + d1[kb][c]) & 15) +
-  // d1[kb + kk][c] - d1[kb][c]; valid for executes whose window start has
-  // tab1_phase as its residue mod 16 (every block when T is a multiple of 16)
+  // d1[kb + kk][c] - d1[kb][c], then abase[kb + kk][s] for kk < ke - kb
+  // (padded to 4); valid for executes whose window start has tab1_phase as
+  // its residue mod 16 (every block when T is a multiple of 16)
   std::vector<int32_t> tab1;
   int32_t tab1_phase = 0;
 

@@ -79,6 +79,7 @@ struct BatchLaunch {
   int nmem = 0, nunits = 0;                  // member beams, work units (stage 1: the plans' items)
   int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
   int layout = 0;                            // stage 1 mL, stage 2 slot words, boxcar wmaxL
+  int aux = 0;                               // stage 2 words of a group's delays
 };
 
 int64_t mod64(int64_t a, int64_t r) { return ((a % r) + r) % r; }
@@ -269,17 +270,18 @@ int build_batch(tx_batch* B, int64_t budget) {
     // Shared memory is laid out for the largest staged chunk and table of the
     // launch (which the plans size to fit, with room for the static sums); a
     // block as large as its largest group would idle warps of smaller groups.
-    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_split;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_split;
     for (int b : mem)
       by_split[{stage2_split(B->plans[b]), B->plans[b]->nsub_chunk2, stage2_threads(B->plans[b]),
-                B->plans[b]->interm == TX_INTERM_F16}].push_back(b);
+                B->plans[b]->interm == TX_INTERM_F16, B->plans[b]->e2w2}].push_back(b);
     auto s2_smem = [&](const std::vector<int>& g) {
-      int slot = 0, sc = 0;
+      int slot = 0, sc = 0, e2w = 0;
       for (int b : g) {
         slot = std::max(slot, B->plans[b]->nsub_chunk2 * B->plans[b]->sww2);
         sc = std::max(sc, B->plans[b]->nsub_chunk2);
+        e2w = std::max(e2w, B->plans[b]->e2w2);
       }
-      return std::make_pair(slot, stage2_u16_smem_for(slot, sc));
+      return std::make_tuple(slot, stage2_u16_smem_for(slot, sc, e2w), e2w);
     };
     for (auto& kv : by_split) {
       BatchLaunch L;
@@ -293,8 +295,9 @@ int build_batch(tx_batch* B, int64_t budget) {
       int threads = 0;
       for (int b : kv.second) threads = std::max(threads, stage2_threads(B->plans[b]));
       const auto sm = s2_smem(kv.second);
-      L.layout = sm.first;
-      L.smem = sm.second;
+      L.layout = std::get<0>(sm);
+      L.smem = std::get<1>(sm);
+      L.aux = std::get<2>(sm);
       if (L.smem > kSmemMax - 1024) { set_error("batched stage-2 shared memory (%d bytes) exceeds the limit", L.smem); return TX_ERR_UNSUPPORTED; }
       L.threads = threads;
       L.grid = std::min(L.nunits, nsm);
@@ -430,10 +433,10 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
   do {                                                                                                         \
     if (L.half)                                                                                                \
       k_stage2_u16<NW, 32, SP, SlotArgs, true><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem,       \
-                                                                                  L.nunits, L.layout);         \
+                                                                                  L.nunits, L.layout, L.aux);  \
     else                                                                                                       \
       k_stage2_u16<NW, 32, SP, SlotArgs, false><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem,      \
-                                                                                   L.nunits, L.layout);        \
+                                                                                   L.nunits, L.layout, L.aux); \
   } while (0)
         switch (L.split) {
           case 8: TX_B2(512, 8); break;

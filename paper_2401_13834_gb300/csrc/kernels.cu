@@ -40,7 +40,7 @@ int upload(T** dst, const std::vector<T>& v) {
 bool is16(const tx_plan* p) { return p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16; }
 
 int stage2_smem(const tx_plan* p) {
-  if (is16(p)) return stage2_u16_smem_for(p->nsub_chunk2 * p->sww2, p->nsub_chunk2);
+  if (is16(p)) return stage2_u16_smem_for(p->nsub_chunk2 * p->sww2, p->nsub_chunk2, p->e2w2);
   return p->nsub_chunk2 * p->sw2_i32 * 4;
 }
 
@@ -421,10 +421,10 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   do {                                                                                                         \
     if (half)                                                                                                  \
       k_stage2_u16<NW, 32, SP, OneBeam, true><<<grid, stage2_threads(p), stage2_smem(p), st>>>(                \
-          OneBeam{a}, nullptr, nullptr, 1, nunits, slot);                                                      \
+          OneBeam{a}, nullptr, nullptr, 1, nunits, slot, p->e2w2);                                             \
     else                                                                                                       \
       k_stage2_u16<NW, 32, SP, OneBeam, false><<<grid, stage2_threads(p), stage2_smem(p), st>>>(               \
-          OneBeam{a}, nullptr, nullptr, 1, nunits, slot);                                                      \
+          OneBeam{a}, nullptr, nullptr, 1, nunits, slot, p->e2w2);                                             \
   } while (0)
       switch (stage2_split(p)) {
         case 8: TX_S2(512, 8); break;
@@ -728,14 +728,14 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
 
   // stage 2 into the caller's series [ndm][T + W_max - 1]
   const int slot = p->nsub_chunk2 * p->sww2;
-  const int smem2 = stage2_u16_smem_for(slot, p->nsub_chunk2);
+  const int smem2 = stage2_u16_smem_for(slot, p->nsub_chunk2, p->e2w2);
   const int nunits = p->nk * p->ntile2;
   const int grid2 = std::min(nunits, std::max(nsm, 1));
 #define TX_NA_S2(NW, SP)                                                                                       \
   do {                                                                                                         \
     TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, 32, SP, OneBeam>, smem2));                          \
     k_stage2_u16<NW, 32, SP, OneBeam><<<grid2, stage2_threads(p), smem2, st>>>(OneBeam{a}, nullptr, nullptr, 1,   \
-                                                                               nunits, slot);                    \
+                                                                               nunits, slot, p->e2w2);           \
   } while (0)
   switch (stage2_split(p)) {
     case 8: TX_NA_S2(512, 8); break;

@@ -749,15 +749,19 @@ __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long
 // even or odd, is a 32-bit load feeding two outputs. Sums use
 //   sum w = sum(lo) + 65536 * sum(hi) (mod 2^32), sum(hi) = sum(w >> 16),
 // exact because every stage-2 sum is below 2^32. Shared memory holds two
-// even-copy slots and one odd-copy slot of `slot` words (the largest
-// SC * SWW of the launch) and the address table.
+// buffers of e2w words for the stage-2 delays of a unit's group (rows
+// dfirst.. of e2, copied with cp.async one unit ahead so that no delay is a
+// dependent global load between barriers), two even-copy slots and one
+// odd-copy slot of `slot` words (the largest SC * SWW of the launch) and the
+// address table.
 template <int NW, int MAXWARPS, int SPLIT, typename Src, bool HALF = false>
 __global__ void __launch_bounds__(MAXWARPS * 32, 1)
 k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
-             int slot) {
+             int slot, int e2w) {
   extern __shared__ __align__(16) uint32_t smem2[];
   constexpr int VW = NW / 32 / SPLIT;                    // words per lane
-  uint32_t* Se = smem2;                                  // [2][slot]
+  int32_t* E = reinterpret_cast<int32_t*>(smem2);        // [2][e2w] delays of a unit's group
+  uint32_t* Se = smem2 + 2 * (size_t)e2w;                // [2][slot]
   uint32_t* So = Se + 2 * (size_t)slot;                  // [slot]
   uint32_t* tab = So + (size_t)slot;                     // [kStage2MaxGroup][SC rounded up to even] word offsets
   __shared__ long long st1[MAXWARPS];
@@ -778,26 +782,35 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       return src.get(0);
     }
   };
-  // copies sub-band chunk ch of unit (k, tile) of beam a into even-copy buffer buf
-  auto issue_chunk = [&](const BeamArgs& a, int k, int64_t t0, int ch, int buf) {
+  // copies the stage-2 delays of unit u's group (rows dfirst .. dfirst + nd - 1) into E buffer eb
+  auto fetch_e2 = [&](int u, int eb) {
+    int lu;
+    const BeamArgs a = locate(cur_i, u, lu);
+    const int dfirst = (lu / a.ntile2) * a.G;
+    const int n = min(a.G, a.ndm - dfirst) * a.nsub;
+    const int32_t* src_e = a.e2 + (size_t)dfirst * a.nsub;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(E + (size_t)eb * e2w + i, src_e + i);
+  };
+  // copies sub-band chunk ch of unit (k, tile) of beam a into even-copy buffer buf (Eu: the group's delays)
+  auto issue_chunk = [&](const BeamArgs& a, int k, int64_t t0, int ch, int buf, const int32_t* Eu) {
     const int s0 = ch * a.SC, ns = min(a.SC, a.nsub - s0);
     const int nq = a.SWW >> 2;
     const uint16_t* P = static_cast<const uint16_t*>(a.P);
     uint32_t* dst = Se + (size_t)buf * slot;
     for (int ss = warp; ss < ns; ss += nwarps) {
       const int s = s0 + ss;
-      const int64_t b = (t0 + a.e2[(size_t)k * a.G * a.nsub + s]) & ~(int64_t)7;
+      const int64_t b = (t0 + Eu[s]) & ~(int64_t)7;
       const uint16_t* src = P + ((size_t)k * a.nsub + s) * a.Pp + b;
       uint32_t* d = dst + (size_t)ss * a.SWW;
       for (int q = lane; q < nq; q += 32) cp_async16(d + 4 * q, src + 8 * q);
     }
     cp_async_commit();
   };
-  auto issue_unit = [&](int u, int buf) {  // first chunk of unit u
+  auto issue_unit = [&](int u, int buf, const int32_t* Eu) {  // first chunk of unit u
     int lu;
     const BeamArgs a = locate(cur_i, u, lu);
     const int k = lu / a.ntile2, tile = lu - k * a.ntile2;
-    issue_chunk(a, k, (int64_t)tile * 2 * NW, 0, buf);
+    issue_chunk(a, k, (int64_t)tile * 2 * NW, 0, buf, Eu);
   };
 
   uint32_t aw[VW], ah[VW];   // uint16 pairs: sum of words, sum of high lanes
@@ -808,10 +821,16 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
     fl[v] = fh[v] = 0.f;
   }
   int buf = 0;
-  if ((int)blockIdx.x < nunits) issue_unit(blockIdx.x, 0);
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+  if ((int)blockIdx.x >= nunits) return;
+  fetch_e2(blockIdx.x, 0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  issue_unit(blockIdx.x, 0, E);
+  for (int u = blockIdx.x, ju = 0; u < nunits; u += gridDim.x, ++ju) {
     int lu;
     const BeamArgs a = locate(cur_c, u, lu);  // once per unit
+    const int32_t* Eu = E + (size_t)(ju & 1) * e2w;  // this unit's delays (rows dfirst ..)
     const int SC = a.SC, SWW = a.SWW, nsub = a.nsub;
     const int SCp = (SC + 1) & ~1;  // table row stride: even, so sub-band pairs load as one uint2
     const int nchunk = (nsub + SC - 1) / SC;
@@ -836,21 +855,28 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
                          __funnelshift_r(x.w, y, 16));
         }
       }
+      if (ch == 0) {
+        // the next unit's delays, one unit ahead (landed at this unit's next
+        // chunk, or waited for below when this is its only chunk)
+        if (u + (int)gridDim.x < nunits) fetch_e2(u + gridDim.x, (ju + 1) & 1);
+        cp_async_commit();
+      }
       for (int gg = warp; gg < nd; gg += nwarps) {
         for (int ss = lane; ss < ns; ss += 32) {
           const int s = s0 + ss;
-          const int32_t emin = a.e2[(size_t)dfirst * nsub + s];
-          const int off = a.e2[(size_t)(dfirst + gg) * nsub + s] - emin + (int)((t0 + emin) & 7);
+          const int32_t emin = Eu[s];
+          const int off = Eu[gg * nsub + s] - emin + (int)((t0 + emin) & 7);
           const uint32_t* base = (off & 1) ? So : cur;
           tab[gg * SCp + ss] = (uint32_t)(base - smem2) + (uint32_t)(ss * SWW + (off >> 1));
         }
       }
+      if (ch + 1 == nchunk) cp_async_wait_all();   // the next unit's delays, for its first chunk
       __syncthreads();
       // prefetch the next chunk: of this unit, else the first of the block's next unit
       if (ch + 1 < nchunk) {
-        issue_chunk(a, k, t0, ch + 1, buf ^ 1);
+        issue_chunk(a, k, t0, ch + 1, buf ^ 1, Eu);
       } else if (u + (int)gridDim.x < nunits) {
-        issue_unit(u + gridDim.x, buf ^ 1);
+        issue_unit(u + gridDim.x, buf ^ 1, E + (size_t)((ju + 1) & 1) * e2w);
       }
 
       if (g < nd) {
@@ -1434,7 +1460,9 @@ inline cudaError_t raise_smem_limit(const void* k, int bytes) {
 inline int box_smem_for(int wmax) { return 2 * ((kBoxTile + wmax + 8 + 3) & ~3) * 4; }
 
 // uint16 stage 2: two even-copy slots, one odd-copy slot, address table
-inline int stage2_u16_smem_for(int slot, int sc) { return (3 * slot + kStage2MaxGroup * ((sc + 1) & ~1)) * 4; }
+inline int stage2_u16_smem_for(int slot, int sc, int e2w) {
+  return (2 * e2w + 3 * slot + kStage2MaxGroup * ((sc + 1) & ~1)) * 4;
+}
 
 // Warps per fine DM of the uint16 stage 2 (the plan's tile choice).
 inline int stage2_split(const tx_plan* p) { return p->split2; }

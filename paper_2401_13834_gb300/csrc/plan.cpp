@@ -212,9 +212,10 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   // reads [t0 + emin, + tt2 + span2 + 16)
   p->Pp = round_up(std::max<int64_t>(last_t0 + 16 + 2 * (int64_t)p->sww2, last_t0 + 16 + tt2 + span2 + 16) + 16, 64);
   if (p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16) {
-    // double-buffered even copy + odd copy + address table
+    // two buffers of a group's delays, double-buffered even copy + odd copy + address table
+    p->e2w2 = (int32_t)round_up((int64_t)G * nsub, 4);
     const int64_t per_sub = 3 * (int64_t)p->sww2 * 4 + (int64_t)kStage2MaxGroup * 4 + 8;
-    p->nsub_chunk2 = (int32_t)std::min<int64_t>(nsub, (kSmemMax - 1024) / per_sub);
+    p->nsub_chunk2 = (int32_t)std::min<int64_t>(nsub, (kSmemMax - 1024 - 8 * (int64_t)p->e2w2) / per_sub);
   } else {
     p->sw2_i32 = (int32_t)(tt2 + span2 + 16);
     const int64_t per_sub = (int64_t)p->sw2_i32 * 4 + (int64_t)kStage2MaxGroup * 4 + 8;

@@ -112,6 +112,7 @@ struct tx_plan {
   int32_t sww2 = 0;               // stage-2 staged words per sub-band (uint16 path)
   int32_t sw2_i32 = 0;            // stage-2 staged elements per sub-band (int32 path)
   int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
+  int32_t e2w2 = 0;               // words of one stage-2 group's delays in shared memory (rounded to 4)
   int32_t ntile3 = 0;             // boxcar tiles over [0, T)
   std::vector<tx::Stage1Item> items1;
   // stage-1 offset tables, per (s, kb, ke): rows kk < ke - kb of (m + 3) & ~3

@@ -579,6 +579,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   int32_t* tabase = reinterpret_cast<int32_t*>(tab + (size_t)kStage1MaxCoarse * TSL);  // P-row base per coarse DM
   Stage1Item* iq = reinterpret_cast<Stage1Item*>(tabase + kStage1MaxCoarse);          // items k, k+1, k+2
   int32_t* wrow = reinterpret_cast<int32_t*>(iq + 3);                                  // [2][TSL] d1[kb][c]
+  int32_t* hsub = wrow + 2 * TSL;  // [2] the sub-band's offset of items k, k+1 (half intermediates)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   MemberCursor cur_c, cur_n, cur_f;  // items being summed / next (prefetched) / two ahead
@@ -601,7 +602,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       cp_async16(reinterpret_cast<uint8_t*>(iq + sl) + 16 * threadIdx.x,
                  reinterpret_cast<const uint8_t*>(a.items + lu) + 16 * threadIdx.x);
   };
-  // delays d1[kb][c] of item u (descriptor in slot sl) into row w
+  // delays d1[kb][c] of item u (descriptor in slot sl) into row w (and its sub-band's offset)
   auto fetch_row = [&](int u, int sl, int w) {
     if (u >= nitems) return;
     int lu;
@@ -609,6 +610,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const Stage1Item& it = iq[sl];
     const int32_t* d1kb = a.d1 + (size_t)it.kb * a.nchan + it.s * a.m;
     for (int c = threadIdx.x; c < a.m; c += blockDim.x) cp_async4(wrow + w * TSL + c, d1kb + c);
+    if (HALF && threadIdx.x == 0) cp_async4(hsub + w, a.hoff + it.s);
   };
   // input windows of item u (descriptor in slot sl, delays in row w)
   auto issue = [&](int u, int sl, int w) {
@@ -705,7 +707,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     __syncthreads();
     if (u + G < nitems) issue(u + G, sl1, (k + 1) & 1);
 
-    const int off = HALF ? a.hoff[it.s] : 0;   // the sub-band's offset (half intermediates)
+    const int off = HALF ? hsub[k & 1] : 0;   // the sub-band's offset (half intermediates)
     // tasks: (coarse DM, part of the tile); split the tile when coarse DMs are few
     int split = 1;
     while (split < V && nkk * split * 2 <= kStage1Warps) split *= 2;

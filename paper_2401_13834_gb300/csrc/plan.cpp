@@ -33,10 +33,10 @@ static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // the offset table (rows padded to a multiple of four entries).
 int64_t stage1_smem_bytes(int m, int q) {
   // staged words, raw windows, offset table, P-row bases, three item
-  // descriptors and two rows of delays
+  // descriptors, two rows of delays and two sub-band offsets
   return (int64_t)m * kStage1StagedWords(q) * 4 + (int64_t)m * kStage1RawBytes(q) +
          (int64_t)kStage1MaxCoarse * ((m + 3) & ~3) * 4 + (int64_t)kStage1MaxCoarse * 4 +
-         3 * (int64_t)sizeof(Stage1Item) + 2 * (int64_t)((m + 3) & ~3) * 4;
+         3 * (int64_t)sizeof(Stage1Item) + 2 * (int64_t)((m + 3) & ~3) * 4 + 16;
 }
 
 static int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }

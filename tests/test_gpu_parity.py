@@ -126,6 +126,10 @@ def test_tf_layout_matches_ft(tx):
 
 @pytest.mark.parametrize("layout", ["ft", "tf"])
 def test_streaming_blocks_and_checkpoint(tx, layout):
+    """Four blocks of one stream and a checkpoint/resume, bit-exact against the oracle.
+    T = 1000 is not a multiple of 16, so the window start's residue mod 16
+    alternates between blocks: blocks 0 and 2 use the plan's precomputed
+    stage-1 offset tables, blocks 1 and 3 the tables built in the kernel."""
     wl = synth.tiny_workload(nchan=64, nsub=8, ndm=16, nsamp=1000, dm_max=80.0)
     plan = make_plan(tx, wl, output="series", layout=layout)
     op = oracle_plan(wl)

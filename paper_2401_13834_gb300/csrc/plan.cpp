@@ -255,7 +255,8 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
       };
       int ke = kb + 1;
       while (ke < nk && ke - kb < kStage1MaxCoarse && spread(kb, ke + 1) <= p->span1_max) ++ke;
-      if (ke - kb >= 16) ke = kb + (ke - kb) / 16 * 16;  // whole rounds of the 16 warps
+      // 16 or 32 coarse DMs fill the 32 warps exactly (two or one warps per DM)
+      if (ke - kb >= 16) ke = kb + (ke - kb) / 16 * 16;
       const int32_t span = spread(kb, ke);
       int64_t lo = INT64_MAX, hi = 0;
       for (int k = kb; k < ke; ++k) {

@@ -83,8 +83,9 @@ def test_pipeline_candidates_match_block_by_block(tx, depth):
         assert key(rec) == key(rrec)
 
 
-def test_pipeline_plane_matches_block_by_block(tx):
-    plan, tail, blocks = stream_case(tx, "plane")
+@pytest.mark.parametrize("output,interm", [("plane", "u16"), ("cube", "f16"), ("series", "i32")])
+def test_pipeline_outputs_match_block_by_block(tx, output, interm):
+    plan, tail, blocks = stream_case(tx, output, interm=interm)
     ref = reference(tx, plan, tail, blocks)
     beam = tx.Beam(plan)
     beam.prime(tail)

@@ -284,6 +284,13 @@ int32_t tx_pipeline_pop(tx_pipeline* pipeline, void* h_out, int64_t* h_ncand, in
 /* Waits for the blocks in flight, then frees everything the pipeline owns. */
 void tx_pipeline_destroy(tx_pipeline* pipeline);
 
+/* Waits that the library's kernels gave up on the current device since the
+   library was loaded: a bulk copy into shared memory that had not completed
+   after the kernel's polling limit (seconds). The kernel that saw one
+   returned early and the results of that launch are not valid; 0 in normal
+   operation. Synchronises with the device. */
+int32_t tx_wait_timeouts(int64_t* count);
+
 /* ---- phase timing (CUDA events recorded on the execute's stream) ----
    Phases of one execute, in order:
      TX_PHASE_INGEST  carried tail + new block into the ring (Sec. 2.3 steps 1, 2, 4)

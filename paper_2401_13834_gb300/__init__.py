@@ -17,7 +17,7 @@ _EXPORTS = (
     "LAYOUTS", "INTERMS", "OUTPUTS", "STATS", "CAND_DTYPE", "PHASES", "TxError", "Plan", "Beam", "Timer",
     "execute", "execute_timed", "execute_host", "geometric_widths", "lib", "library_path", "version",
     "cands_view", "plane_view", "cube_view", "series_view", "dedisperse_noalloc", "Batch", "Clusterer",
-    "clusters_view", "CLUSTER_DTYPE", "segment_factors", "downsample", "Pipeline",
+    "clusters_view", "CLUSTER_DTYPE", "segment_factors", "downsample", "Pipeline", "wait_timeouts",
 )
 __all__ = list(_EXPORTS)
 

@@ -115,6 +115,7 @@ def _load():
         "tx_pipeline_push": (I32, [P, VP]),
         "tx_pipeline_pop": (I32, [P, VP, VP, I64]),
         "tx_pipeline_destroy": (None, [P]),
+        "tx_wait_timeouts": (I32, [C.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -361,6 +362,13 @@ def execute_host(plan: Plan, beam: Beam, h_block: np.ndarray, h_out: np.ndarray,
     if rc not in (0, TX_ERR_CAND_OVERFLOW):
         _check(rc)
     return int(hn[0]) if plan.output == "cands" else None
+
+
+def wait_timeouts() -> int:
+    """Waits the kernels gave up on the current device (tx_wait_timeouts); 0 in normal operation."""
+    n = C.c_int64()
+    _check(lib.tx_wait_timeouts(C.byref(n)))
+    return int(n.value)
 
 
 class Pipeline:

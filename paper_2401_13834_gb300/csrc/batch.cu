@@ -602,6 +602,17 @@ int32_t tx_execute_batch(tx_batch* B, const uint8_t* const* d_blocks, void* cons
   return TX_OK;
 }
 
+}  // extern "C"
+
+int batch_wait_timeouts(int64_t* n) {
+  int v = 0;
+  TX_CUDA(cudaMemcpyFromSymbol(&v, g_tx_wait_timeouts, sizeof(int)));
+  *n = v;
+  return TX_OK;
+}
+
+extern "C" {
+
 int32_t tx_batch_wait(tx_batch* B, int64_t timeout_us) {
   if (!B) { set_error("null batch"); return TX_ERR_INVALID_ARG; }
   if (!B->nsteps) return TX_OK;

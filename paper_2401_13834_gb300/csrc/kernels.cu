@@ -567,6 +567,17 @@ int32_t tx_execute_host(const tx_plan* p, tx_beam* b, const uint8_t* h_block, vo
 
 extern "C" {
 
+int32_t tx_wait_timeouts(int64_t* count) {
+  if (!count) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  int v = 0;
+  TX_CUDA(cudaMemcpyFromSymbol(&v, g_tx_wait_timeouts, sizeof(int)));
+  int64_t nb = 0;
+  const int rc = batch_wait_timeouts(&nb);
+  if (rc) return rc;
+  *count = v + nb;
+  return TX_OK;
+}
+
 int32_t tx_downsample(const uint8_t* d_in, int32_t layout, int32_t nchan, int64_t nsamp, int32_t factor,
                       uint8_t* d_out, void* stream) {
   if (!d_in || !d_out || nchan < 1 || nsamp < 1 || factor < 1 || factor > 1024 || (factor & (factor - 1))) {

@@ -140,6 +140,44 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+
+// Bulk (TMA) copies into shared memory, completed on an mbarrier: the
+// issuing side announces the byte count (expect_tx, one arrival) and each
+// copy completes its bytes on the barrier; waiting threads poll the phase.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this CTA's earlier generic-proxy accesses of shared memory before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared.b64 st, [%0], %1;\n\t}"
+               ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+// waits for phase `parity` of bar to complete, giving up after max_iter polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
+  for (uint32_t i = 0; i < max_iter; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr uint32_t kMbarPolls = 1u << 22;   // each poll may suspend the thread for a while: seconds in all
+
+// Waits that gave up (a copy that never completed) in this translation
+// unit's kernels; a kernel that saw one returns early and its results are not
+// valid. Read by tx_wait_timeouts.
+__device__ int g_tx_wait_timeouts = 0;
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
@@ -543,11 +581,13 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 // absolute times [tau0, tau0 + 4Q)) of the plan, or in a batch the members'
 // items in turn (unit u of member j is item u - off[j] of its plan). For each
 // item the channels' input windows (from 16-byte aligned ring positions) are
-// copied with cp.async into a raw buffer while the previous item is being
-// summed, then rearranged so that shared word S[c][j] holds channel c's
-// samples at raw offsets j + qQ in byte q (q = 0..3). For coarse DM k the
-// output word j is sum_c S[c][j + a_c + d1[k][c] - d1[kb][c]] (a_c the
-// window's misalignment): four outputs per 32-bit load whatever the delays.
+// brought into a raw buffer by bulk (TMA) copies, one per channel (two where
+// a window wraps the ring's end), completed on an mbarrier, while the
+// previous item is being summed; they are then rearranged so that shared
+// word S[c][j] holds channel c's samples at raw offsets j + qQ in byte q
+// (q = 0..3). For coarse DM k the output word j is
+// sum_c S[c][j + a_c + d1[k][c] - d1[kb][c]] (a_c the window's
+// misalignment): four outputs per 32-bit load whatever the delays.
 // Sums use the byte-lane identity
 //   sum w = sum(lo lanes) + 256 * sum(hi lanes)  (mod 2^32)
 // with the hi lanes (bytes 1, 3) accumulated separately as 16-bit lanes,
@@ -581,8 +621,10 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   int32_t* wrow = reinterpret_cast<int32_t*>(iq + 3);                                  // [2][TSL] d1[kb][c]
   int32_t* hsub = wrow + 2 * TSL;  // [2] the sub-band's offset of items k, k+1 (half intermediates)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ __align__(8) uint64_t barr;   // completion of the bulk copies of the raw windows
+  uint32_t rphase = 0u;
 
-  MemberCursor cur_c, cur_n, cur_f;  // items being summed / next (prefetched) / two ahead
+  MemberCursor cur_c, cur_n, cur_f, cur_x;  // items being summed / next (prefetched) / two ahead / announced
   auto locate = [&](MemberCursor& c, int u, int& lu) -> BeamArgs {
     if constexpr (Src::kBatch) {
       c.seek(uoff, umem, nmem, u);
@@ -613,29 +655,42 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     if (HALF && threadIdx.x == 0) cp_async4(hsub + w, a.hoff + it.s);
   };
   // input windows of item u (descriptor in slot sl, delays in row w)
+  // bulk copies of the windows (RB bytes per channel, split at the ring's end); the byte count
+  // was announced on barr before the barrier that precedes this call
   auto issue = [&](int u, int sl, int w) {
     int lu;
     const BeamArgs a = locate(cur_n, u, lu);
     const Stage1Item& it = iq[sl];
     const int R = (int)a.R;
-    for (int c = warp; c < a.m; c += kStage1Warps) {
-      int64_t p = a.start + it.tau0 + wrow[w * TSL + c];
-      while (p >= R) p -= R;
-      const int pa = (int)p & ~15;
-      const uint8_t* row = a.ring + (size_t)(it.s * a.m + c) * R;
-      uint8_t* dst = raw + (size_t)c * RB;
-      for (int ch = lane; ch < NCH; ch += 32) {
-        int q = pa + 16 * ch;  // R is a multiple of 64: a chunk never straddles the wrap
-        while (q >= R) q -= R;
-        cp_async16(dst + 16 * ch, row + q);
+    if (lane == 0) {
+      for (int c = warp; c < a.m; c += kStage1Warps) {
+        int64_t p = a.start + it.tau0 + wrow[w * TSL + c];
+        while (p >= R) p -= R;
+        const int pa = (int)p & ~15;
+        const uint8_t* row = a.ring + (size_t)(it.s * a.m + c) * R;
+        uint8_t* dst = raw + (size_t)c * RB;
+        fence_proxy_async();
+        const int first = min(RB, R - pa);
+        bulk_g2s(dst, row + pa, (uint32_t)first, &barr);
+        if (first < RB) bulk_g2s(dst + first, row, (uint32_t)(RB - first), &barr);
       }
     }
-    cp_async_commit();
+  };
+  auto announce = [&](int u) {  // thread 0: the bytes of item u's windows
+    if (threadIdx.x == 0 && u < nitems) {
+      int lu;
+      const BeamArgs a = locate(cur_x, u, lu);
+      mbar_expect_tx(&barr, (uint32_t)(a.m * RB));
+    }
   };
 
   const int G = gridDim.x;
   const int u0 = blockIdx.x;
   if (u0 >= nitems) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&barr, 1);
+    fence_mbar_init();
+  }
   fetch_item(u0, 0);
   fetch_item(u0 + G, 1);
   cp_async_commit();
@@ -644,6 +699,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   fetch_row(u0, 0, 0);
   cp_async_commit();
   cp_async_wait_all();
+  announce(u0);
   __syncthreads();
   issue(u0, 0, 0);
   for (int k = 0, u = u0; u < nitems; ++k, u += G) {
@@ -651,7 +707,17 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     int lu;
     const BeamArgs a = locate(cur_c, u, lu);
     cp_async_wait_all();
-    __syncthreads();  // this item's windows, descriptor and delays landed; the previous item is done
+    const uint32_t ph = rphase;
+    const bool landed = mbar_wait(&barr, ph, kMbarPolls);
+    rphase ^= 1u;
+    if (__syncthreads_or(!landed)) {
+      // a copy never completed: record it, give the copies in flight a last bounded wait, give up
+      if (threadIdx.x == 0) {
+        atomicAdd(&g_tx_wait_timeouts, 1);
+        mbar_wait(&barr, ph, kMbarPolls);
+      }
+      return;
+    }
     const Stage1Item it = iq[sl];
     const int m = a.m;
     const int TS = (m + 3) & ~3;                 // offset-table row stride (16-byte aligned quads)
@@ -704,6 +770,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       for (int kk = threadIdx.x; kk < nkk; kk += blockDim.x) tabase[kk] = a.abase[(size_t)(it.kb + kk) * a.nsub + it.s];
     }
     cp_async_wait_all();
+    announce(u + G);
     __syncthreads();
     if (u + G < nitems) issue(u + G, sl1, (k + 1) & 1);
 

@@ -150,3 +150,5 @@ struct tx_beam {
 
 // Implemented in kernels.cu.
 int tx_upload_plan(const tx_plan* plan);
+// Waits given up by the batched kernels on the current device (batch.cu).
+int batch_wait_timeouts(int64_t* n);

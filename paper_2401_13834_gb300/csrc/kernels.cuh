@@ -610,7 +610,6 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   extern __shared__ __align__(16) uint8_t smem1[];
   constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
-  constexpr int NCH = RB / 16;
   constexpr int V = Q / 32;
   const int TSL = (mL + 3) & ~3;
   uint32_t* S = reinterpret_cast<uint32_t*>(smem1);
@@ -812,9 +811,11 @@ __device__ __forceinline__ void warp_sum_stats(long long& s1, unsigned long long
 
 // Persistent blocks walk units (coarse group k, tile of 2 NW outputs) in
 // sub-band chunks; SPLIT warps share fine DM kG + g, each summing NW / SPLIT
-// words of the tile. A chunk's uint16 stage-1 rows are copied (cp.async,
-// double-buffered) into shared memory as 32-bit words of consecutive pairs
-// (even copy) and re-paired one element later (odd copy), so every delay,
+// words of the tile. A chunk's uint16 stage-1 rows are copied (bulk TMA
+// copies, one per row, issued by lane 0 of the warps in turn and completed on
+// the buffer's mbarrier; double-buffered) into shared memory as 32-bit words
+// of consecutive pairs (even copy) and re-paired one element later (odd
+// copy), so every delay,
 // even or odd, is a 32-bit load feeding two outputs. Sums use
 //   sum w = sum(lo) + 65536 * sum(hi) (mod 2^32), sum(hi) = sum(w >> 16),
 // exact because every stage-2 sum is below 2^32. Shared memory holds two
@@ -835,12 +836,14 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
   uint32_t* tab = So + (size_t)slot;                     // [kStage2MaxGroup][SC rounded up to even] word offsets
   __shared__ long long st1[MAXWARPS];
   __shared__ unsigned long long st2[MAXWARPS];
+  __shared__ __align__(8) uint64_t bar2[2];  // completion of the bulk copies into even buffer 0 / 1
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const int g = warp / SPLIT, part_i = warp - g * SPLIT;  // fine DM of the group, part of the tile
   const int jbase = part_i * (NW / SPLIT);
+  uint32_t phase[2] = {0u, 0u};
 
-  MemberCursor cur_c, cur_i;  // units being computed / being prefetched
+  MemberCursor cur_c, cur_i, cur_x;  // units being computed / being prefetched / announced
   auto locate = [&](MemberCursor& c, int u, int& lu) -> BeamArgs {
     if constexpr (Src::kBatch) {
       c.seek(uoff, umem, nmem, u);
@@ -860,20 +863,28 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
     const int32_t* src_e = a.e2 + (size_t)dfirst * a.nsub;
     for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(E + (size_t)eb * e2w + i, src_e + i);
   };
-  // copies sub-band chunk ch of unit (k, tile) of beam a into even-copy buffer buf (Eu: the group's delays)
+  // copies sub-band chunk ch of unit (k, tile) of beam a into even-copy buffer buf (Eu: the group's
+  // delays); its byte count was announced on the buffer's mbarrier before the barrier preceding this
   auto issue_chunk = [&](const BeamArgs& a, int k, int64_t t0, int ch, int buf, const int32_t* Eu) {
     const int s0 = ch * a.SC, ns = min(a.SC, a.nsub - s0);
-    const int nq = a.SWW >> 2;
     const uint16_t* P = static_cast<const uint16_t*>(a.P);
     uint32_t* dst = Se + (size_t)buf * slot;
-    for (int ss = warp; ss < ns; ss += nwarps) {
-      const int s = s0 + ss;
-      const int64_t b = (t0 + Eu[s]) & ~(int64_t)7;
-      const uint16_t* src = P + ((size_t)k * a.nsub + s) * a.Pp + b;
-      uint32_t* d = dst + (size_t)ss * a.SWW;
-      for (int q = lane; q < nq; q += 32) cp_async16(d + 4 * q, src + 8 * q);
+    if (lane == 0) {
+      for (int ss = warp; ss < ns; ss += nwarps) {
+        const int s = s0 + ss;
+        const int64_t b = (t0 + Eu[s]) & ~(int64_t)7;
+        fence_proxy_async();
+        bulk_g2s(dst + (size_t)ss * a.SWW, P + ((size_t)k * a.nsub + s) * a.Pp + b, (uint32_t)a.SWW * 4u, &bar2[buf]);
+      }
     }
-    cp_async_commit();
+  };
+  // thread 0: announce the bytes of chunk ch of unit u into buffer buf (before the barrier that precedes the copies)
+  auto announce = [&](int u, int ch, int buf) {
+    if (threadIdx.x != 0) return;
+    int lu;
+    const BeamArgs a = locate(cur_x, u, lu);
+    const int ns = min(a.SC, a.nsub - ch * a.SC);
+    mbar_expect_tx(&bar2[buf], (uint32_t)ns * (uint32_t)a.SWW * 4u);
   };
   auto issue_unit = [&](int u, int buf, const int32_t* Eu) {  // first chunk of unit u
     int lu;
@@ -891,9 +902,15 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
   }
   int buf = 0;
   if ((int)blockIdx.x >= nunits) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar2[0], 1);
+    mbar_init(&bar2[1], 1);
+    fence_mbar_init();
+  }
   fetch_e2(blockIdx.x, 0);
   cp_async_commit();
   cp_async_wait_all();
+  announce(blockIdx.x, 0, 0);
   __syncthreads();
   issue_unit(blockIdx.x, 0, E);
   for (int u = blockIdx.x, ju = 0; u < nunits; u += gridDim.x, ++ju) {
@@ -911,7 +928,17 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       const int s0 = ch * SC, ns = min(SC, nsub - s0);
       uint32_t* cur = Se + (size_t)buf * slot;
       cp_async_wait_all();
-      __syncthreads();
+      const uint32_t ph = phase[buf];
+      const bool landed = mbar_wait(&bar2[buf], ph, kMbarPolls);
+      phase[buf] ^= 1u;
+      if (__syncthreads_or(!landed)) {
+        // a copy never completed: record it, give the copies in flight a last bounded wait, give up
+        if (threadIdx.x == 0) {
+          atomicAdd(&g_tx_wait_timeouts, 1);
+          mbar_wait(&bar2[buf], ph, kMbarPolls);
+        }
+        return;
+      }
       // odd copy: So[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged base
       for (int ss = warp; ss < ns; ss += nwarps) {
         const uint32_t* r = cur + (size_t)ss * SWW;
@@ -940,6 +967,8 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
         }
       }
       if (ch + 1 == nchunk) cp_async_wait_all();   // the next unit's delays, for its first chunk
+      if (ch + 1 < nchunk) announce(u, ch + 1, buf ^ 1);
+      else if (u + (int)gridDim.x < nunits) announce(u + gridDim.x, 0, buf ^ 1);
       __syncthreads();
       // prefetch the next chunk: of this unit, else the first of the block's next unit
       if (ch + 1 < nchunk) {

@@ -1220,6 +1220,8 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   __shared__ uint32_t wsum[kBoxThreads / 32];
   __shared__ int32_t sW[kMaxWidths];
   __shared__ SnrConst sC[kMaxWidths];
+  __shared__ __align__(8) uint64_t barb[2];  // completion of the bulk copy into series buffer 0 / 1
+  uint32_t bph[2] = {0u, 0u};
   const int bufw = (kBoxTile + wmaxL + 8 + 3) & ~3;  // words per buffer: 4 pad + series + chunk rounding
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int u_begin = (int)((int64_t)nunits * blockIdx.x / gridDim.x);
@@ -1247,13 +1249,23 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const int nq = (n + a.wmax - 1 + 3) >> 2;  // 16-byte chunks of the series window
     const int32_t* src = a.D + (size_t)d * a.Dp + t0;
     uint32_t* dst = smb + (size_t)buf * bufw + 4;
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) cp_async16(dst + 4 * q, src + 4 * q);
-    cp_async_commit();
+    if (threadIdx.x == 0) {  // one bulk copy of the window (16-byte aligned both sides)
+      fence_proxy_async();
+      mbar_expect_tx(&barb[buf], (uint32_t)nq * 16u);
+      bulk_g2s(dst, src, (uint32_t)nq * 16u, &barb[buf]);
+    }
   };
 
   int32_t Wr[NR], thr[NR];
   int cur_d = -1, cur_j = -1;
-  if (u_begin < u_end) issue(u_begin, 0);
+  if (u_begin >= u_end) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&barb[0], 1);
+    mbar_init(&barb[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  issue(u_begin, 0);
   for (int u = u_begin, it = 0; u < u_end; ++u, ++it) {
     const int buf = it & 1;
     int lu, j;
@@ -1275,8 +1287,18 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         thr[w] = cst[w].thr;
       }
     }
-    cp_async_wait_all();
-    __syncthreads();  // this unit's series landed; the previous unit is done with sW/sC and the other buffer
+    const uint32_t ph = bph[buf];
+    const bool landed = mbar_wait(&barb[buf], ph, kMbarPolls);
+    bph[buf] ^= 1u;
+    // this unit's series landed; the previous unit is done with sW/sC and the other buffer
+    if (__syncthreads_or(!landed)) {
+      // a copy never completed: record it, give the copy in flight a last bounded wait, give up
+      if (threadIdx.x == 0) {
+        atomicAdd(&g_tx_wait_timeouts, 1);
+        mbar_wait(&barb[buf], ph, kMbarPolls);
+      }
+      return;
+    }
     if (NWT == 0 && fresh && threadIdx.x < nw) {
       sW[threadIdx.x] = a.widths[threadIdx.x];
       sC[threadIdx.x] = cst[threadIdx.x];

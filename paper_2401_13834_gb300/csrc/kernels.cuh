@@ -623,7 +623,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   __shared__ __align__(8) uint64_t barr;   // completion of the bulk copies of the raw windows
   uint32_t rphase = 0u;
 
-  MemberCursor cur_c, cur_n, cur_f, cur_x;  // items being summed / next (prefetched) / two ahead / announced
+  MemberCursor cur_c, cur_n, cur_f;  // items being summed / next (prefetched and announced) / two ahead
   auto locate = [&](MemberCursor& c, int u, int& lu) -> BeamArgs {
     if constexpr (Src::kBatch) {
       c.seek(uoff, umem, nmem, u);
@@ -678,7 +678,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   auto announce = [&](int u) {  // thread 0: the bytes of item u's windows
     if (threadIdx.x == 0 && u < nitems) {
       int lu;
-      const BeamArgs a = locate(cur_x, u, lu);
+      const BeamArgs a = locate(cur_n, u, lu);
       mbar_expect_tx(&barr, (uint32_t)(a.m * RB));
     }
   };
@@ -843,7 +843,7 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
   const int jbase = part_i * (NW / SPLIT);
   uint32_t phase[2] = {0u, 0u};
 
-  MemberCursor cur_c, cur_i, cur_x;  // units being computed / being prefetched / announced
+  MemberCursor cur_c, cur_i;  // units being computed / being prefetched
   auto locate = [&](MemberCursor& c, int u, int& lu) -> BeamArgs {
     if constexpr (Src::kBatch) {
       c.seek(uoff, umem, nmem, u);
@@ -878,13 +878,15 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       }
     }
   };
-  // thread 0: announce the bytes of chunk ch of unit u into buffer buf (before the barrier that precedes the copies)
-  auto announce = [&](int u, int ch, int buf) {
+  // thread 0: announce the bytes of chunk ch of beam a into buffer buf (before the barrier that precedes the copies)
+  auto announce = [&](const BeamArgs& a, int ch, int buf) {
     if (threadIdx.x != 0) return;
-    int lu;
-    const BeamArgs a = locate(cur_x, u, lu);
     const int ns = min(a.SC, a.nsub - ch * a.SC);
     mbar_expect_tx(&bar2[buf], (uint32_t)ns * (uint32_t)a.SWW * 4u);
+  };
+  auto announce_unit = [&](int u, int buf) {  // the first chunk of unit u (the unit prefetched next)
+    int lu;
+    announce(locate(cur_i, u, lu), 0, buf);
   };
   auto issue_unit = [&](int u, int buf, const int32_t* Eu) {  // first chunk of unit u
     int lu;
@@ -910,7 +912,7 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
   fetch_e2(blockIdx.x, 0);
   cp_async_commit();
   cp_async_wait_all();
-  announce(blockIdx.x, 0, 0);
+  announce_unit(blockIdx.x, 0);
   __syncthreads();
   issue_unit(blockIdx.x, 0, E);
   for (int u = blockIdx.x, ju = 0; u < nunits; u += gridDim.x, ++ju) {
@@ -967,8 +969,8 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
         }
       }
       if (ch + 1 == nchunk) cp_async_wait_all();   // the next unit's delays, for its first chunk
-      if (ch + 1 < nchunk) announce(u, ch + 1, buf ^ 1);
-      else if (u + (int)gridDim.x < nunits) announce(u + gridDim.x, 0, buf ^ 1);
+      if (ch + 1 < nchunk) announce(a, ch + 1, buf ^ 1);
+      else if (u + (int)gridDim.x < nunits) announce_unit(u + gridDim.x, buf ^ 1);
       __syncthreads();
       // prefetch the next chunk: of this unit, else the first of the block's next unit
       if (ch + 1 < nchunk) {

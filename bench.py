@@ -182,7 +182,8 @@ KERNEL_SECTIONS = {
 
 def kernel_sha(kernel):
     """Hash of one kernel's source: its section of kernels.cuh (banner to next
-    banner) and the constants of tx_internal.h."""
+    banner, comments and blank space left out) and the constants of
+    tx_internal.h."""
     csrc = os.path.join(ROOT, "paper_2401_13834_gb300", "csrc")
     with open(os.path.join(csrc, "kernels.cuh")) as fh:
         lines = fh.read().split("\n")
@@ -190,7 +191,9 @@ def kernel_sha(kernel):
     i = next(k for k, ln in enumerate(lines) if ln.startswith(title))
     j = next((k for k in range(i + 2, len(lines)) if lines[k].startswith("// ----") and k + 1 < len(lines)
               and lines[k + 1].startswith("// ") and not lines[k + 1].startswith("// ----")), len(lines))
-    h = hashlib.sha256("\n".join(lines[i:j]).encode())
+    # code only: comments and blank space do not change what the counters measured
+    code = [re.sub(r"//.*$", "", ln).strip() for ln in lines[i:j]]
+    h = hashlib.sha256("\n".join(c for c in code if c).encode())
     with open(os.path.join(csrc, "tx_internal.h")) as fh:
         h.update("\n".join(ln for ln in fh.read().split("\n") if ln.startswith("constexpr")).encode())
     return h.hexdigest()[:16]

@@ -653,9 +653,9 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     for (int c = threadIdx.x; c < a.m; c += blockDim.x) cp_async4(wrow + w * TSL + c, d1kb + c);
     if (HALF && threadIdx.x == 0) cp_async4(hsub + w, a.hoff + it.s);
   };
-  // input windows of item u (descriptor in slot sl, delays in row w)
-  // bulk copies of the windows (RB bytes per channel, split at the ring's end); the byte count
-  // was announced on barr before the barrier that precedes this call
+  // input windows of item u (descriptor in slot sl, delays in row w): bulk copies of RB bytes per
+  // channel (split at the ring's end), issued by lane 0 of the warps; the byte count was announced
+  // on barr before the barrier that precedes this call
   auto issue = [&](int u, int sl, int w) {
     int lu;
     const BeamArgs a = locate(cur_n, u, lu);

@@ -147,3 +147,20 @@ def test_delay_table_equals_oracle(tx, mk):
     plan = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp)
     ref = CL.delay_ms(wl.dms, float(wl.freqs_mhz.min()), float(wl.freqs_mhz.max()))
     assert np.array_equal(plan.delay_table(), ref)
+
+
+@pytest.mark.parametrize("m", [1, 16, 64, 128, 257])
+def test_stage1_tile_fits_shared_memory_for_every_subband_width(tx, m):
+    """The automatic stage-1 tile is the largest whose staged words, raw
+    windows, offset tables, row bases, item descriptors and delay rows fit the
+    227 KB of shared memory (MeerKAT-L's 64 channels per sub-band keep the
+    largest tile; 257 channels, the most the 16-bit sums allow, still fit)."""
+    wl = synth.tiny_workload(nchan=m * 2, nsub=2, ndm=16)
+    p = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 2, wl.widths, wl.nsamp)
+    assert p.tile_q1 in (32, 64, 128, 256)
+    if m <= 64:
+        assert p.tile_q1 == 256
+    if p.tile_q1 < 256:   # the next larger tile would not have fitted
+        with pytest.raises(tx.TxError) as e:
+            tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 2, wl.widths, wl.nsamp, tile_q1=2 * p.tile_q1)
+        assert e.value.code == -8

@@ -470,6 +470,49 @@ def test_detection_probability_symmetry():
     assert float(LS.p_detect(5.0, 8.0)) > float(LS.p_detect(5.0, 5.0))
 
 
+def test_detection_probabilities_by_value():
+    """Eqs. 6-7 are the Gaussian tail and the Gaussian CDF of the excess S/N
+    over gamma: pinned to the textbook 95% quantile of the standard normal
+    (1.6448536269514722), to P(Z > 6) and P(Z > 3), and to the normal CDF
+    computed by integrating the density with quadrature (not through erfc)."""
+    z95 = 1.6448536269514722
+    for gamma in (0.0, 5.0, 7.0):
+        assert float(LS.p_detect(gamma, gamma + z95)) == pytest.approx(0.95, abs=1e-12)
+        assert float(LS.p_detect(gamma, gamma - z95)) == pytest.approx(0.05, abs=1e-12)
+    assert float(LS.p_false_alarm(z95)) == pytest.approx(0.05, abs=1e-12)
+    assert float(LS.p_false_alarm(6.0)) == pytest.approx(9.865876450376946e-10, rel=1e-9)
+    assert float(LS.p_false_alarm(3.0)) == pytest.approx(1.3498980316300946e-3, rel=1e-12)
+
+    def phi(x):  # standard normal CDF by quadrature of the density
+        v, _ = integrate.quad(lambda u: math.exp(-0.5 * u * u) / math.sqrt(2.0 * math.pi), -40.0, x,
+                              epsabs=1e-14, epsrel=1e-12, limit=200)
+        return v
+
+    for gamma, snr in ((7.0, 5.0), (7.0, 8.3), (5.0, 10.0), (6.0, 6.5)):
+        assert float(LS.p_detect(gamma, snr)) == pytest.approx(phi(snr - gamma), rel=1e-9, abs=1e-13)
+
+
+def test_scattered_pulse_against_numerical_convolution():
+    """Eq. 15 for tau > 0: the closed form (both of its branches) equals the
+    convolution of exp(-u^2/w^2) with the causal (1/tau) exp(-t/tau) done by
+    quadrature, point by point; its area is that of the Gaussian, w sqrt(pi)
+    (the kernel has unit area), whatever tau; and tau -> 0 gives the Gaussian."""
+    w = 1.3
+    for tau in (0.05, 0.4, 1.0, 3.0, 13.0):
+        t = np.array([-3.0, -1.0, -0.2, 0.0, 0.3, 1.0, 2.5, 6.0, 15.0, 40.0]) * w
+        got = LS.scattered_pulse(t, w, tau)
+        for ti, gi in zip(t, got):
+            ref, _ = integrate.quad(lambda u: math.exp(-(u / w) ** 2) * math.exp(-(ti - u) / tau) / tau,
+                                    -12.0 * w, ti, epsabs=1e-15, epsrel=1e-11, limit=400)
+            assert gi == pytest.approx(ref, rel=1e-8, abs=1e-14), (tau, ti, gi, ref)
+        # area over a grid wide enough for the tail
+        tt = np.linspace(-8.0 * w, 8.0 * w + 60.0 * tau, 400001)
+        area = integrate.trapezoid(LS.scattered_pulse(tt, w, tau), tt)
+        assert area == pytest.approx(w * math.sqrt(math.pi), rel=2e-6), tau
+    t = np.linspace(-3.0, 3.0, 61)
+    assert np.allclose(LS.scattered_pulse(t, 1.0, 1e-6), np.exp(-t * t), atol=2e-6)
+
+
 # ---------------------------------------------------------------------------
 # Half-precision storage of the stage-1 sums (the FP16 form)
 # ---------------------------------------------------------------------------

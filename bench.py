@@ -44,8 +44,7 @@ import synth  # noqa: E402
 
 METRIC = "DM-trial*samples/s (dedisp+boxcar)"
 UNIT = "DM-trial*samples/s"
-SMS = 152
-SM_MAX_MHZ_NOMINAL = 2070.0
+SM_MAX_MHZ_NOMINAL = 2070.0       # used only when MEASURED_PEAKS.json has no sm_max_mhz
 
 
 def parse_args():
@@ -83,6 +82,10 @@ def parse_args():
     ap.add_argument("--cluster-r", type=float, nargs="*", default=[4.0, 8.0],
                     help="clustering radii (ms) timed on the last block's candidates")
     ap.add_argument("--cluster-k", type=int, default=2)
+    ap.add_argument("--latency-blocks", type=int, default=200,
+                    help="blocks of the separate latency loop (p50/p99 per block)")
+    ap.add_argument("--cube-steps", type=int, default=10,
+                    help="blocks of the same workload in cube mode, for the block's HBM fraction there (0: skip)")
     return ap.parse_args()
 
 
@@ -245,16 +248,55 @@ def algorithmic_work(plan, ncand_avg):
             "boxcar": ("hbm", box)}
 
 
-def alu_peak(phase, sm_mhz):
-    """Derived on-chip peak in sample-adds/s.
+BYTES_PER_ADD = {"stage1": 1.0, "stage2": 2.0}
 
-    Both de-dispersion stages stream their shifted operands through shared
-    memory, whose port moves 128 B per clock per SM. Stage 1 reads one byte per
-    sample-add (uint8 samples, four per 32-bit word), stage 2 two bytes (uint16
-    sums, two per word): 128 and 64 sample-adds per clock per SM.
+
+def onchip_peaks(tx, peaks):
+    """The on-chip bound of both de-dispersion stages, measured and derived.
+
+    Both stages stream their shifted operands through shared memory: stage 1
+    reads one byte per sample-add (uint8 samples, four per 32-bit word), stage
+    2 two bytes (uint16 sums, two per word). Measured: the library's
+    shared-memory read probe (tx_measure_smem_bandwidth) on this GPU. Derived:
+    SMs (from the device) x 128 B per clock x the maximum SM clock
+    (MEASURED_PEAKS.json).
     """
-    per_clk = {"stage1": 128.0, "stage2": 64.0}[phase]
-    return SMS * per_clk * sm_mhz * 1e6
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz") or SM_MAX_MHZ_NOMINAL)
+    derived = nsm * 128.0 * mhz * 1e6
+    measured = tx.measure_smem_bandwidth(4096)
+    return {"smem_bytes_per_s_measured": measured, "smem_bytes_per_s_derived": derived, "sms": nsm,
+            "sm_max_mhz": mhz, "frac_of_derived": measured / derived}
+
+
+def alu_peak(phase, onchip):
+    """On-chip peak of a de-dispersion stage in sample-adds/s: the measured
+    shared-memory read bandwidth over the stage's bytes per sample-add."""
+    return onchip["smem_bytes_per_s_measured"] / BYTES_PER_ADD[phase]
+
+
+def block_hbm_bytes(plan, ncand_avg):
+    """Counted bytes of one block, by the definition the fraction of the HBM
+    roofline is quoted on: new input + the carried tail re-read + the stage-1
+    intermediates written and read at their storage width + the output. And,
+    separately, what this implementation also moves: the block written into
+    the ring, and the series written by stage 2 and read by the boxcar."""
+    t = plan.tables()
+    d2 = t["d2"]
+    G = plan.group
+    m = plan.nchan // plan.nsub
+    width = {"u16": 2, "f16": 2, "i32": 4}[plan.interm]
+    entries = 0
+    for k in range(plan.ncoarse):
+        blk = d2[k * G:min((k + 1) * G, plan.ndm)]
+        entries += int((plan.series_len + (blk.max(axis=0) - blk.min(axis=0))).sum())
+    out = {"cands": 8 + 16 * ncand_avg, "plane": plan.ndm * plan.nsamp * 5,
+           "cube": plan.ndm * plan.nwidth * plan.nsamp * 4, "series": plan.ndm * plan.series_len * 4}[plan.output]
+    counted = {"input": plan.block_bytes, "tail_reread": plan.nchan * plan.overlap,
+               "intermediates": 2 * entries * width, "output": out}
+    extra = {"ring_write": plan.block_bytes, "series_round_trip": 2 * plan.ndm * plan.series_len * 4}
+    return counted, extra
 
 
 # ----------------------------------------------------------------------------
@@ -487,6 +529,16 @@ def run_ours(args):
     ncand_last = int(ncand.item()) if ncand is not None else 0
     phase_ms, nsteps, step_ms = timer.read()
 
+    # ---- block latency: a separate loop of at least --latency-blocks blocks ----------
+    lat_timer = tx.Timer(max(args.latency_blocks, 1))
+    for i in range(max(args.latency_blocks, 1)):
+        tx.execute_timed(plan, beam, blocks[i % nb], out, ncand, ws, lat_timer)
+    _, lat_n, lat_ms = lat_timer.read()
+    latency = {"blocks": lat_n, "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+               "max_ms": float(lat_ms.max()), "block_duration_ms": T * wl.tsamp_s * 1e3,
+               "what": "CUDA events around each block's launches on the execute's stream, blocks back to back"}
+    del lat_timer
+
     elapsed_ms = max_over_ranks(elapsed_ms, dev)
     units = wl.ndm * T
     value = aggregate_throughput(units, args.steps, world, elapsed_ms / 1e3)
@@ -566,8 +618,32 @@ def run_ours(args):
                                "ms": ev[0].elapsed_time(ev[1]) / reps})
             del cl, res, ncl
 
+    # ---- the same workload in cube mode: the block's HBM fraction with the S/N cube written ----
+    cube = None
+    if args.cube_steps > 0 and args.output == "cands":
+        del out, ncand
+        torch.cuda.empty_cache()
+        pc = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, layout=args.layout,
+                     interm=args.interm, output="cube")
+        bc = tx.Beam(pc)
+        bc.prime(torch.from_numpy(tail_h).to(dev))
+        oc, _ = pc.alloc_out(dev)
+        wsc = ws if pc.workspace_bytes <= ws.numel() else pc.alloc_workspace(dev)
+        for i in range(2):
+            tx.execute(pc, bc, blocks[i % nb], out=oc, workspace=wsc)
+        ct = tx.Timer(args.cube_steps)
+        torch.cuda.synchronize()
+        for i in range(args.cube_steps):
+            tx.execute_timed(pc, bc, blocks[i % nb], oc, None, wsc, ct)
+        cph, cn, cms = ct.read()
+        cube = {"steps": cn, "ms_per_step": float(np.mean(cms)), "phase_ms": {k: v / cn for k, v in cph.items()},
+                "plan": pc}
+        del oc, bc, ct, wsc
+        torch.cuda.empty_cache()
+
     if rank == 0:
         peaks, peak_kind = measured_peaks()
+        onchip = onchip_peaks(tx, peaks)
         work = algorithmic_work(plan, ncand_last)
         phases = {}
         for name, ms in phase_ms.items():
@@ -579,7 +655,7 @@ def run_ours(args):
                 entry.update({"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": ach / peaks["hbm_gbs"], "algorithmic": amount})
             else:
-                pk = alu_peak(name, SM_MAX_MHZ_NOMINAL) / 1e12
+                pk = alu_peak(name, onchip) / 1e12
                 ach = amount / (avg / 1e3) / 1e12 if avg > 0 else 0.0
                 entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": amount})
             phases[name] = entry
@@ -590,8 +666,24 @@ def run_ours(args):
         roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": profiled_traffic(kernel_of[dom], wl.name), "kernel": kernel_of[dom],
                 "peak_source": (f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
-                                "derived: 152 SMs x shared-memory port 128 B/clk x 2.07 GHz, "
+                                "measured: shared-memory read bandwidth of this GPU (tx_measure_smem_bandwidth, "
+                                f"{onchip['smem_bytes_per_s_measured'] / 1e12:.2f} TB/s), "
                                 f"{'1' if dom == 'stage1' else '2'} B per sample-add")}
+
+        def block_fraction(p, ms, ncand_avg):
+            counted, extra = block_hbm_bytes(p, ncand_avg)
+            cb = sum(counted.values())
+            eb = cb + sum(extra.values())
+            return {"frac": cb / (ms / 1e3) / (peaks["hbm_gbs"] * 1e9), "counted_bytes": cb, "bytes": counted,
+                    "ms_per_block": ms, "peak_gbs": peaks["hbm_gbs"],
+                    "frac_all_traffic": eb / (ms / 1e3) / (peaks["hbm_gbs"] * 1e9), "also_moved": extra,
+                    "definition": "(new input + carried tail re-read + stage-1 intermediates written and read at "
+                                  "their storage width + output) / time per block / measured HBM copy bandwidth; "
+                                  "frac_all_traffic adds the ring write and the series round trip"}
+        hbm_block = {args.output: block_fraction(plan, elapsed_ms / args.steps, ncand_last)}
+        if cube is not None:
+            hbm_block["cube"] = block_fraction(cube.pop("plan"), cube["ms_per_step"], 0)
+            hbm_block["cube"]["phase_ms"] = cube["phase_ms"]
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(wl, X[:, :L + T], args.gamma, args.cpu_seconds)
@@ -615,10 +707,11 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32 sums, f32 S/N", "data": "synthetic",
             "config": dict(workload_config(wl, plan.group, L, args), parallelism=f"replicas{world}"),
-            "p50_block_ms": float(np.percentile(step_ms, 50)), "p99_block_ms": float(np.percentile(step_ms, 99)),
+            "p50_block_ms": latency["p50_ms"], "p99_block_ms": latency["p99_ms"], "latency": latency,
             "real_time_factor": (T * wl.tsamp_s) / (elapsed_ms / args.steps / 1e3),
             "candidates_per_block": ncand_last if plan.output == "cands" else None,
-            "roofline": roof, "phases": phases, "clocks": clocks, "e2e": e2e,
+            "roofline": roof, "hbm_frac_block": hbm_block[args.output]["frac"], "hbm_block": hbm_block,
+            "onchip_peak": onchip, "phases": phases, "clocks": clocks, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches,
             "clustering": clustering,
             "paper_context": "TransientX de-dispersion runs in real time on one i7-10750H core for 4096 channels x "
@@ -646,7 +739,7 @@ def init_dist():
     return world, rank, torch.device("cuda", torch.cuda.current_device())
 
 
-def phase_roofline(name, ms_per_step, work_units, peaks):
+def phase_roofline(name, ms_per_step, work_units, peaks, onchip):
     """Roofline entry of one phase: achieved vs peak for its bound."""
     bound = "alu" if name in ("stage1", "stage2") else "hbm"
     entry = {"ms_per_step": ms_per_step, "bound": bound}
@@ -657,7 +750,7 @@ def phase_roofline(name, ms_per_step, work_units, peaks):
         entry.update({"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                       "algorithmic": work_units})
     else:
-        pk = alu_peak(name, SM_MAX_MHZ_NOMINAL) / 1e12
+        pk = alu_peak(name, onchip) / 1e12
         ach = work_units / (ms_per_step / 1e3) / 1e12
         entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": work_units})
     return entry
@@ -837,6 +930,7 @@ def run_batched(args):
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
+        onchip = onchip_peaks(tx, peaks)
         work = {k: 0 for k in ("ingest", "stage1", "stage2", "stats", "boxcar")}
         for p, n in zip(plans, ncands):
             for k, (_, amount) in algorithmic_work(p, n).items():
@@ -844,7 +938,7 @@ def run_batched(args):
         total = max(sum(phase_ms.values()), 1e-12)
         phases = {}
         for name, ms in phase_ms.items():
-            e = phase_roofline(name, ms / max(pn, 1), work[name], peaks)
+            e = phase_roofline(name, ms / max(pn, 1), work[name], peaks, onchip)
             e["share"] = ms / total
             phases[name] = e
         dom = max(phase_ms, key=phase_ms.get)

@@ -66,6 +66,9 @@ extern "C" {
 #define TX_ERR_CAND_OVERFLOW  -6  /* more candidates than max_cands (results kept)    */
 #define TX_ERR_BUDGET         -7  /* an allocation would exceed a caller's budget     */
 #define TX_ERR_UNSUPPORTED    -8  /* valid but not supported by this build            */
+#define TX_ERR_ABORTED        -9  /* a kernel gave up a bounded wait: the beam's
+                                     results and state are not valid (see
+                                     tx_beam_failed)                                 */
 
 /* ---- enums ---- */
 enum tx_layout { TX_LAYOUT_FT = 0,   /* block is channel-major  uint8 [nchan][T]      */
@@ -222,17 +225,30 @@ int32_t tx_beam_import(const tx_plan* plan, tx_beam* beam, const void* h_src, in
 /* Blocks processed since create/reset/import. */
 int32_t tx_beam_blocks(const tx_beam* beam, int64_t* nblocks);
 
+/* Waits the beam's kernels gave up since create/reset/import (a bulk copy
+   into shared memory that had not completed after the polling limit; see
+   tx_set_wait_polls). A kernel that gives up returns early, so once this is
+   nonzero every result since the last check is not valid, and neither is the
+   beam's state (carried tail, running statistics): reset or import it before
+   going on. The host-synchronous calls (tx_execute_host, tx_pipeline_pop,
+   tx_batch_wait) check it and return TX_ERR_ABORTED. Waits for the device
+   (cudaDeviceSynchronize), then reads the count into *count. */
+int32_t tx_beam_failed(const tx_plan* plan, const tx_beam* beam, int64_t* count);
+
 void tx_beam_destroy(tx_beam* beam);
 
 /* Processes one block (Sec. 2.3 data flow, then Sec. 2.4 and 2.5):
      d_block     uint8, nchan * T bytes in the plan's layout
-     d_out       info.out_bytes bytes; format set by the plan's output mode
+     d_out       info.out_bytes bytes; format set by the plan's output mode;
+                 8-byte aligned for TX_OUT_SERIES, 4-byte aligned otherwise
      d_ncand     int64 [1], TX_OUT_CANDS only (else may be NULL): set to the number
                  of candidates found; records beyond max_cands are dropped, so a
                  value above max_cands means the buffer overflowed
-     d_workspace info.workspace_bytes bytes of device scratch (not kept);
-                 info.workspace_bytes_compact for a compact beam
-   All kernels go on `stream`; the call returns once they are enqueued. */
+     d_workspace info.workspace_bytes bytes of device scratch (not kept),
+                 16-byte aligned; info.workspace_bytes_compact for a compact beam
+   All kernels go on `stream`; the call returns once they are enqueued.
+   Errors: INVALID_ARG (null or misaligned buffer, beam of another plan or
+   device) before anything is enqueued, CUDA. */
 int32_t tx_execute(const tx_plan* plan, tx_beam* beam, const uint8_t* d_block, void* d_out,
                    int64_t* d_ncand, void* d_workspace, void* stream);
 
@@ -243,7 +259,8 @@ int32_t tx_execute(const tx_plan* plan, tx_beam* beam, const uint8_t* d_block, v
      other modes:  info.out_bytes bytes to h_out
    d_block_staging / d_out / d_ncand / d_workspace are device scratch as in
    tx_execute. Returns TX_ERR_CAND_OVERFLOW (results kept) if candidates were
-   dropped. */
+   dropped, TX_ERR_ABORTED if the beam's kernels have given up a wait (see
+   tx_beam_failed). */
 int32_t tx_execute_host(const tx_plan* plan, tx_beam* beam, const uint8_t* h_block,
                         void* h_out, int64_t* h_ncand, uint8_t* d_block_staging, void* d_out,
                         int64_t* d_ncand, void* d_workspace, void* stream);
@@ -278,7 +295,8 @@ int32_t tx_pipeline_push(tx_pipeline* pipeline, const uint8_t* h_block);
      other modes:  info.out_bytes bytes to h_out
    Returns TX_ERR_TIMEOUT when the limit ran out first (the block stays in
    flight: pop again), TX_ERR_INVALID_ARG when no block is in flight, and
-   TX_ERR_CAND_OVERFLOW (results kept, block popped) as tx_execute_host. */
+   TX_ERR_CAND_OVERFLOW (results kept, block popped) and TX_ERR_ABORTED (block
+   popped, results not valid) as tx_execute_host. */
 int32_t tx_pipeline_pop(tx_pipeline* pipeline, void* h_out, int64_t* h_ncand, int64_t timeout_us);
 
 /* Waits for the blocks in flight, then frees everything the pipeline owns. */
@@ -290,6 +308,24 @@ void tx_pipeline_destroy(tx_pipeline* pipeline);
    returned early and the results of that launch are not valid; 0 in normal
    operation. Synchronises with the device. */
 int32_t tx_wait_timeouts(int64_t* count);
+
+/* Sets the polling limit of the first wait for each bulk copy in kernels
+   launched from now on (process-wide; default and maximum 2^22 polls, which
+   is seconds). With 0 every such wait gives up at once, which drives the
+   failure path (tx_beam_failed, TX_ERR_ABORTED, tx_wait_timeouts) without
+   any fault: for tests only. Whatever the setting, a kernel that gives up
+   waits at the full limit for the copies it has in flight before it returns.
+   The previous limit goes to *previous (may be NULL). */
+int32_t tx_set_wait_polls(int64_t polls, int64_t* previous);
+
+/* Measures the shared-memory read bandwidth of the current device, the
+   on-chip bound of both de-dispersion stages (stage 1 reads one byte of
+   shared memory per sample-add, stage 2 two): one 1024-thread block per SM
+   streams conflict-free 32-bit loads (a warp reads one 128-byte row per
+   load) `iters` x 8 times each from a 32 KB buffer; the second of two
+   launches is timed with CUDA events on `stream`. Writes bytes per second
+   over all SMs to *h_bytes_per_s. Synchronises `stream`. */
+int32_t tx_measure_smem_bandwidth(int32_t iters, double* h_bytes_per_s, void* stream);
 
 /* ---- phase timing (CUDA events recorded on the execute's stream) ----
    Phases of one execute, in order:
@@ -389,14 +425,17 @@ int32_t tx_batch_get_info(const tx_batch* batch, tx_batch_info* info);
                   d_ncands[i] is beam i's int64 counter (NULL for other modes)
      d_workspace  tx_batch_info.workspace_bytes of device scratch
    Enqueued on `stream`; may block the host until the step two calls back
-   has finished (see above). */
+   has finished (see above). d_workspace must be 16-byte aligned; each
+   d_outs[i] is aligned as tx_execute's d_out. */
 int32_t tx_execute_batch(tx_batch* batch, const uint8_t* const* d_blocks, void* const* d_outs,
                          int64_t* const* d_ncands, void* d_workspace, void* stream);
 
 /* Waits, polling, until the batch's last enqueued step has finished on the
    GPU, at most timeout_us microseconds (< 0: no limit). Returns TX_OK, or
    TX_ERR_TIMEOUT when the limit ran out first (the step keeps running and
-   can be waited for again), or TX_ERR_CUDA if the step failed. */
+   can be waited for again), TX_ERR_ABORTED when the kernels of a member beam
+   have given up a wait (tx_last_error names it; see tx_beam_failed), or
+   TX_ERR_CUDA if the step failed. */
 int32_t tx_batch_wait(tx_batch* batch, int64_t timeout_us);
 
 /* TX_BATCH_PROFILE batches: waits for the last step, then writes the summed
@@ -468,6 +507,40 @@ void tx_clusterer_destroy(tx_clusterer* c);
 int32_t tx_plan_segments(int32_t nchan, const double* freq_mhz, double tsamp_s, int32_t ndm, const double* dm,
                          int32_t f_max, int32_t* h_factor);
 
+/* A downsampled plan: the DM grid of `desc` split into those segments, each
+   with its own plan (f_max first drops to the largest power of two dividing
+   T, so every factor divides the block):
+     segment j   DM trials [dm_lo, dm_hi) of desc's grid with factor f
+     its plan    desc with sampling time f t_samp, those DMs, blocks of T / f
+                 samples and widths W / f (at least 1, duplicates dropped, so
+                 the physical widths that are resolved are kept)
+   Its input is the block averaged over f samples (tx_downsample). The
+   segment plan's output t' covers native samples [f t', f (t' + 1)) of its
+   own window, which starts f L_j native samples before the block (L_j its
+   overlap); with the native overlap L = max_j f L_j, that is native window
+   time f t' + native_offset, native_offset = L - f L_j.
+   The segment plans belong to the downsampled plan: do not destroy them.
+   Errors: as tx_plan_create for any segment, and INVALID_ARG. */
+typedef struct tx_segment {
+  int32_t dm_lo, dm_hi;     /* DM trials [dm_lo, dm_hi) of the full grid                */
+  int32_t factor;           /* f                                                        */
+  int32_t nwidth;           /* widths of the segment plan, in downsampled samples       */
+  int32_t widths[32];
+  int64_t nsamp;            /* T / f                                                    */
+  int64_t overlap;          /* L_j, downsampled samples                                 */
+  int64_t native_offset;    /* L - f L_j, native samples                                */
+} tx_segment;
+
+typedef struct tx_dsplan tx_dsplan;
+
+int32_t tx_dsplan_create(const tx_plan_desc* desc, int32_t f_max, tx_dsplan** out);
+/* Number of segments and the native overlap L (either pointer may be NULL). */
+int32_t tx_dsplan_get_info(const tx_dsplan* ds, int32_t* nseg, int64_t* overlap);
+/* Segment j's description and plan (either pointer may be NULL). */
+int32_t tx_dsplan_segment(const tx_dsplan* ds, int32_t j, tx_segment* seg, const tx_plan** plan);
+/* Frees the downsampled plan and its segment plans. */
+void tx_dsplan_destroy(tx_dsplan* ds);
+
 /* Averages `factor` consecutive samples of every channel, rounding half up:
    out[t'] = (sum_{i<factor} in[factor t' + i] + factor / 2) / factor for
    t' < nsamp / factor, in the same layout (FT [nchan][n] or TF [n][nchan]).
@@ -487,7 +560,7 @@ int32_t tx_downsample(const uint8_t* d_in, int32_t layout, int32_t nchan, int64_
                then the T new ones (T + L <= ld); 16-byte aligned start, ld a
                multiple of 64 (samples past T + L are read but never affect
                the result)
-     d_series  int32 [ndm][T + W_max - 1], written
+     d_series  int32 [ndm][T + W_max - 1], written; 8-byte aligned
    The stage-1 sums, per-tile sums and copies of the plan's tables live in one
    32 MiB static device array that every GPU loading this library holds until
    the process exits; plans that need more return TX_ERR_BUDGET with the size
@@ -496,7 +569,11 @@ int32_t tx_downsample(const uint8_t* d_in, int32_t layout, int32_t nchan, int64_
    that first call outside any stream capture. Every call uses the same array
    and leaves its contents behind (nothing in it needs to start at zero):
    calls that overlap on the GPU, on any streams, race with each other. The
-   plan's tables are copied in from host memory on every call. */
+   plan's tables are copied in from host memory on every call. A kernel that
+   gives up a wait (see tx_set_wait_polls) is counted by tx_wait_timeouts
+   only; the series of that call are then not valid.
+   Errors: INVALID_ARG (null or misaligned pointer, bad ld), UNSUPPORTED,
+   BUDGET, before anything is enqueued; CUDA. */
 int32_t tx_dedisperse_noalloc(const tx_plan* plan, const uint8_t* d_x, int64_t ld, int32_t* d_series,
                               void* stream);
 

@@ -18,6 +18,7 @@ _EXPORTS = (
     "execute", "execute_timed", "execute_host", "geometric_widths", "lib", "library_path", "version",
     "cands_view", "plane_view", "cube_view", "series_view", "dedisperse_noalloc", "Batch", "Clusterer",
     "clusters_view", "CLUSTER_DTYPE", "segment_factors", "downsample", "Pipeline", "wait_timeouts",
+    "set_wait_polls", "measure_smem_bandwidth", "TX_ERR_ABORTED", "TX_ERR_TIMEOUT", "TX_ERR_INVALID_ARG",
 )
 __all__ = list(_EXPORTS)
 

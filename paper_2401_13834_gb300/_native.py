@@ -14,8 +14,10 @@ INTERMS = {"u16": 0, "i32": 1, "f16": 2}
 OUTPUTS = {"cands": 0, "plane": 1, "cube": 2, "series": 3}
 STATS = {"block": 0, "running": 1}
 
+TX_ERR_INVALID_ARG = -1
 TX_ERR_TIMEOUT = -5
 TX_ERR_CAND_OVERFLOW = -6
+TX_ERR_ABORTED = -9
 
 CAND_DTYPE = np.dtype([("dm_index", np.int32), ("t", np.int32), ("w_index", np.int32), ("snr", np.float32)])
 CLUSTER_DTYPE = np.dtype([("id", np.int32), ("dm_index", np.int32), ("t", np.int32), ("w_index", np.int32),
@@ -49,6 +51,13 @@ class _Info(C.Structure):
         ("export_bytes", C.c_int64), ("block_bytes", C.c_int64), ("ring_len", C.c_int64),
         ("ring_head0", C.c_int64), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32),
         ("workspace_bytes_compact", C.c_int64), ("compact_beam_state_bytes", C.c_int64),
+    ]
+
+
+class _Segment(C.Structure):
+    _fields_ = [
+        ("dm_lo", C.c_int32), ("dm_hi", C.c_int32), ("factor", C.c_int32), ("nwidth", C.c_int32),
+        ("widths", C.c_int32 * 32), ("nsamp", C.c_int64), ("overlap", C.c_int64), ("native_offset", C.c_int64),
     ]
 
 
@@ -116,6 +125,13 @@ def _load():
         "tx_pipeline_pop": (I32, [P, VP, VP, I64]),
         "tx_pipeline_destroy": (None, [P]),
         "tx_wait_timeouts": (I32, [C.POINTER(I64)]),
+        "tx_set_wait_polls": (I32, [I64, C.POINTER(I64)]),
+        "tx_measure_smem_bandwidth": (I32, [I32, C.POINTER(C.c_double), VP]),
+        "tx_dsplan_create": (I32, [C.POINTER(_Desc), I32, C.POINTER(P)]),
+        "tx_dsplan_get_info": (I32, [P, C.POINTER(I32), C.POINTER(I64)]),
+        "tx_dsplan_segment": (I32, [P, I32, C.POINTER(_Segment), C.POINTER(P)]),
+        "tx_dsplan_destroy": (None, [P]),
+        "tx_beam_failed": (I32, [P, P, C.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -159,50 +175,78 @@ def geometric_widths(ratio: float, wmax: int) -> np.ndarray:
     return out
 
 
+def _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output, snr_threshold,
+               max_cands, stats, stats_lambda, tile_q1, tile_split2):
+    """A tx_plan_desc over arrays kept alive in `keep` (a dict)."""
+    keep["freqs"] = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
+    keep["dms"] = np.ascontiguousarray(dms, dtype=np.float64)
+    keep["widths"] = np.ascontiguousarray(widths, dtype=np.int32)
+    d = _Desc()
+    d.nchan = keep["freqs"].size
+    d.freq_mhz = keep["freqs"].ctypes.data_as(C.POINTER(C.c_double))
+    d.tsamp_s = float(tsamp_s)
+    d.ndm = keep["dms"].size
+    d.dm = keep["dms"].ctypes.data_as(C.POINTER(C.c_double))
+    d.nsub = int(nsub)
+    d.group = int(group)
+    d.nwidth = keep["widths"].size
+    d.widths = keep["widths"].ctypes.data_as(C.POINTER(C.c_int32))
+    d.nsamp = int(nsamp)
+    d.layout = LAYOUTS[layout]
+    d.interm = INTERMS[interm]
+    d.output = OUTPUTS[output]
+    d.snr_threshold = float(snr_threshold)
+    d.max_cands = int(max_cands)
+    d.stats = STATS[stats]
+    d.stats_lambda = float(stats_lambda)
+    d.tile_q1 = int(tile_q1)
+    d.tile_split2 = int(tile_split2)
+    return d
+
+
 class Plan:
     """A de-dispersion + matched-filter plan (tables on the host until first use)."""
 
-    def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group=0, layout="ft", interm="u16",
-                 output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25,
-                 tile_q1=0, tile_split2=0):
+    @classmethod
+    def _wrap(cls, handle, owner, freqs_mhz, dms, widths, layout, interm, output, stats, snr_threshold, max_cands):
+        """A Plan over a handle that `owner` holds (and frees): a segment of a downsampled plan."""
+        self = cls.__new__(cls)
+        self._owner = owner
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
         self.dms = np.ascontiguousarray(dms, dtype=np.float64)
         self.widths = np.ascontiguousarray(widths, dtype=np.int32)
-        d = _Desc()
-        d.nchan = self.freqs.size
-        d.freq_mhz = self.freqs.ctypes.data_as(C.POINTER(C.c_double))
-        d.tsamp_s = float(tsamp_s)
-        d.ndm = self.dms.size
-        d.dm = self.dms.ctypes.data_as(C.POINTER(C.c_double))
-        d.nsub = int(nsub)
-        d.group = int(group)
-        d.nwidth = self.widths.size
-        d.widths = self.widths.ctypes.data_as(C.POINTER(C.c_int32))
-        d.nsamp = int(nsamp)
-        d.layout = LAYOUTS[layout]
-        d.interm = INTERMS[interm]
-        d.output = OUTPUTS[output]
-        d.snr_threshold = float(snr_threshold)
-        d.max_cands = int(max_cands)
-        d.stats = STATS[stats]
-        d.stats_lambda = float(stats_lambda)
-        d.tile_q1 = int(tile_q1)
-        d.tile_split2 = int(tile_split2)
         self.layout, self.interm, self.output, self.stats = layout, interm, output, stats
-        self.snr_threshold = float(snr_threshold)
-        self.max_cands = int(max_cands)
-        h = C.c_void_p()
-        _check(lib.tx_plan_create(C.byref(d), C.byref(h)))
-        self._h = h
+        self.snr_threshold, self.max_cands = float(snr_threshold), int(max_cands)
+        self._h = None
+        self._borrowed = handle
+        self._read_info(handle)
+        return self
+
+    def _read_info(self, h):
         inf = _Info()
         _check(lib.tx_plan_get_info(h, C.byref(inf)))
         self.info = {k: int(getattr(inf, k)) for k, _ in _Info._fields_ if k != "reserved0"}
         for k, v in self.info.items():
             setattr(self, k, v)
 
+    def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group=0, layout="ft", interm="u16",
+                 output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25,
+                 tile_q1=0, tile_split2=0):
+        keep = {}
+        d = _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output,
+                       snr_threshold, max_cands, stats, stats_lambda, tile_q1, tile_split2)
+        self.freqs, self.dms, self.widths = keep["freqs"], keep["dms"], keep["widths"]
+        self.layout, self.interm, self.output, self.stats = layout, interm, output, stats
+        self.snr_threshold = float(snr_threshold)
+        self.max_cands = int(max_cands)
+        h = C.c_void_p()
+        _check(lib.tx_plan_create(C.byref(d), C.byref(h)))
+        self._h = h
+        self._read_info(h)
+
     @property
     def handle(self):
-        return self._h
+        return self._h if self._h is not None else getattr(self, "_borrowed", None)
 
     def tables(self):
         nk, nc, nd, ns = self.ncoarse, self.nchan, self.ndm, self.nsub
@@ -210,20 +254,20 @@ class Plan:
         d2 = np.zeros((nd, ns), dtype=np.int32)
         kof = np.zeros(nd, dtype=np.int32)
         cdm = np.zeros(nk, dtype=np.float64)
-        _check(lib.tx_plan_tables(self._h, d1.ctypes.data_as(C.c_void_p), d2.ctypes.data_as(C.c_void_p),
+        _check(lib.tx_plan_tables(self.handle, d1.ctypes.data_as(C.c_void_p), d2.ctypes.data_as(C.c_void_p),
                                   kof.ctypes.data_as(C.c_void_p), cdm.ctypes.data_as(C.c_void_p)))
         return {"d1": d1, "d2": d2, "coarse_of_fine": kof, "coarse_dm": cdm}
 
     def delay_table(self):
         """Delay of each DM trial across the band, ms (the clustering axis)."""
         out = np.zeros(self.ndm, dtype=np.float64)
-        _check(lib.tx_plan_delay_table(self._h, out.ctypes.data_as(C.c_void_p)))
+        _check(lib.tx_plan_delay_table(self.handle, out.ctypes.data_as(C.c_void_p)))
         return out
 
     def stage1_layout(self):
         off, pitch = C.c_int64(), C.c_int64()
         base = np.zeros((self.ncoarse, self.nsub), dtype=np.int32)
-        _check(lib.tx_plan_stage1_layout(self._h, C.byref(off), C.byref(pitch), base.ctypes.data_as(C.c_void_p)))
+        _check(lib.tx_plan_stage1_layout(self.handle, C.byref(off), C.byref(pitch), base.ctypes.data_as(C.c_void_p)))
         return int(off.value), int(pitch.value), base
 
     def alloc_workspace(self, device=None, compact=False):
@@ -287,6 +331,13 @@ class Beam:
     def nblocks(self) -> int:
         n = C.c_int64()
         _check(lib.tx_beam_blocks(self._h, C.byref(n)))
+        return int(n.value)
+
+    def failed(self) -> int:
+        """Waits this beam's kernels gave up since create/reset/import (tx_beam_failed;
+        synchronises the device). Nonzero: its results and state are not valid."""
+        n = C.c_int64()
+        _check(lib.tx_beam_failed(self.plan.handle, self._h, C.byref(n)))
         return int(n.value)
 
     def __del__(self):
@@ -371,6 +422,21 @@ def wait_timeouts() -> int:
     return int(n.value)
 
 
+def measure_smem_bandwidth(iters: int = 4096, stream=None) -> float:
+    """Shared-memory read bandwidth of the current device, bytes/s (tx_measure_smem_bandwidth)."""
+    v = C.c_double()
+    _check(lib.tx_measure_smem_bandwidth(int(iters), C.byref(v), _stream_ptr(stream)))
+    return float(v.value)
+
+
+def set_wait_polls(polls: int) -> int:
+    """Polling limit of the kernels' first wait for each bulk copy (tx_set_wait_polls);
+    returns the previous one. 0 makes every such wait give up at once (tests only)."""
+    old = C.c_int64()
+    _check(lib.tx_set_wait_polls(int(polls), C.byref(old)))
+    return int(old.value)
+
+
 class Pipeline:
     """A stream of one beam's host blocks with up to ``depth`` in flight
     (tx_pipeline_*): ``push`` enqueues a block's copy and kernels, ``pop``
@@ -410,6 +476,8 @@ class Pipeline:
         rc = lib.tx_pipeline_pop(self._h, C.c_void_p(self.h_out.data_ptr()), self._hn.ctypes.data_as(C.c_void_p), us)
         if rc == TX_ERR_TIMEOUT:
             return None
+        if rc == TX_ERR_ABORTED:
+            self._inflight.pop(0)          # popped; its results are not valid
         if rc not in (0, TX_ERR_CAND_OVERFLOW):
             _check(rc)
         self._inflight.pop(0)
@@ -461,10 +529,27 @@ def series_view(plan: Plan, out):
 def dedisperse_noalloc(plan: Plan, x, ld: int, series, stream=None):
     """De-dispersed series of one window through the allocation-free entry point.
 
-    x: uint8 CUDA tensor holding [nchan][ld] (tail then block); series: int32
-    CUDA tensor of ndm * (T + W_max - 1) elements. Nothing is allocated.
+    x: contiguous uint8 CUDA tensor holding [nchan][ld] (tail then block);
+    series: contiguous int32 CUDA tensor of ndm * (T + W_max - 1) elements.
+    Nothing is allocated. The tensors are checked here (device, dtype,
+    contiguity, size) because the library sees only their addresses.
     """
-    _check(lib.tx_dedisperse_noalloc(plan.handle, _ptr(x), int(ld), _ptr(series), _stream_ptr(stream)))
+    import torch
+    ld = int(ld)
+    args = (("x", x, torch.uint8, plan.nchan * ld), ("series", series, torch.int32, plan.ndm * plan.series_len))
+    for name, t, dt, n in args:
+        if not isinstance(t, torch.Tensor):
+            raise TxError(TX_ERR_INVALID_ARG, f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise TxError(TX_ERR_INVALID_ARG, f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise TxError(TX_ERR_INVALID_ARG, f"{name} must be contiguous")
+        if t.numel() < n:
+            raise TxError(TX_ERR_INVALID_ARG, f"{name} holds {t.numel()} elements, needs {n}")
+    for name, t, _, _ in args:
+        if not t.is_cuda:
+            raise TxError(TX_ERR_INVALID_ARG, f"{name} must be a CUDA tensor")
+    _check(lib.tx_dedisperse_noalloc(plan.handle, _ptr(x), ld, _ptr(series), _stream_ptr(stream)))
 
 
 class Batch:
@@ -568,6 +653,39 @@ def clusters_view(out, nclusters):
     """Host structured array of the cluster records."""
     n = int(nclusters.item())
     return out[:n].contiguous().cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)
+
+
+class DsPlan:
+    """tx_dsplan: a DM grid split into downsampled segments, each with its own plan."""
+
+    def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, f_max=64, group=0, layout="ft", interm="u16",
+                 output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25,
+                 tile_q1=0, tile_split2=0):
+        keep = {}
+        d = _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output,
+                       snr_threshold, max_cands, stats, stats_lambda, tile_q1, tile_split2)
+        h = C.c_void_p()
+        _check(lib.tx_dsplan_create(C.byref(d), int(f_max), C.byref(h)))
+        self._h = h
+        n, L = C.c_int32(), C.c_int64()
+        _check(lib.tx_dsplan_get_info(h, C.byref(n), C.byref(L)))
+        self.overlap = int(L.value)
+        self.segments = []
+        for j in range(n.value):
+            sg, ph = _Segment(), C.c_void_p()
+            _check(lib.tx_dsplan_segment(h, j, C.byref(sg), C.byref(ph)))
+            w = np.array(sg.widths[:sg.nwidth], dtype=np.int32)
+            plan = Plan._wrap(ph, self, keep["freqs"], keep["dms"][sg.dm_lo:sg.dm_hi], w, layout, interm, output,
+                              stats, snr_threshold, max_cands)
+            self.segments.append(dict(dm_lo=sg.dm_lo, dm_hi=sg.dm_hi, factor=sg.factor, widths=w,
+                                      nsamp=sg.nsamp, overlap=sg.overlap, native_offset=sg.native_offset,
+                                      plan=plan))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and lib is not None:
+            lib.tx_dsplan_destroy(h)
+            self._h = None
 
 
 def segment_factors(freqs_mhz, tsamp_s, dms, f_max: int = 64) -> np.ndarray:

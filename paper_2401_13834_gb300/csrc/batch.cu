@@ -620,7 +620,20 @@ int32_t tx_batch_wait(tx_batch* B, int64_t timeout_us) {
   const auto t0 = std::chrono::steady_clock::now();
   while (true) {
     const cudaError_t e = cudaEventQuery(ev);
-    if (e == cudaSuccess) return TX_OK;
+    if (e == cudaSuccess) {
+      // the members' counts of waits their kernels gave up
+      // (copied on the batch's private non-blocking stream: nothing else waits)
+      for (int i = 0; i < B->n; ++i) {
+        int32_t v = 0;
+        TX_CUDA(cudaMemcpyAsync(&v, B->beams[i]->fail, sizeof(v), cudaMemcpyDeviceToHost, B->cap));
+        TX_CUDA(cudaStreamSynchronize(B->cap));
+        if (v) {
+          set_error("the kernels of beam %d gave up %d waits: its results are not valid (reset the beam)", i, v);
+          return TX_ERR_ABORTED;
+        }
+      }
+      return TX_OK;
+    }
     if (e != cudaErrorNotReady) {
       set_error("waiting for the batch failed: %s", cudaGetErrorString(e));
       return TX_ERR_CUDA;

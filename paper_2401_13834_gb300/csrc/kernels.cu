@@ -238,7 +238,9 @@ int beam_create(const tx_plan* p, tx_beam** out, int compact) {
   cudaGetDevice(&b->device);
   cudaError_t e = compact ? cudaMalloc((void**)&b->tail, std::max<size_t>((size_t)p->nchan * p->tail_pitch, 16))
                           : cudaMalloc((void**)&b->ring, (size_t)p->nchan * p->R);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->run, (size_t)p->ndm * 2 * sizeof(double));
+  // the running statistics, then the beam's count of waits its kernels gave up
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->run, (size_t)p->ndm * 2 * sizeof(double) + 16);
+  if (e == cudaSuccess) b->fail = reinterpret_cast<int32_t*>(b->run + (size_t)p->ndm * 2);
   if (e != cudaSuccess) {
     set_error("beam allocation failed: %s", cudaGetErrorString(e));
     tx_beam_destroy(b);
@@ -270,7 +272,7 @@ int32_t tx_beam_reset(const tx_plan* p, tx_beam* b, void* stream) {
     TX_CUDA(cudaMemsetAsync(b->tail, 0, (size_t)p->nchan * p->tail_pitch, st));
   else
     TX_CUDA(cudaMemsetAsync(b->ring, 0, (size_t)p->nchan * p->R, st));
-  TX_CUDA(cudaMemsetAsync(b->run, 0, (size_t)p->ndm * 2 * sizeof(double), st));
+  TX_CUDA(cudaMemsetAsync(b->run, 0, (size_t)p->ndm * 2 * sizeof(double) + 16, st));
   k_fill_run<<<(p->ndm + 255) / 256, 256, 0, st>>>(b->run, p->ndm);
   TX_CUDA(cudaGetLastError());
   b->head = p->head0;
@@ -332,7 +334,19 @@ int32_t tx_beam_import(const tx_plan* p, tx_beam* b, const void* h_src, int64_t 
   TX_CUDA(cudaDeviceSynchronize());
   if ((rc = copy_tail(p, b, const_cast<uint8_t*>(h + 64), false))) return rc;
   TX_CUDA(cudaMemcpy(b->run, h + 64 + (size_t)p->nchan * p->L, (size_t)p->ndm * 16, cudaMemcpyHostToDevice));
+  TX_CUDA(cudaMemset(b->fail, 0, sizeof(int32_t)));   // an imported state is a valid one
   b->nblocks = hdr[3];
+  return TX_OK;
+}
+
+int32_t tx_beam_failed(const tx_plan* p, const tx_beam* b, int64_t* count) {
+  int rc = check_beam(p, b);
+  if (rc) return rc;
+  if (!count) { set_error("null argument"); return TX_ERR_INVALID_ARG; }
+  TX_CUDA(cudaDeviceSynchronize());
+  int32_t v = 0;
+  TX_CUDA(cudaMemcpy(&v, b->fail, sizeof(v), cudaMemcpyDeviceToHost));
+  *count = v;
   return TX_OK;
 }
 
@@ -369,6 +383,12 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   if (rc) return rc;
   if (!d_block || !d_out || !d_workspace) { set_error("null device buffer"); return TX_ERR_INVALID_ARG; }
   if (p->output == TX_OUT_CANDS && !d_ncand) { set_error("candidate mode needs d_ncand"); return TX_ERR_INVALID_ARG; }
+  if (((uintptr_t)d_workspace & 15) != 0) { set_error("d_workspace must be 16-byte aligned"); return TX_ERR_INVALID_ARG; }
+  // the series are stored two outputs at a time (8-byte stores), the other outputs as 4-byte words
+  if (((uintptr_t)d_out & (p->output == TX_OUT_SERIES ? 7 : 3)) != 0) {
+    set_error("d_out must be %d-byte aligned", p->output == TX_OUT_SERIES ? 8 : 4);
+    return TX_ERR_INVALID_ARG;
+  }
   if ((rc = tx_upload_plan(p))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   TX_MARK(0);
@@ -549,17 +569,21 @@ int32_t tx_execute_host(const tx_plan* p, tx_beam* b, const uint8_t* h_block, vo
   TX_CUDA(cudaMemcpyAsync(d_block_staging, h_block, (size_t)p->nchan * p->T, cudaMemcpyHostToDevice, st));
   int rc = tx_execute(p, b, d_block_staging, d_out, d_ncand, d_workspace, stream);
   if (rc) return rc;
+  int32_t failed = 0;
+  TX_CUDA(cudaMemcpyAsync(&failed, b->fail, sizeof(failed), cudaMemcpyDeviceToHost, st));
   if (p->output == TX_OUT_CANDS) {
     TX_CUDA(cudaMemcpyAsync(h_ncand, d_ncand, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TX_CUDA(cudaStreamSynchronize(st));
     const int64_t n = std::min<int64_t>(*h_ncand, p->max_cands);
     if (n > 0) TX_CUDA(cudaMemcpyAsync(h_out, d_out, (size_t)n * sizeof(tx_cand), cudaMemcpyDeviceToHost, st));
     TX_CUDA(cudaStreamSynchronize(st));
+    if (failed) { set_error("the beam's kernels gave up %d waits: results not valid (reset the beam)", failed); return TX_ERR_ABORTED; }
     if (*h_ncand > p->max_cands) { set_error("%lld candidates, capacity %lld", (long long)*h_ncand, (long long)p->max_cands); return TX_ERR_CAND_OVERFLOW; }
     return TX_OK;
   }
   TX_CUDA(cudaMemcpyAsync(h_out, d_out, (size_t)p->out_bytes, cudaMemcpyDeviceToHost, st));
   TX_CUDA(cudaStreamSynchronize(st));
+  if (failed) { set_error("the beam's kernels gave up %d waits: results not valid (reset the beam)", failed); return TX_ERR_ABORTED; }
   return TX_OK;
 }
 
@@ -575,6 +599,73 @@ int32_t tx_wait_timeouts(int64_t* count) {
   const int rc = batch_wait_timeouts(&nb);
   if (rc) return rc;
   *count = v + nb;
+  return TX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shared-memory read bandwidth: every thread of a 1024-thread block reads
+// 32-bit words of a 32 KB buffer, a warp 32 consecutive words (one 128-byte
+// wavefront) per load, eight independent loads in flight per thread, for
+// `iters` rounds, each round one row further on; the loads are volatile and
+// their words are folded into a value that may be written out, so that none
+// is dropped or merged. One block per SM.
+constexpr int kProbeWords = 8192;   // 32 KB
+__device__ uint32_t g_probe_sink[1024];
+
+__global__ void __launch_bounds__(1024, 1) k_smem_probe(int iters) {
+  __shared__ uint32_t buf[kProbeWords];
+  for (int i = threadIdx.x; i < kProbeWords; i += blockDim.x) buf[i] = (uint32_t)i * 2654435761u;
+  __syncthreads();
+  const uint32_t base = smem_addr(buf);
+  uint32_t acc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  uint32_t off = (uint32_t)threadIdx.x;                  // word index of this thread's first load
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t v;
+      const uint32_t w = (off + (uint32_t)k * 1024u) & (kProbeWords - 1);
+      // volatile: every load is issued, none is merged with an earlier one
+      asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(base + 4u * w));
+      acc[k] ^= v;
+    }
+    off = (off + 32u) & (kProbeWords - 1);               // the next 32-word row of each warp
+  }
+  uint32_t r = 0u;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r += acc[k];
+  if (r == 0x9e3779b9u) g_probe_sink[blockIdx.x & 1023] = r;   // rarely taken; keeps the loads live
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t tx_measure_smem_bandwidth(int32_t iters, double* h_bytes_per_s, void* stream) {
+  if (!h_bytes_per_s || iters < 1 || iters > (1 << 20)) { set_error("need 1 <= iters <= 2^20 and an output"); return TX_ERR_INVALID_ARG; }
+  int dev = 0, nsm = 0;
+  TX_CUDA(cudaGetDevice(&dev));
+  TX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TX_CUDA(cudaEventCreate(&e0));
+  TX_CUDA(cudaEventCreate(&e1));
+  float ms = 0.f;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) k_smem_probe<<<nsm, 1024, 0, st>>>(iters);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) { set_error("shared-memory probe failed: %s", cudaGetErrorString(e)); return TX_ERR_CUDA; }
+  *h_bytes_per_s = (double)nsm * 1024.0 * 8.0 * 4.0 * (double)iters / ((double)ms * 1e-3);
   return TX_OK;
 }
 
@@ -658,6 +749,10 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
               (long long)(p->L + p->T));
     return TX_ERR_INVALID_ARG;
   }
+  if (((uintptr_t)d_series & 7) != 0) {  // the series are stored two outputs at a time
+    set_error("d_series must be 8-byte aligned");
+    return TX_ERR_INVALID_ARG;
+  }
   // scratch layout: stage-1 work items, d1, abase, e2, stage-1 sums, per-tile sums
   const size_t b_items = align256(p->items1.size() * sizeof(Stage1Item));
   const size_t b_d1 = align256(p->d1.size() * 4);
@@ -717,6 +812,7 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   a.SC = p->nsub_chunk2;
   a.SWW = p->sww2;
   a.ntile2 = p->ntile2;
+  a.polls = first_wait_polls();   // a wait that gives up counts in tx_wait_timeouts only
 
   // stage 1
   const int nitems = (int)p->items1.size();

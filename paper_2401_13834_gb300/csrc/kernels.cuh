@@ -50,7 +50,8 @@ struct BeamArgs {
   int32_t* D;                    // series [ndm][Dp]
   longlong2* part;               // per-tile (sum D, sum D^2) [ndm][ntile2]
   SnrConst* cst;                 // per (DM, width) S/N constants [ndm][nw]
-  double* run;                   // running (mu, var) [ndm][2]
+  double* run;                   // running (mu, var) [ndm][2], then the beam's count of waits its kernels
+                                 // gave up (int32; no count when run is null)
   const int32_t* d1;             // [nk][nchan]
   const int32_t* abase;          // [nk][nsub]
   const int32_t* e2;             // [ndm][nsub]
@@ -68,6 +69,7 @@ struct BeamArgs {
   double lam, gamma;
   int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
   int32_t layout, ingest_vec, running, output, compact, tail_pad, half, box_vec, tab1_phase;
+  uint32_t polls;                // polling limit of the first wait for each bulk copy
 };
 
 // Where a kernel finds a beam's arguments (the Src template parameter).
@@ -172,12 +174,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   }
   return false;
 }
-constexpr uint32_t kMbarPolls = 1u << 22;   // each poll may suspend the thread for a while: seconds in all
+constexpr uint32_t kMbarPolls = kWaitPolls;   // the full limit
 
 // Waits that gave up (a copy that never completed) in this translation
 // unit's kernels; a kernel that saw one returns early and its results are not
 // valid. Read by tx_wait_timeouts.
 __device__ int g_tx_wait_timeouts = 0;
+// Records a wait that gave up: in the counter above and in the beam's own
+// count, which marks the beam's state (tail, running statistics) and every
+// later result as not valid until the beam is reset or imported.
+template <typename A>
+__device__ __forceinline__ void record_give_up(const A& a) {
+  atomicAdd(&g_tx_wait_timeouts, 1);
+  if (a.run) atomicAdd(reinterpret_cast<int32_t*>(a.run + 2 * (size_t)a.ndm), 1);
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
@@ -707,12 +717,12 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const BeamArgs a = locate(cur_c, u, lu);
     cp_async_wait_all();
     const uint32_t ph = rphase;
-    const bool landed = mbar_wait(&barr, ph, kMbarPolls);
+    const bool landed = mbar_wait(&barr, ph, a.polls);
     rphase ^= 1u;
     if (__syncthreads_or(!landed)) {
-      // a copy never completed: record it, give the copies in flight a last bounded wait, give up
+      // a copy never completed: record it, give the copies in flight a last wait at the full limit, give up
       if (threadIdx.x == 0) {
-        atomicAdd(&g_tx_wait_timeouts, 1);
+        record_give_up(a);
         mbar_wait(&barr, ph, kMbarPolls);
       }
       return;
@@ -931,12 +941,12 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
       uint32_t* cur = Se + (size_t)buf * slot;
       cp_async_wait_all();
       const uint32_t ph = phase[buf];
-      const bool landed = mbar_wait(&bar2[buf], ph, kMbarPolls);
+      const bool landed = mbar_wait(&bar2[buf], ph, a.polls);
       phase[buf] ^= 1u;
       if (__syncthreads_or(!landed)) {
-        // a copy never completed: record it, give the copies in flight a last bounded wait, give up
+        // a copy never completed: record it, give the copies in flight a last wait at the full limit, give up
         if (threadIdx.x == 0) {
-          atomicAdd(&g_tx_wait_timeouts, 1);
+          record_give_up(a);
           mbar_wait(&bar2[buf], ph, kMbarPolls);
         }
         return;
@@ -1290,13 +1300,13 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       }
     }
     const uint32_t ph = bph[buf];
-    const bool landed = mbar_wait(&barb[buf], ph, kMbarPolls);
+    const bool landed = mbar_wait(&barb[buf], ph, a.polls);
     bph[buf] ^= 1u;
     // this unit's series landed; the previous unit is done with sW/sC and the other buffer
     if (__syncthreads_or(!landed)) {
-      // a copy never completed: record it, give the copy in flight a last bounded wait, give up
+      // a copy never completed: record it, give the copy in flight a last wait at the full limit, give up
       if (threadIdx.x == 0) {
-        atomicAdd(&g_tx_wait_timeouts, 1);
+        record_give_up(a);
         mbar_wait(&barb[buf], ph, kMbarPolls);
       }
       return;
@@ -1658,6 +1668,7 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.ingest_vec = p->layout == TX_LAYOUT_TF ? (al && p->nchan % 16 == 0) : (al && p->T % 16 == 0);
   a.running = p->stats == TX_STATS_RUNNING;
   a.output = p->output;
+  a.polls = first_wait_polls();
   return a;
 }
 

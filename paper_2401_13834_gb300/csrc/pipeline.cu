@@ -33,7 +33,7 @@ struct Slot {
   uint8_t* d_block = nullptr;     // staging for the block's input
   void* d_out = nullptr;          // the block's output
   int64_t* d_ncand = nullptr;     // candidate counter (TX_OUT_CANDS)
-  int64_t* h_ncand = nullptr;     // pinned copy of the counter
+  int64_t* h_ncand = nullptr;     // pinned copies of the counter and of the beam's give-up count
   cudaEvent_t in = nullptr;       // input on the device
   cudaEvent_t done = nullptr;     // kernels finished
   cudaEvent_t count = nullptr;    // counter copied to the host
@@ -125,7 +125,7 @@ int32_t tx_pipeline_create(const tx_plan* p, tx_beam* b, int32_t depth, void* st
     if ((rc = cuda(cudaMalloc((void**)&s.d_block, (size_t)p->nchan * p->T), "staging buffer"))) return fail(rc);
     if ((rc = cuda(cudaMalloc(&s.d_out, (size_t)std::max<int64_t>(p->out_bytes, 16)), "output buffer"))) return fail(rc);
     if ((rc = cuda(cudaMalloc((void**)&s.d_ncand, sizeof(int64_t)), "counter"))) return fail(rc);
-    if ((rc = cuda(cudaHostAlloc((void**)&s.h_ncand, sizeof(int64_t), cudaHostAllocDefault), "pinned counter")))
+    if ((rc = cuda(cudaHostAlloc((void**)&s.h_ncand, 2 * sizeof(int64_t), cudaHostAllocDefault), "pinned counter")))
       return fail(rc);
     for (cudaEvent_t* e : {&s.in, &s.done, &s.count, &s.out})
       if ((rc = cuda(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event"))) return fail(rc);
@@ -166,6 +166,14 @@ int32_t tx_pipeline_pop(tx_pipeline* pl, void* h_out, int64_t* h_ncand, int64_t 
   // input copy behind it (the two directions may share a queue).
   int rc;
   if ((rc = wait_event(s.done, t0, timeout_us, "the block's kernels"))) return rc;
+  // the beam's count of waits its kernels gave up comes back with the first result copy
+  int32_t* h_fail = reinterpret_cast<int32_t*>(s.h_ncand + 1);
+  TX_CUDA(cudaMemcpyAsync(h_fail, pl->beam->fail, sizeof(int32_t), cudaMemcpyDeviceToHost, pl->d2h));
+  auto gave_up = [&]() -> int {
+    if (*h_fail == 0) return TX_OK;
+    set_error("the beam's kernels gave up %d waits: results not valid (reset the beam)", *h_fail);
+    return TX_ERR_ABORTED;
+  };
   if (p->output == TX_OUT_CANDS) {
     TX_CUDA(cudaMemcpyAsync(s.h_ncand, s.d_ncand, sizeof(int64_t), cudaMemcpyDeviceToHost, pl->d2h));
     TX_CUDA(cudaEventRecord(s.count, pl->d2h));
@@ -177,6 +185,7 @@ int32_t tx_pipeline_pop(tx_pipeline* pl, void* h_out, int64_t* h_ncand, int64_t 
     if ((rc = wait_event(s.out, t0, timeout_us, "the candidate copy"))) return rc;
     *h_ncand = total;
     ++pl->popped;
+    if ((rc = gave_up())) return rc;
     if (total > p->max_cands) {
       set_error("%lld candidates, capacity %lld", (long long)total, (long long)p->max_cands);
       return TX_ERR_CAND_OVERFLOW;
@@ -187,7 +196,7 @@ int32_t tx_pipeline_pop(tx_pipeline* pl, void* h_out, int64_t* h_ncand, int64_t 
   TX_CUDA(cudaEventRecord(s.out, pl->d2h));
   if ((rc = wait_event(s.out, t0, timeout_us, "the block's results"))) return rc;
   ++pl->popped;
-  return TX_OK;
+  return gave_up();
 }
 
 void tx_pipeline_destroy(tx_pipeline* pl) {

@@ -6,6 +6,7 @@
 // operations on every host architecture, then rounded half away from zero
 // (llround).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -17,6 +18,9 @@
 namespace tx {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint32_t> g_first_wait_polls{kWaitPolls};
+
+uint32_t first_wait_polls() { return g_first_wait_polls.load(std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -324,7 +328,14 @@ using namespace tx;
 
 extern "C" {
 
-int32_t tx_version(void) { return 200; }
+int32_t tx_version(void) { return 300; }
+
+int32_t tx_set_wait_polls(int64_t polls, int64_t* previous) {
+  if (polls < 0 || polls > (int64_t)kWaitPolls) { set_error("polls must be in [0, %u]", kWaitPolls); return TX_ERR_INVALID_ARG; }
+  const uint32_t old = g_first_wait_polls.exchange((uint32_t)polls);
+  if (previous) *previous = old;
+  return TX_OK;
+}
 
 int32_t tx_last_error(char* buf, size_t size) {
   const std::string& e = g_last_error;
@@ -418,6 +429,94 @@ int32_t tx_plan_segments(int32_t nchan, const double* freq_mhz, double tsamp_s, 
   }
   return TX_OK;
 }
+
+}  // extern "C"
+
+struct tx_dsplan {
+  int64_t T = 0, L = 0;
+  std::vector<tx_segment> seg;
+  std::vector<tx_plan*> plans;
+  ~tx_dsplan() {
+    for (tx_plan* p : plans) tx_plan_destroy(p);
+  }
+};
+
+extern "C" {
+
+int32_t tx_dsplan_create(const tx_plan_desc* desc, int32_t f_max, tx_dsplan** out) {
+  if (!desc || !out || f_max < 1) { set_error("need a plan description, f_max >= 1 and an output handle"); return TX_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (desc->nsamp < 1 || desc->ndm < 1 || !desc->dm || !desc->widths || desc->nwidth < 1) {
+    set_error("need nsamp >= 1, ndm >= 1 and DM and width tables");
+    return TX_ERR_INVALID_ARG;
+  }
+  // a factor must divide the block: f_max drops to the largest power of two dividing T
+  int32_t fdiv = 1;
+  while (desc->nsamp % ((int64_t)fdiv * 2) == 0 && fdiv * 2 <= f_max) fdiv *= 2;
+  std::vector<int32_t> fac(desc->ndm);
+  int rc = tx_plan_segments(desc->nchan, desc->freq_mhz, desc->tsamp_s, desc->ndm, desc->dm, fdiv, fac.data());
+  if (rc) return rc;
+  tx_dsplan* ds = new (std::nothrow) tx_dsplan();
+  if (!ds) { set_error("out of host memory"); return TX_ERR_OOM; }
+  ds->T = desc->nsamp;
+  try {
+    int a = 0;
+    for (int i = 1; i <= desc->ndm; ++i) {
+      if (i < desc->ndm && fac[i] == fac[a]) continue;
+      const int32_t f = fac[a];
+      // widths in downsampled samples: W / f, at least 1, duplicates dropped
+      std::vector<int32_t> w;
+      for (int k = 0; k < desc->nwidth; ++k) w.push_back(std::max(1, desc->widths[k] / f));
+      std::sort(w.begin(), w.end());
+      w.erase(std::unique(w.begin(), w.end()), w.end());
+      tx_plan_desc d = *desc;
+      d.tsamp_s = desc->tsamp_s * f;
+      d.ndm = i - a;
+      d.dm = desc->dm + a;
+      d.nwidth = (int32_t)w.size();
+      d.widths = w.data();
+      d.nsamp = desc->nsamp / f;
+      tx_plan* p = nullptr;
+      if ((rc = tx_plan_create(&d, &p))) break;
+      ds->plans.push_back(p);
+      tx_segment sg{};
+      sg.dm_lo = a;
+      sg.dm_hi = i;
+      sg.factor = f;
+      sg.nwidth = d.nwidth;
+      for (int k = 0; k < d.nwidth; ++k) sg.widths[k] = w[k];
+      sg.nsamp = d.nsamp;
+      sg.overlap = p->L;
+      ds->seg.push_back(sg);
+      ds->L = std::max(ds->L, (int64_t)f * p->L);
+      a = i;
+    }
+  } catch (const std::bad_alloc&) {
+    set_error("out of host memory");
+    rc = TX_ERR_OOM;
+  }
+  if (rc) { delete ds; return rc; }
+  // native window time of a segment's output t' is f t' + L - f L_j
+  for (tx_segment& sg : ds->seg) sg.native_offset = ds->L - (int64_t)sg.factor * sg.overlap;
+  *out = ds;
+  return TX_OK;
+}
+
+int32_t tx_dsplan_get_info(const tx_dsplan* ds, int32_t* nseg, int64_t* overlap) {
+  if (!ds) { set_error("null plan"); return TX_ERR_INVALID_ARG; }
+  if (nseg) *nseg = (int32_t)ds->seg.size();
+  if (overlap) *overlap = ds->L;
+  return TX_OK;
+}
+
+int32_t tx_dsplan_segment(const tx_dsplan* ds, int32_t j, tx_segment* seg, const tx_plan** plan) {
+  if (!ds || j < 0 || j >= (int32_t)ds->seg.size()) { set_error("no segment %d", j); return TX_ERR_INVALID_ARG; }
+  if (seg) *seg = ds->seg[j];
+  if (plan) *plan = ds->plans[j];
+  return TX_OK;
+}
+
+void tx_dsplan_destroy(tx_dsplan* ds) { delete ds; }
 
 int32_t tx_plan_delay_table(const tx_plan* p, double* h_delay_ms) {
   if (!p || !h_delay_ms) { set_error("null argument"); return TX_ERR_INVALID_ARG; }

@@ -29,6 +29,10 @@ constexpr int kStage1StagedWords(int q) { return 2 * q + 16; }
 constexpr int kStage1RawBytes(int q) { return (5 * q + 2 + 15) / 16 * 16 + 16; }
 constexpr int kSmemMax = 232448;       // opt-in dynamic shared memory per block (227 KB)
 
+// Polls of an mbarrier before a kernel gives up waiting for a bulk copy; each
+// poll may suspend the thread for a while, so this is seconds in all.
+constexpr uint32_t kWaitPolls = 1u << 22;
+
 // ---- stage 2 (sub-bands -> fine DMs) tiling ---------------------------------
 // A stage-2 tile is nw2 32-bit words of uint16 pairs (two outputs each):
 // 512 words for groups of up to 16 fine DMs (16 warps), 256 beyond.
@@ -72,6 +76,9 @@ struct DevicePlan {
 
 void set_error(const char* fmt, ...);
 int64_t stage1_smem_bytes(int m, int q);
+// Polling limit of the first wait for each bulk copy in the kernels launched
+// from now on (tx_set_wait_polls; kWaitPolls unless changed).
+uint32_t first_wait_polls();
 
 }  // namespace tx
 
@@ -145,6 +152,7 @@ struct tx_beam {
   uint8_t* tail = nullptr;        // [nchan][tail_pitch] carried tail (compact beams)
   int64_t head = 0;               // where the next block lands
   double* run = nullptr;          // [ndm][2] running (mu, var); var < 0 = unset
+  int32_t* fail = nullptr;        // waits the beam's kernels gave up (device word after run)
   int64_t nblocks = 0;
 };
 

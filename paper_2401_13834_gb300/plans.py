@@ -2,18 +2,18 @@
 
 At high DM the smearing inside one channel exceeds the sampling time, so a
 plan de-disperses each DM range on data downsampled to about that smearing.
-The library gives every DM trial its factor (tx_plan_segments: the largest
-power of two not above the Eq. 1 delay across the lowest channel, in samples);
-runs of equal factors become segments. Segment j is an ordinary plan with
-sampling time f_j t_samp, blocks of T / f_j samples and widths W / f_j (at
-least 1, duplicates dropped); its input is the block averaged over f_j samples
-per channel (tx_downsample, rounded half up, still uint8). All segments of a
-block run as one batched step.
+The library makes the plan (tx_dsplan_create): every DM trial gets its factor
+(the largest power of two not above the Eq. 1 delay across the lowest
+channel, in samples, and dividing the block), runs of equal factors become
+segments, and segment j is an ordinary plan with sampling time f_j t_samp,
+blocks of T / f_j samples and widths W / f_j (at least 1, duplicates
+dropped); its input is the block averaged over f_j samples per channel
+(tx_downsample, rounded half up, still uint8). All segments of a block run
+as one batched step. This module only marshals those calls.
 
-Times: segment j's output t' refers to native samples [f_j t', f_j (t' + 1))
-of its own window, which starts f_j L_j native samples before the block (L_j
-its overlap); with the plan's native overlap L = max_j f_j L_j, the native
-window time of t' is f_j t' + L - f_j L_j (native_time()).
+Times: the library gives each segment its native offset, L - f_j L_j (L the
+native overlap, L_j the segment's); segment j's output t' then refers to
+native window time f_j t' + offset_j (native_time()).
 """
 from __future__ import annotations
 
@@ -31,32 +31,21 @@ class Segment:
     factor: int
     widths: np.ndarray  # in downsampled samples
     plan: "N.Plan"
+    native_offset: int  # native window time of output 0
 
 
 class DownsampledPlan:
     """Segments of a DM grid de-dispersed at their own time resolution."""
 
     def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, f_max: int = 64, group: int = 0, **plan_kw):
-        dms = np.ascontiguousarray(dms, dtype=np.float64)
-        widths = np.asarray(widths, dtype=np.int64)
-        fdiv = 1
-        while nsamp % (fdiv * 2) == 0 and fdiv * 2 <= f_max:
-            fdiv *= 2                                  # a factor must divide the block
-        fac = np.minimum(N.segment_factors(freqs_mhz, tsamp_s, dms, f_max), fdiv)
+        self._ds = N.DsPlan(freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, f_max=f_max, group=group, **plan_kw)
         self.nsamp = int(nsamp)
-        self.segments = []
-        a = 0
-        for i in range(1, dms.size + 1):
-            if i == dms.size or fac[i] != fac[a]:
-                f = int(fac[a])
-                w = np.array(sorted({max(1, int(W) // f) for W in widths}), dtype=np.int32)
-                p = N.Plan(freqs_mhz, tsamp_s * f, dms[a:i], nsub, w, nsamp // f, group=group, **plan_kw)
-                self.segments.append(Segment(a, i, f, w, p))
-                a = i
-        self.overlap = max(s.factor * s.plan.overlap for s in self.segments)
+        self.segments = [Segment(s["dm_lo"], s["dm_hi"], s["factor"], s["widths"], s["plan"], s["native_offset"])
+                         for s in self._ds.segments]
+        self.overlap = self._ds.overlap
         self.layout = self.segments[0].plan.layout
         self.nchan = self.segments[0].plan.nchan
-        self.ndm = int(dms.size)
+        self.ndm = int(np.asarray(dms).size)
 
     # ---- work, for the record ------------------------------------------------------
     def relative_stage1_work(self) -> float:
@@ -104,9 +93,9 @@ class DownsampledPlan:
 
     # ---- outputs -------------------------------------------------------------------
     def native_time(self, j: int, t):
-        """Native window time of segment j's output times t (see the module doc)."""
+        """Native window time of segment j's output times t (the library's offset; see the module doc)."""
         s = self.segments[j]
-        return s.factor * np.asarray(t, dtype=np.int64) + self.overlap - s.factor * s.plan.overlap
+        return s.factor * np.asarray(t, dtype=np.int64) + s.native_offset
 
     def merge_cands(self, outs):
         """All segments' candidates as one structured array with global DM index and

@@ -14,7 +14,10 @@ server takes such blocks from many beams as they arrive, at any time:
   batched step (tx_execute_batch), on one of two streams, so a new step is
   launched while the previous one is still running and their work overlaps
   on the device; memory of a step returns to the budget when it completes;
-* a block's latency runs from its arrival to its results being on the host.
+* a block's latency runs from its arrival to its results being on the host;
+* a step whose kernels gave up a bounded wait (tx_beam_failed) completes its
+  jobs with ``error`` set and no result, and takes the beams concerned out
+  of service: their carried state is no longer valid.
 
 The GPU side is behind a small engine interface (launch / done / finish), so
 the scheduling logic also runs, and is tested, with a simulated engine.
@@ -41,6 +44,7 @@ class Job:
     launched: Optional[float] = None
     done: Optional[float] = None
     result: Any = None
+    error: Optional[str] = None   # set when the block's results are not valid
 
     @property
     def latency(self) -> Optional[float]:
@@ -122,6 +126,8 @@ class Server:
                     j.done = t
                     self.busy[j.beam] = False
                     self.reserved -= j.reserve
+                    if j.error is not None:
+                        self.remove_beam(j.beam)
                 out += jobs
             else:
                 still.append((h, s, jobs))
@@ -259,10 +265,20 @@ class TxEngine:
         return h["ev"].query()
 
     def finish(self, h, jobs):
-        torch = self.torch
+        torch, tx = self.torch, self.tx
+        try:
+            h["batch"].wait()          # also checks that no member's kernels gave up a wait
+        except tx.TxError as e:
+            if e.code != tx.TX_ERR_ABORTED:
+                raise
+            for j in jobs:
+                if self.beams[j.beam][1].failed():
+                    j.error = "aborted: a kernel gave up a bounded wait"
         with torch.cuda.stream(h["stream"]):
             for j, p, (o, nc) in zip(jobs, [self.beams[j.beam][0] for j in jobs], h["outs"]):
-                if self.results is None:
+                if j.error is not None:
+                    j.result = None
+                elif self.results is None:
                     j.result = None
                 elif self.results == "cands" and p.output == "cands":
                     n = int(nc.item())

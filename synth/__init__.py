@@ -136,6 +136,23 @@ def tiny_workload(nchan=32, nsub=4, ndm=12, nsamp=300, dm_max=60.0, widths=(1, 2
     )
 
 
+def batched_beam(nchan: int, ndm: int, nsamp: int, dm_max: float = 3000.0, name: str = "beam") -> Workload:
+    """One beam of the batched workload: the MeerKAT-L band and sampling time
+    with its own channel count, DM-trial count (the MeerKAT-L grid's doubling
+    steps up to dm_max) and block length; 64 channels per sub-band."""
+    return Workload(
+        name=f"{name}-{nchan}ch-{ndm}dm-T{nsamp}",
+        freqs_mhz=channel_centres(856.0, 1712.0, nchan),
+        tsamp_s=153.12e-6,
+        dms=meerkat_dm_grid(ndm, dm_max),
+        nsub=nchan // 64,
+        widths=geometric_widths(256),
+        nsamp=nsamp,
+        noise_mean=128.0,
+        noise_std=12.0,
+    )
+
+
 def batched_workloads(nbeams: int = 64, seed: int = 3, dm_max: float = 3000.0) -> list:
     """Beams of uneven shape sharing the MeerKAT-L band and sampling time.
 
@@ -149,17 +166,7 @@ def batched_workloads(nbeams: int = 64, seed: int = 3, dm_max: float = 3000.0) -
         nchan = int(rng.choice([1024, 2048, 4096]))
         nsamp = int(rng.choice([32768, 65536, 131072]))
         ndm = int(rng.choice([1024, 4096, 8192]))
-        out.append(Workload(
-            name=f"beam{i}-{nchan}ch-{ndm}dm-T{nsamp}",
-            freqs_mhz=channel_centres(856.0, 1712.0, nchan),
-            tsamp_s=153.12e-6,
-            dms=meerkat_dm_grid(ndm, dm_max),
-            nsub=nchan // 64,
-            widths=geometric_widths(256),
-            nsamp=nsamp,
-            noise_mean=128.0,
-            noise_std=12.0,
-        ))
+        out.append(batched_beam(nchan, ndm, nsamp, dm_max, name=f"beam{i}"))
     return out
 
 

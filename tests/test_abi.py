@@ -164,3 +164,55 @@ def test_stage1_tile_fits_shared_memory_for_every_subband_width(tx, m):
         with pytest.raises(tx.TxError) as e:
             tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 2, wl.widths, wl.nsamp, tile_q1=2 * p.tile_q1)
         assert e.value.code == -8
+
+
+def test_noalloc_refuses_misaligned_buffers_before_any_launch(tx):
+    """tx_dedisperse_noalloc checks its pointers before it touches the GPU: a
+    series buffer that is 4- but not 8-byte aligned (the kernel stores two
+    outputs at a time) and an unaligned window are refused with
+    TX_ERR_INVALID_ARG. The addresses are never dereferenced."""
+    import ctypes as C
+    wl = synth.tiny_workload(nchan=32, nsub=4, ndm=6, nsamp=300)
+    p = _plan(tx, wl, output="series")
+    ld = (p.overlap + p.nsamp + 63) // 64 * 64
+    st = C.c_void_p(0)
+    rc = tx.lib.tx_dedisperse_noalloc(p.handle, C.c_void_p(0x10000), ld, C.c_void_p(0x20004), st)
+    assert rc == -1
+    rc = tx.lib.tx_dedisperse_noalloc(p.handle, C.c_void_p(0x10008), ld, C.c_void_p(0x20000), st)
+    assert rc == -1
+    rc = tx.lib.tx_dedisperse_noalloc(p.handle, C.c_void_p(0x10000), ld + 1, C.c_void_p(0x20000), st)
+    assert rc == -1
+
+
+def test_noalloc_wrapper_checks_tensors(tx):
+    """The binding checks what the C side cannot see (dtype, contiguity, size,
+    device) and raises before calling into the library."""
+    torch = pytest.importorskip("torch")
+    wl = synth.tiny_workload(nchan=32, nsub=4, ndm=6, nsamp=300)
+    p = _plan(tx, wl, output="series")
+    ld = (p.overlap + p.nsamp + 63) // 64 * 64
+    x = torch.zeros(p.nchan * ld, dtype=torch.uint8)
+    ser = torch.zeros(p.ndm * p.series_len, dtype=torch.int32)
+    cases = [
+        (x.to(torch.int16), ser, "must be torch.uint8"),
+        (x, ser.to(torch.int64), "must be torch.int32"),
+        (x.view(p.nchan, ld).t(), ser, "contiguous"),
+        (x[: p.nchan * ld - 1], ser, "needs"),
+        (x, ser[:-1], "needs"),
+        (x, ser, "CUDA tensor"),
+    ]
+    for xx, ss, msg in cases:
+        with pytest.raises(tx.TxError) as e:
+            tx.dedisperse_noalloc(p, xx, ld, ss)
+        assert e.value.code == -1 and msg in str(e.value), (msg, str(e.value))
+
+
+def test_wait_polls_setting_is_range_checked(tx):
+    """tx_set_wait_polls takes 0 .. 2^22 and returns the previous limit."""
+    import ctypes as C
+    old = C.c_int64()
+    assert tx.lib.tx_set_wait_polls(-1, C.byref(old)) == -1
+    assert tx.lib.tx_set_wait_polls((1 << 22) + 1, C.byref(old)) == -1
+    prev = tx.set_wait_polls(1000)
+    assert prev == 1 << 22
+    assert tx.set_wait_polls(prev) == 1000

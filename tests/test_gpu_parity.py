@@ -459,3 +459,29 @@ def test_f16_with_rfi_over_blocks(tx, compact):
         assert np.array_equal(got.astype(np.float64), ref), f"block {b}"
         rounded += int((ref != O.subband_dedisperse(win, op, plan.series_len)).sum())
     assert rounded > 0          # the bursts did push sums past 2048
+
+
+def test_misaligned_buffers_are_refused_before_any_launch(tx):
+    """A series buffer that is 4- but not 8-byte aligned (the kernel stores
+    two outputs at a time) and a workspace that is not 16-byte aligned (bulk
+    copies) are refused with TX_ERR_INVALID_ARG, and nothing runs: the beam
+    still gives the right series afterwards."""
+    wl = synth.tiny_workload(nchan=32, nsub=4, ndm=12, nsamp=300)
+    plan = make_plan(tx, wl, output="series")
+    X = rand_stream(plan.nchan, plan.overlap + plan.nsamp, 3)
+    beam = tx.Beam(plan)
+    beam.prime(torch.from_numpy(np.ascontiguousarray(X[:, :plan.overlap])).cuda())
+    blk = torch.from_numpy(np.ascontiguousarray(X[:, plan.overlap:])).cuda()
+    big = torch.zeros(plan.ndm * plan.series_len + 2, dtype=torch.int32, device="cuda")
+    ws = plan.alloc_workspace()
+    wsb = torch.zeros(plan.workspace_bytes + 16, dtype=torch.uint8, device="cuda")
+    for out, w in ((big[1:], ws), (big[:-2], wsb[4:])):
+        with pytest.raises(tx.TxError) as e:
+            tx.execute(plan, beam, blk, out=out, workspace=w)
+        assert e.value.code == -1
+    assert beam.nblocks == 0
+    out = big[:-2]
+    tx.execute(plan, beam, blk, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    D = O.subband_dedisperse(X, oracle_plan(wl), plan.series_len)
+    assert np.array_equal(tx.series_view(plan, out).cpu().numpy(), D)

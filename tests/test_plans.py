@@ -30,6 +30,37 @@ def test_segments_equal_oracle(tx):
     assert dp.relative_stage1_work() < 0.6
 
 
+@pytest.mark.parametrize("mk,f_max", [
+    (lambda: synth.tiny_workload(**WL), 64),
+    (lambda: synth.tiny_workload(**dict(WL, nsamp=6000)), 64),     # 16 is the largest power of two dividing T
+    (lambda: synth.tiny_workload(**dict(WL, nsamp=4096)), 4),
+    (lambda: synth.meerkat_l_workload(), 64),
+])
+def test_dsplan_segments_overlaps_and_offsets_equal_oracle(tx, mk, f_max):
+    """The library's downsampled plan (tx_dsplan_*) against oracle/plans.py:
+    segment DM ranges, factors and widths (f_max lowered to the largest power
+    of two dividing T), each segment plan's overlap against the oracle's
+    sub-band plan at f t_samp, the native overlap max_j f L_j, and the native
+    offsets L - f L_j."""
+    wl = mk()
+    ds = tx._native.DsPlan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, f_max=f_max,
+                           output="series")
+    fdiv = 1
+    while wl.nsamp % (2 * fdiv) == 0 and 2 * fdiv <= f_max:
+        fdiv *= 2
+    ref = PL.segments(wl.dms, wl.freqs_mhz, wl.tsamp_s, wl.widths, f_max=fdiv)
+    got = [(s["dm_lo"], s["dm_hi"], s["factor"], list(s["widths"])) for s in ds.segments]
+    assert got == [(a, b, f, list(w)) for a, b, f, w in ref]
+    Ls = []
+    for s, (a, b, f, w) in zip(ds.segments, ref):
+        op = O.SubbandPlan(wl.freqs_mhz, wl.tsamp_s * f, wl.dms[a:b], wl.nsub, 0, w)
+        assert s["overlap"] == op.overlap == s["plan"].overlap
+        assert s["nsamp"] == wl.nsamp // f == s["plan"].nsamp
+        Ls.append(f * op.overlap)
+    assert ds.overlap == max(Ls)
+    assert [s["native_offset"] for s in ds.segments] == [ds.overlap - x for x in Ls]
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("layout,nchan", [("ft", 64), ("tf", 64), ("tf", 63), ("ft", 63)])
 def test_downsample_kernel(tx, layout, nchan):

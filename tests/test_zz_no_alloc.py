@@ -60,10 +60,18 @@ def test_noalloc_matches_execute_on_two_calls(tx, mk):
 
 
 def test_noalloc_rejects_plans_beyond_its_scratch(tx):
+    """A plan whose scratch exceeds the static array is refused (TX_ERR_BUDGET)
+    before the library touches the buffers, so small ones do here; the C entry
+    point is called directly, past the binding's size checks."""
+    import ctypes as C
     wl = synth.meerkat_l_workload()
     plan = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, output="series")
     x = torch.zeros(64, dtype=torch.uint8, device="cuda")
     s = torch.zeros(64, dtype=torch.int32, device="cuda")
-    with pytest.raises(tx.TxError) as e:
-        tx.dedisperse_noalloc(plan, x, (plan.overlap + plan.nsamp + 63) // 64 * 64, s)
-    assert e.value.code == -7 and "static scratch" in str(e.value)
+    ld = (plan.overlap + plan.nsamp + 63) // 64 * 64
+    rc = tx.lib.tx_dedisperse_noalloc(plan.handle, C.c_void_p(x.data_ptr()), ld, C.c_void_p(s.data_ptr()),
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -7
+    buf = C.create_string_buffer(1024)
+    tx.lib.tx_last_error(buf, 1024)
+    assert "static scratch" in buf.value.decode()

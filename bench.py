@@ -265,7 +265,7 @@ def onchip_peaks(tx, peaks):
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     mhz = float(peaks.get("sm_max_mhz") or SM_MAX_MHZ_NOMINAL)
     derived = nsm * 128.0 * mhz * 1e6
-    measured = tx.measure_smem_bandwidth(4096)
+    measured = tx.measure_smem_bandwidth(16384)
     return {"smem_bytes_per_s_measured": measured, "smem_bytes_per_s_derived": derived, "sms": nsm,
             "sm_max_mhz": mhz, "frac_of_derived": measured / derived}
 

@@ -375,7 +375,7 @@ void tx_timer_destroy(tx_timer* timer);
    results are exactly those tx_execute would give for the same block, and
    its beam state (tail, running statistics, block count) advances the same way.
 
-   Waves: the beams are split, in order, into waves of at most 96 beams
+   Waves: the beams are split, in order, into waves of at most 92 beams
    whose summed per-beam workspace (tx_plan_info.workspace_bytes, or
    workspace_bytes_compact for a compact beam) fits workspace_budget when it
    is > 0; waves run one after another in the same workspace. At most two

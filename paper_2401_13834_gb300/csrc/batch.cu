@@ -38,7 +38,7 @@ namespace {
 // Constant-memory argument slots: a batch holds one slot for its lifetime; a
 // wave has at most kArgSlotBeams beams.
 constexpr int kArgSlots = 2;
-constexpr int kArgSlotBeams = 96;
+constexpr int kArgSlotBeams = 92;
 constexpr int kMaxDevices = 64;
 
 }  // namespace
@@ -74,7 +74,7 @@ int64_t beam_ws(const tx_plan* p, const tx_beam* b) { return b->compact ? p->ws_
 struct BatchLaunch {
   int kind = 0;
   int wave = 0;
-  int q1 = 0, split = 0, nwc = 0, mode = 0, half = 0;  // template selectors
+  int q1 = 0, split = 0, nwc = 0, mode = 0, half = 0, pipe = 0;  // template selectors
   int grid = 0, threads = 0, smem = 0;
   int nmem = 0, nunits = 0;                  // member beams, work units (stage 1: the plans' items)
   int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
@@ -129,6 +129,7 @@ const void* launch_kernel(const BatchLaunch& L) {
       }
 #undef TX_K1
     case kStage2:
+      if (L.pipe) return stage2_pipe_kernel<SlotArgs>(L.split, L.half);
 #define TX_K2(NW, SP)                                                        \
   (L.half ? (const void*)k_stage2_u16<NW, 32, SP, SlotArgs, true>            \
           : (const void*)k_stage2_u16<NW, 32, SP, SlotArgs, false>)
@@ -270,9 +271,9 @@ int build_batch(tx_batch* B, int64_t budget) {
     // Shared memory is laid out for the largest staged chunk and table of the
     // launch (which the plans size to fit, with room for the static sums); a
     // block as large as its largest group would idle warps of smaller groups.
-    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_split;
+    std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> by_split;
     for (int b : mem)
-      by_split[{stage2_split(B->plans[b]), B->plans[b]->nsub_chunk2, stage2_threads(B->plans[b]),
+      by_split[{B->plans[b]->pipe2, stage2_split(B->plans[b]), B->plans[b]->nsub_chunk2, stage2_threads(B->plans[b]),
                 B->plans[b]->interm == TX_INTERM_F16, B->plans[b]->e2w2}].push_back(b);
     auto s2_smem = [&](const std::vector<int>& g) {
       int slot = 0, sc = 0, e2w = 0;
@@ -287,8 +288,9 @@ int build_batch(tx_batch* B, int64_t budget) {
       BatchLaunch L;
       L.kind = kStage2;
       L.wave = wv;
-      L.split = std::get<0>(kv.first);
-      L.half = std::get<3>(kv.first);
+      L.pipe = std::get<0>(kv.first);
+      L.split = std::get<1>(kv.first);
+      L.half = std::get<4>(kv.first);
       if ((rc = add_members(L, kv.second, first,
                             [&](int b) -> int64_t { return (int64_t)B->plans[b]->nk * B->plans[b]->ntile2; })))
         return rc;
@@ -298,6 +300,12 @@ int build_batch(tx_batch* B, int64_t budget) {
       L.layout = std::get<0>(sm);
       L.smem = std::get<1>(sm);
       L.aux = std::get<2>(sm);
+      if (L.pipe) {   // stages of the largest chunk (slot words) and address table (aux: sub-bands per chunk)
+        int sc = 0;
+        for (int b : kv.second) sc = std::max(sc, B->plans[b]->nsub_chunk2);
+        L.aux = sc;
+        L.smem = (int)((int64_t)kPipeStages2 * (2 * (int64_t)L.layout + (int64_t)(kPipeMaxGroup2 + 1) * ((sc + 3) & ~3)) * 4);
+      }
       if (L.smem > kSmemMax - 1024) { set_error("batched stage-2 shared memory (%d bytes) exceeds the limit", L.smem); return TX_ERR_UNSUPPORTED; }
       L.threads = threads;
       L.grid = std::min(L.nunits, nsm);
@@ -429,6 +437,11 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
         break;
       }
       case kStage2:
+        if (L.pipe) {
+          launch_stage2_pipe<SlotArgs>(L.split, L.half, L.grid, L.threads, L.smem, st, src, off, mem, L.nmem, L.nunits,
+                                       L.aux, L.layout);
+          break;
+        }
 #define TX_B2(NW, SP)                                                                                          \
   do {                                                                                                         \
     if (L.half)                                                                                                \

@@ -40,6 +40,7 @@ int upload(T** dst, const std::vector<T>& v) {
 bool is16(const tx_plan* p) { return p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16; }
 
 int stage2_smem(const tx_plan* p) {
+  if (p->pipe2) return (int)stage2_pipe_smem(p->nsub_chunk2, p->sww2);
   if (is16(p)) return stage2_u16_smem_for(p->nsub_chunk2 * p->sww2, p->nsub_chunk2, p->e2w2);
   return p->nsub_chunk2 * p->sw2_i32 * 4;
 }
@@ -78,6 +79,7 @@ int do_upload(tx_plan* p) {
   if ((rc = upload(&p->dev.widths, p->widths))) return rc;
   if ((rc = upload(&p->dev.items1, p->items1))) return rc;
   if ((rc = upload(&p->dev.tab1, p->tab1))) return rc;
+  if ((rc = upload(&p->dev.tab2, p->tab2))) return rc;
   const int s1 = (int)stage1_smem_bytes(p->m, p->q1);
   switch (p->q1) {
     case 256: rc = set_stage1_attr_for<256>(p, s1); break;
@@ -87,7 +89,9 @@ int do_upload(tx_plan* p) {
   }
   if (rc) return rc;
   const int s2 = stage2_smem(p);
-  if (is16(p)) {
+  if (p->pipe2) {
+    TX_CUDA(raise_smem_limit(stage2_pipe_kernel<OneBeam>(p->split2, p->interm == TX_INTERM_F16), s2));
+  } else if (is16(p)) {
     switch (stage2_split(p)) {
       case 8: rc = set_stage2_attr<512, 32, 8>(s2); break;
       case 4: rc = set_stage2_attr<512, 32, 4>(s2); break;
@@ -217,6 +221,7 @@ void tx_plan_destroy(tx_plan* p) {
     cudaFree(p->dev.widths);
     cudaFree(p->dev.items1);
     cudaFree(p->dev.tab1);
+    cudaFree(p->dev.tab2);
     cudaSetDevice(prev);
   }
   delete p;
@@ -433,7 +438,12 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   // stage 2 (+ exact per-tile sums)
   const bool series = p->output == TX_OUT_SERIES;
   {
-    if (is16(p)) {
+    if (p->pipe2) {
+      const int nunits = p->nk * p->ntile2;
+      launch_stage2_pipe<OneBeam>(p->split2, half, std::min(nunits, std::max(p->dev.num_sms, 1)), stage2_threads(p),
+                                  stage2_smem(p), st, OneBeam{a}, nullptr, nullptr, 1, nunits, p->nsub_chunk2,
+                                  p->nsub_chunk2 * p->sww2);
+    } else if (is16(p)) {
       const int nunits = p->nk * p->ntile2;
       const int grid = std::min(nunits, std::max(p->dev.num_sms, 1));
       const int slot = p->nsub_chunk2 * p->sww2;
@@ -759,8 +769,9 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   const size_t b_abase = align256(p->abase.size() * 4);
   const size_t b_e2 = align256(p->e2.size() * 4);
   const size_t b_P = align256((size_t)p->nk * p->nsub * p->Pp * 2);
-  const size_t b_part = align256((size_t)p->ndm * p->ntile2 * 16);
-  const size_t need = b_items + b_d1 + b_abase + b_e2 + b_P + b_part;
+  const size_t b_part = align256((size_t)p->ndm * p->ntile2 * (p->pipe2 ? p->split2 : 1) * 16);
+  const size_t b_tab2 = align256(p->tab2.size() * 4);
+  const size_t need = b_items + b_d1 + b_abase + b_e2 + b_P + b_part + b_tab2;
   if (need > kNoAllocScratchBytes) {
     set_error("this plan needs %zu bytes of scratch; the static scratch of tx_dedisperse_noalloc holds %zu",
               need, kNoAllocScratchBytes);
@@ -779,11 +790,14 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   int32_t* e2 = reinterpret_cast<int32_t*>(base + b_items + b_d1 + b_abase);
   uint16_t* P = reinterpret_cast<uint16_t*>(base + b_items + b_d1 + b_abase + b_e2);
   longlong2* part = reinterpret_cast<longlong2*>(base + b_items + b_d1 + b_abase + b_e2 + b_P);
+  int32_t* tab2 = reinterpret_cast<int32_t*>(base + b_items + b_d1 + b_abase + b_e2 + b_P + b_part);
   cudaStream_t st = (cudaStream_t)stream;
   TX_CUDA(cudaMemcpyAsync(items, p->items1.data(), p->items1.size() * sizeof(Stage1Item), cudaMemcpyHostToDevice, st));
   TX_CUDA(cudaMemcpyAsync(d1, p->d1.data(), p->d1.size() * 4, cudaMemcpyHostToDevice, st));
   TX_CUDA(cudaMemcpyAsync(abase, p->abase.data(), p->abase.size() * 4, cudaMemcpyHostToDevice, st));
   TX_CUDA(cudaMemcpyAsync(e2, p->e2.data(), p->e2.size() * 4, cudaMemcpyHostToDevice, st));
+  if (!p->tab2.empty())
+    TX_CUDA(cudaMemcpyAsync(tab2, p->tab2.data(), p->tab2.size() * 4, cudaMemcpyHostToDevice, st));
   // Nothing in the scratch must start at zero: stage 1 writes every stage-1
   // sum that stage 2 reads, and stage 2 writes every per-tile sum.
 
@@ -796,6 +810,7 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   a.d1 = d1;
   a.abase = abase;
   a.e2 = e2;
+  a.tab2 = tab2;
   a.items = items;
   a.R = ld;
   a.start = 0;
@@ -808,7 +823,7 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   a.nsub = p->nsub;
   a.ndm = p->ndm;
   a.G = p->group;
-  a.nk = p->nk;
+  a.split2 = p->pipe2 ? p->split2 : 1;
   a.SC = p->nsub_chunk2;
   a.SWW = p->sww2;
   a.ntile2 = p->ntile2;
@@ -835,9 +850,17 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
 
   // stage 2 into the caller's series [ndm][T + W_max - 1]
   const int slot = p->nsub_chunk2 * p->sww2;
-  const int smem2 = stage2_u16_smem_for(slot, p->nsub_chunk2, p->e2w2);
+  const int smem2 = p->pipe2 ? (int)stage2_pipe_smem(p->nsub_chunk2, p->sww2)
+                             : stage2_u16_smem_for(slot, p->nsub_chunk2, p->e2w2);
   const int nunits = p->nk * p->ntile2;
   const int grid2 = std::min(nunits, std::max(nsm, 1));
+  if (p->pipe2) {
+    TX_CUDA(raise_smem_limit(stage2_pipe_kernel<OneBeam>(p->split2, false), smem2));
+    launch_stage2_pipe<OneBeam>(p->split2, false, grid2, stage2_threads(p), smem2, st, OneBeam{a}, nullptr, nullptr, 1,
+                                nunits, p->nsub_chunk2, slot);
+    TX_CUDA(cudaGetLastError());
+    return TX_OK;
+  }
 #define TX_NA_S2(NW, SP)                                                                                       \
   do {                                                                                                         \
     TX_CUDA(raise_smem_limit((const void*)k_stage2_u16<NW, 32, SP, OneBeam>, smem2));                          \

@@ -58,6 +58,7 @@ struct BeamArgs {
   const int32_t* widths;         // [nw]
   const Stage1Item* items;       // stage-1 work items of the plan
   const int32_t* tab1;           // their precomputed offset tables (window phase tab1_phase)
+  const int32_t* tab2;           // pipelined stage 2: offset tables per (coarse group, sub-band chunk)
   float* outf;                   // cube / plane S/N
   uint8_t* outw;                 // plane best-width index
   tx_cand* cands;                // candidate records
@@ -67,7 +68,7 @@ struct BeamArgs {
   int64_t R, head, start, T, Pp, Dp, Td, max_cands;
   int64_t L, tail_pitch;
   double lam, gamma;
-  int32_t nchan, m, nsub, ndm, G, nk, SC, SWW, ntile2, ntile3, nw, wmax;
+  int32_t nchan, m, nsub, ndm, G, split2, SC, SWW, ntile2, ntile3, nw, wmax;  // split2: part entries per stage-2 tile
   int32_t layout, ingest_vec, running, output, compact, tail_pad, half, box_vec, tab1_phase;
   uint32_t polls;                // polling limit of the first wait for each bulk copy
 };
@@ -1081,6 +1082,318 @@ k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __r
   }
 }
 
+// Stage 2 as a pipeline without block-wide barriers (16-bit intermediates,
+// groups of up to 16 fine DMs). Warps [0, NC) are consumers: warp w sums
+// fine DM kG + w / SPLIT over words (w % SPLIT) * 512 / SPLIT .. of a unit's
+// tile of 512 words (1024 outputs), VW words per lane. Then one issuing warp
+// and kPipeProc processing warps. A block walks the chunks of its units (unit
+// u = blockIdx.x + i * gridDim.x; a chunk = up to SC sub-bands) in order
+// through kPipeStages shared-memory stages; for chunk c in stage c % kPipeStages:
+//   * the issuing warp waits until every consumer has left the stage
+//     (mbarrier `empty`), announces the bytes and bulk-copies (TMA) the
+//     chunk's uint16 rows into the stage's even slots, one row per lane, and
+//     the chunk's offset table (precomputed with the plan: per fine DM and
+//     sub-band the element offset of its pairs from the staged row start,
+//     then the rows' start offsets) into the stage's table; both complete the
+//     mbarrier `full`. It runs up to kPipeStages chunks ahead;
+//   * the processing warps wait for `full`, write the odd copy (pairs re-formed
+//     one element later, as in k_stage2_u16) and arrive on `ready`;
+//   * consumers wait for `ready`, sum (an odd offset reads the odd copy), and
+//     arrive on `empty`.
+// The copies, the odd copies and the sums of different chunks thus overlap,
+// and no thread waits for the whole block. After a unit's last chunk each
+// consumer warp stores its slice of the series and its exact sums to
+// part[d][tile * SPLIT + (w % SPLIT)]. Every wait is bounded; a wait that
+// gives up raises a block-wide abort flag that every other wait sees, the
+// issuing warp waits (at the full limit) for the copies it has in flight, and
+// the block returns.
+constexpr int kPipeStages = kPipeStages2;
+constexpr int kPipeProc = kPipeProd2 - 1;   // processing warps (the other producer warp issues)
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(done)
+               : "r"(smem_addr(bar)), "r"(parity)
+               : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar)) : "memory");
+}
+// Bounded wait that also gives up as soon as another thread of the block has
+// raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, uint32_t polls,
+                                                   const volatile int* abort) {
+  for (uint32_t i = 0; i < polls; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  return false;
+}
+
+// The walk of one role over the block's chunks: unit, chunk within the unit,
+// tile, and which member's arguments apply (read from the source when used,
+// so that no copy of them lives in registers).
+template <typename Src>
+struct PipeCursor {
+  MemberCursor mc;
+  int u, ch, nchunk, k, tile, ns, s0, SC, nsub, beam;
+  int64_t t0;
+  __device__ __forceinline__ BeamArgs args(const Src& src) const { return src.get(beam); }
+  __device__ __forceinline__ void load(const Src& src, const int32_t* __restrict__ uoff,
+                                       const int32_t* __restrict__ umem, int nmem) {
+    int lu;
+    if constexpr (Src::kBatch) {
+      mc.seek(uoff, umem, nmem, u);
+      lu = u - mc.lo;
+      beam = mc.beam;
+    } else {
+      lu = u;
+      beam = 0;
+    }
+    const BeamArgs a = src.get(beam);
+    SC = a.SC;
+    nsub = a.nsub;
+    nchunk = (nsub + SC - 1) / SC;
+    k = lu / a.ntile2;
+    tile = lu - k * a.ntile2;
+    t0 = (int64_t)tile * 1024;
+    ch = 0;
+    s0 = 0;
+    ns = min(SC, nsub);
+  }
+  // first chunk of unit u0; false when the block has no unit
+  __device__ __forceinline__ bool start(const Src& src, const int32_t* uoff, const int32_t* umem, int nmem,
+                                        int nunits) {
+    u = blockIdx.x;
+    if (u >= nunits) return false;
+    load(src, uoff, umem, nmem);
+    return true;
+  }
+  // the next chunk; false past the block's last one
+  __device__ __forceinline__ bool next(const Src& src, const int32_t* uoff, const int32_t* umem, int nmem,
+                                       int nunits) {
+    if (++ch < nchunk) {
+      s0 = ch * SC;
+      ns = min(SC, nsub - s0);
+      return true;
+    }
+    u += gridDim.x;
+    if (u >= nunits) return false;
+    load(src, uoff, umem, nmem);
+    return true;
+  }
+};
+
+template <int VW, typename Src, bool HALF = false>
+__global__ void __launch_bounds__(VW == 16 ? 640 : 1024, 1)
+k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem,
+              int nunits, int slot, int tabw) {
+  extern __shared__ __align__(16) uint32_t smp[];
+  constexpr int SPLIT = 16 / VW;                         // consumer warps per fine DM
+  __shared__ __align__(8) uint64_t full[kPipeStages], ready[kPipeStages], empty[kPipeStages];
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NC = (int)(blockDim.x >> 5) - 1 - kPipeProc;   // consumer warps
+  const int stage_words = 2 * slot + tabw;                 // even slots, odd slots, offset table
+  if ((int)blockIdx.x >= nunits) return;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kPipeStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&ready[i], kPipeProc * 32);
+      mbar_init(&empty[i], NC * 32);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();   // barriers initialised: the only block-wide barrier
+  volatile int* abort = &abort_flag;
+  // a wait that gave up: the first thread to see it raises the flag and records it
+  auto give_up = [&](const BeamArgs& a) {
+    if (atomicExch(&abort_flag, 1) == 0) record_give_up(a);
+  };
+
+  if (warp == NC) {
+    // --------------------------------------------------------- the issuing warp
+    PipeCursor<Src> ic;
+    bool more = ic.start(src, uoff, umem, nmem, nunits);
+    int64_t q = 0;   // chunks issued
+    while (more) {
+      const BeamArgs a = ic.args(src);
+      const int bq = (int)(q % kPipeStages);
+      // the stage's previous chunk: every consumer has left it
+      if (q >= kPipeStages &&
+          !mbar_wait_or_abort(&empty[bq], (uint32_t)((q / kPipeStages - 1) & 1), a.polls, abort)) {
+        give_up(a);
+        break;
+      }
+      const int SCq = (a.SC + 3) & ~3;
+      const int32_t* tabk = a.tab2 + ((size_t)ic.k * ic.nchunk + ic.ch) * (size_t)(a.G + 1) * SCq;
+      uint32_t* ev = smp + (size_t)bq * stage_words;
+      if (lane == 0) mbar_expect_tx(&full[bq], ((uint32_t)ic.ns * (uint32_t)a.SWW + (uint32_t)(a.G + 1) * SCq) * 4u);
+      __syncwarp();
+      fence_proxy_async();
+      const uint16_t* P = static_cast<const uint16_t*>(a.P);
+      for (int ss = lane; ss < ic.ns; ss += 32) {   // one row per lane: its start from the table's last row
+        const int s = ic.s0 + ss;
+        const int64_t b = ic.t0 + __ldg(tabk + (size_t)a.G * SCq + ss);
+        bulk_g2s(ev + (size_t)ss * a.SWW, P + ((size_t)ic.k * a.nsub + s) * a.Pp + b, (uint32_t)a.SWW * 4u,
+                 &full[bq]);
+      }
+      if (lane == 0) bulk_g2s(ev + 2 * (size_t)slot, tabk, (uint32_t)(a.G + 1) * SCq * 4u, &full[bq]);
+      ++q;
+      more = ic.next(src, uoff, umem, nmem, nunits);
+    }
+    if (lane == 0) {
+      // copies still in flight complete before the block's shared memory is released
+      for (int64_t r = q > kPipeStages ? q - kPipeStages : 0; r < q; ++r)
+        mbar_wait(&full[(int)(r % kPipeStages)], (uint32_t)((r / kPipeStages) & 1), kMbarPolls);
+    }
+    return;
+  }
+
+  if (warp > NC) {
+    // ---------------------------------------------------- the processing warps
+    const int pw = warp - NC - 1;
+    PipeCursor<Src> pc;
+    bool more = pc.start(src, uoff, umem, nmem, nunits);
+    for (int64_t p = 0; more; ++p) {
+      const BeamArgs a = pc.args(src);
+      const int bp = (int)(p % kPipeStages);
+      if (!mbar_wait_or_abort(&full[bp], (uint32_t)((p / kPipeStages) & 1), a.polls, abort)) {
+        give_up(a);
+        return;
+      }
+      // odd copy: od[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged row start
+      const uint32_t* ev = smp + (size_t)bp * stage_words;
+      uint32_t* od = smp + (size_t)bp * stage_words + slot;
+      for (int ss = pw; ss < pc.ns; ss += kPipeProc) {
+        const uint32_t* r = ev + (size_t)ss * a.SWW;
+        uint32_t* o = od + (size_t)ss * a.SWW;
+        for (int j = 4 * lane; j < a.SWW - 4; j += 128) {
+          const uint4 x = *reinterpret_cast<const uint4*>(r + j);
+          const uint32_t y = r[j + 4];
+          *reinterpret_cast<uint4*>(o + j) =
+              make_uint4(__funnelshift_r(x.x, x.y, 16), __funnelshift_r(x.y, x.z, 16), __funnelshift_r(x.z, x.w, 16),
+                         __funnelshift_r(x.w, y, 16));
+        }
+      }
+      mbar_arrive(&ready[bp]);
+      more = pc.next(src, uoff, umem, nmem, nunits);
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  const int g = warp / SPLIT, part_i = warp - g * SPLIT;   // fine DM of the group, part of the tile
+  const int jbase = part_i * (512 / SPLIT);
+  uint32_t aw[VW], ah[VW];   // uint16 pairs: sum of words, sum of high lanes
+  float fl[VW], fh[VW];      // half pairs: FP32 sums of the low and high halves
+#pragma unroll
+  for (int v = 0; v < VW; ++v) {
+    aw[v] = ah[v] = 0u;
+    fl[v] = fh[v] = 0.f;
+  }
+  PipeCursor<Src> cc;
+  cc.start(src, uoff, umem, nmem, nunits);
+  for (int64_t p = 0;; ++p) {
+    const BeamArgs a = cc.args(src);
+    const int bp = (int)(p % kPipeStages);
+    if (!mbar_wait_or_abort(&ready[bp], (uint32_t)((p / kPipeStages) & 1), a.polls, abort)) {
+      give_up(a);
+      return;
+    }
+    const int dfirst = cc.k * a.G;
+    const int nd = min(a.G, a.ndm - dfirst);
+    if (g < nd) {
+      const int SCq = (a.SC + 3) & ~3;
+      const uint32_t* ev = smp + (size_t)bp * stage_words + jbase + lane;   // this lane's first word, even slots
+      const uint32_t* od = ev + slot;                                         // ... odd slots
+      const int32_t* t = reinterpret_cast<const int32_t*>(smp + (size_t)bp * stage_words + 2 * (size_t)slot) + g * SCq;
+      const int ns = cc.ns, sww = a.SWW;
+      int ss = 0;
+#pragma unroll 2
+      for (; ss + 1 < ns; ss += 2) {
+        const int2 tt = *reinterpret_cast<const int2*>(t + ss);
+        const uint32_t* r0 = ((tt.x & 1) ? od : ev) + ss * sww + (tt.x >> 1);
+        const uint32_t* r1 = ((tt.y & 1) ? od : ev) + (ss + 1) * sww + (tt.y >> 1);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          if constexpr (HALF) {
+            const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(r0 + 32 * v));
+            const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(r1 + 32 * v));
+            fl[v] += f0.x + f1.x;
+            fh[v] += f0.y + f1.y;
+          } else {
+            const uint32_t w0 = r0[32 * v], w1 = r1[32 * v];
+            aw[v] += w0 + w1;
+            madd_hi16(ah[v], w0);
+            madd_hi16(ah[v], w1);
+          }
+        }
+      }
+      if (ss < ns) {
+        const int o = t[ss];
+        const uint32_t* r0 = ((o & 1) ? od : ev) + ss * sww + (o >> 1);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          if constexpr (HALF) {
+            const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(r0 + 32 * v));
+            fl[v] += f0.x;
+            fh[v] += f0.y;
+          } else {
+            const uint32_t w0 = r0[32 * v];
+            aw[v] += w0;
+            madd_hi16(ah[v], w0);
+          }
+        }
+      }
+    }
+    mbar_arrive(&empty[bp]);   // this thread is done with the stage
+    if (cc.ch + 1 == cc.nchunk) {
+      // the unit's sums are complete: this warp's slice of the series and its exact sums
+      long long s1 = 0;
+      unsigned long long s2 = 0;
+      if (g < nd) {
+        const int d = dfirst + g;
+        int32_t* drow = a.D + (size_t)d * a.Dp;
+        const int O = HALF ? a.hoff[a.nsub] : 0;   // the offsets taken out in stage 1, added back
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const int64_t ta = cc.t0 + 2 * (jbase + lane + 32 * v);
+          uint32_t lo, hi;
+          if constexpr (HALF) {
+            // the halves hold integers and their FP32 sums stay below 2^24: exact
+            lo = (uint32_t)((int)fl[v] + O);
+            hi = (uint32_t)((int)fh[v] + O);
+          } else {
+            lo = aw[v] - (ah[v] << 16);
+            hi = ah[v];
+          }
+          if (ta + 1 < a.Td && (a.Dp & 1) == 0) {
+            *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
+          } else {
+            if (ta < a.Td) drow[ta] = (int32_t)lo;
+            if (ta + 1 < a.Td) drow[ta + 1] = (int32_t)hi;
+          }
+          if (ta < a.T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
+          if (ta + 1 < a.T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
+        }
+      }
+      warp_sum_stats(s1, s2);
+      if (g < nd && lane == 0)
+        a.part[((size_t)(dfirst + g) * a.ntile2 + cc.tile) * SPLIT + part_i] = make_longlong2(s1, (long long)s2);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        aw[v] = ah[v] = 0u;
+        fl[v] = fh[v] = 0.f;
+      }
+    }
+    if (!cc.next(src, uoff, umem, nmem, nunits)) break;
+  }
+}
+
 // Stage 2 from int32 intermediates (plain layout, one output per load); one
 // block per (tile of 2 NW outputs, coarse group), sub-band chunks in turn.
 template <int NW>
@@ -1165,8 +1478,9 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
   }
   const int64_t T = a.T;
   unsigned long long s1 = 0, s2 = 0;
-  for (int i = 0; i < a.ntile2; ++i) {
-    const longlong2 v = a.part[(size_t)d * a.ntile2 + i];
+  const int np = a.ntile2 * a.split2;   // the stage-2 tiles' exact sums (per warp of a fine DM in a pipeline plan)
+  for (int i = 0; i < np; ++i) {
+    const longlong2 v = a.part[(size_t)d * np + i];
     s1 += (unsigned long long)v.x;
     s2 += (unsigned long long)v.y;
   }
@@ -1599,7 +1913,42 @@ inline int stage2_u16_smem_for(int slot, int sc, int e2w) {
 // Warps per fine DM of the uint16 stage 2 (the plan's tile choice).
 inline int stage2_split(const tx_plan* p) { return p->split2; }
 
-inline int stage2_threads(const tx_plan* p) { return std::min(p->group, kStage2MaxGroup) * 32 * stage2_split(p); }
+inline int stage2_threads(const tx_plan* p) {
+  if (p->pipe2) return (p->group * p->split2 + kPipeProd2) * 32;   // consumer warps, then the issuing and processing warps
+  return std::min(p->group, kStage2MaxGroup) * 32 * stage2_split(p);
+}
+
+// The pipelined stage 2 for `split` consumer warps per fine DM (4, 2 or 1: 4, 8
+// or 16 words per lane), half or uint16 intermediates.
+template <typename Src>
+const void* stage2_pipe_kernel(int split, bool half) {
+  switch (split) {
+    case 4: return half ? (const void*)k_stage2_pipe<4, Src, true> : (const void*)k_stage2_pipe<4, Src, false>;
+    case 2: return half ? (const void*)k_stage2_pipe<8, Src, true> : (const void*)k_stage2_pipe<8, Src, false>;
+    default: return half ? (const void*)k_stage2_pipe<16, Src, true> : (const void*)k_stage2_pipe<16, Src, false>;
+  }
+}
+
+// Launches it over `nunits` (coarse group, tile) units; slot = the largest
+// chunk's staged words (sub-bands x words), smem from stage2_pipe_smem.
+template <typename Src>
+void launch_stage2_pipe(int split, bool half, int grid, int threads, int smem, cudaStream_t st, const Src& src,
+                        const int32_t* uoff, const int32_t* umem, int nmem, int nunits, int sc, int slot) {
+  const int tabw = (kPipeMaxGroup2 + 1) * ((sc + 3) & ~3);
+#define TX_P2(VW)                                                                                               \
+  do {                                                                                                          \
+    if (half)                                                                                                   \
+      k_stage2_pipe<VW, Src, true><<<grid, threads, smem, st>>>(src, uoff, umem, nmem, nunits, slot, tabw);    \
+    else                                                                                                        \
+      k_stage2_pipe<VW, Src, false><<<grid, threads, smem, st>>>(src, uoff, umem, nmem, nunits, slot, tabw);   \
+  } while (0)
+  switch (split) {
+    case 4: TX_P2(4); break;
+    case 2: TX_P2(8); break;
+    default: TX_P2(16); break;
+  }
+#undef TX_P2
+}
 
 // The arguments of one execute of plan p on beam b: the block lands at ring
 // position `head`, buffer time 0 sits at `start` (a compact beam uses its
@@ -1630,6 +1979,7 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.half = p->interm == TX_INTERM_F16;
   a.box_vec = p->box_vec;
   a.tab1 = p->dev.tab1;
+  a.tab2 = p->dev.tab2;
   a.tab1_phase = p->tab1_phase;
   a.run = b->run;
   a.d1 = p->dev.d1;
@@ -1656,7 +2006,7 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.nsub = p->nsub;
   a.ndm = p->ndm;
   a.G = p->group;
-  a.nk = p->nk;
+  a.split2 = p->pipe2 ? p->split2 : 1;
   a.SC = p->nsub_chunk2;
   a.SWW = p->sww2;
   a.ntile2 = p->ntile2;

@@ -208,6 +208,16 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   if (std::min(G, kStage2MaxGroup) * split > 32) { set_error("min(group, 32) * tile_split2 must be <= 32 (group %d)", G); return TX_ERR_INVALID_ARG; }
   p->split2 = split;
   p->nw2 = split == 1 ? 256 : 512;
+  // 16-bit intermediates with groups of up to 16 fine DMs: the pipelined stage 2,
+  // 1024-output tiles, consumer warps per fine DM the largest of 4, 2, 1 that
+  // keeps group x warps <= 28 (the desc's tile_split2 applies to the other kernel)
+  const bool is16 = d->interm == TX_INTERM_U16 || d->interm == TX_INTERM_F16;
+  const int32_t sww_pipe = (int32_t)round_up(512 + (span2 + 7 + 2) / 2 + 6, 4);
+  p->pipe2 = is16 && G <= kPipeMaxGroup2 && stage2_pipe_smem(1, sww_pipe) <= kSmemMax - 1024;
+  if (p->pipe2) {
+    p->split2 = G * 4 <= 28 ? 4 : G * 2 <= 28 ? 2 : 1;
+    p->nw2 = 512;
+  }
   const int64_t tt2 = 2 * (int64_t)p->nw2;
   p->ntile2 = (int32_t)((p->Td + tt2 - 1) / tt2);
   p->sww2 = (int32_t)round_up(p->nw2 + (span2 + 7 + 2) / 2 + 6, 4);
@@ -215,7 +225,12 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   // uint16 path reads [base, base + 2 sww2) with base <= t0 + 15; int32 path
   // reads [t0 + emin, + tt2 + span2 + 16)
   p->Pp = round_up(std::max<int64_t>(last_t0 + 16 + 2 * (int64_t)p->sww2, last_t0 + 16 + tt2 + span2 + 16) + 16, 64);
-  if (p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16) {
+  if (p->pipe2) {
+    // per stage: even and odd slots of sww2 words per sub-band, and the address table
+    int32_t sc = nsub;
+    while (sc > 1 && stage2_pipe_smem(sc, p->sww2) > kSmemMax - 1024) --sc;
+    p->nsub_chunk2 = stage2_pipe_smem(sc, p->sww2) <= kSmemMax - 1024 ? sc : 0;
+  } else if (p->interm == TX_INTERM_U16 || p->interm == TX_INTERM_F16) {
     // two buffers of a group's delays, double-buffered even copy + odd copy + address table
     p->e2w2 = (int32_t)round_up((int64_t)G * nsub, 4);
     const int64_t per_sub = 3 * (int64_t)p->sww2 * 4 + (int64_t)kStage2MaxGroup * 4 + 8;
@@ -226,6 +241,24 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
     p->nsub_chunk2 = (int32_t)std::min<int64_t>(nsub, (kSmemMax - 1024) / per_sub);
   }
   if (p->nsub_chunk2 < 1) { set_error("stage-2 delay spread within a DM group (%d samples) too large; use a smaller group", span2); return TX_ERR_UNSUPPORTED; }
+  if (p->pipe2) {
+    // offsets of every (fine DM, sub-band) from its sub-band's staged row start,
+    // which is the tile start plus the group's first (smallest) delay rounded
+    // down to 8 elements; tiles start at multiples of 1024
+    const int SC = p->nsub_chunk2, SCq = (SC + 3) & ~3, nch = (nsub + SC - 1) / SC;
+    p->tab2.assign((size_t)nk * nch * (G + 1) * SCq, 0);
+    for (int k = 0; k < nk; ++k)
+      for (int ch = 0; ch < nch; ++ch) {
+        int32_t* blk = p->tab2.data() + ((size_t)k * nch + ch) * (G + 1) * SCq;
+        for (int ss = 0; ss < SC && ch * SC + ss < nsub; ++ss) {
+          const int s = ch * SC + ss;
+          const int32_t start = p->e2[(size_t)k * G * nsub + s] & ~7;
+          blk[(size_t)G * SCq + ss] = start;
+          for (int g = 0; g < G && k * G + g < ndm; ++g)
+            blk[(size_t)g * SCq + ss] = p->e2[(size_t)(k * G + g) * nsub + s] - start;
+        }
+      }
+  }
   p->Dp = round_up(p->Td + 8, 8);
   p->ntile3 = (int32_t)((p->T + kBoxTile - 1) / kBoxTile);
 
@@ -302,7 +335,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   int64_t off = 0;
   p->ws_P = off; off = round_up(off + (int64_t)nk * nsub * p->Pp * psz, 256);
   p->ws_D = off; off = round_up(off + (p->output == TX_OUT_SERIES ? 0 : (int64_t)ndm * p->Dp * 4), 256);
-  p->ws_part = off; off = round_up(off + (int64_t)ndm * p->ntile2 * 16, 256);
+  p->ws_part = off; off = round_up(off + (int64_t)ndm * p->ntile2 * (p->pipe2 ? p->split2 : 1) * 16, 256);
   p->ws_const = off; off = round_up(off + (int64_t)ndm * p->nw * (int64_t)sizeof(SnrConst), 256);
   p->ws_hoff = off; off = round_up(off + (p->interm == TX_INTERM_F16 ? (int64_t)(nsub + 1) * 4 : 0), 256);
   p->ws_bytes = off;

@@ -37,6 +37,15 @@ constexpr uint32_t kWaitPolls = 1u << 22;
 // A stage-2 tile is nw2 32-bit words of uint16 pairs (two outputs each):
 // 512 words for groups of up to 16 fine DMs (16 warps), 256 beyond.
 constexpr int kStage2MaxGroup = 32;    // one warp per fine DM of a group
+// The pipelined 16-bit stage 2: stages of sub-band chunks in flight, producer
+// warps, and the largest group it takes (consumer warps = group x warps per DM <= 28).
+constexpr int kPipeStages2 = 3;
+constexpr int kPipeProd2 = 4;
+constexpr int kPipeMaxGroup2 = 16;
+// shared-memory bytes of the pipelined stage 2 for `sc` sub-bands of `sww` words per stage
+constexpr int64_t stage2_pipe_smem(int sc, int sww) {
+  return (int64_t)kPipeStages2 * (2 * (int64_t)sc * sww + (int64_t)(kPipeMaxGroup2 + 1) * ((sc + 3) & ~3)) * 4;
+}
 
 // ---- matched filter ---------------------------------------------------------
 constexpr int kBoxTile = 2048;         // outputs per block of the boxcar kernel
@@ -72,6 +81,7 @@ struct DevicePlan {
   int32_t* widths = nullptr;     // [nw]
   Stage1Item* items1 = nullptr;  // [n_items1]
   int32_t* tab1 = nullptr;       // stage-1 offset tables of the item groups
+  int32_t* tab2 = nullptr;       // pipelined stage 2: offset tables per (coarse group, sub-band chunk)
 };
 
 void set_error(const char* fmt, ...);
@@ -115,6 +125,7 @@ struct tx_plan {
   int32_t span2_max = 0;          // max stage-2 delay spread within a group
   int32_t nw2 = 512;              // stage-2 tile words (2 * nw2 outputs)
   int32_t split2 = 2;             // stage-2 warps per fine DM (uint16 path)
+  int32_t pipe2 = 0;              // 16-bit stage 2 runs as the barrier-free pipeline (groups <= 16)
   int32_t ntile2 = 0;             // stage-2 tiles over the series
   int32_t sww2 = 0;               // stage-2 staged words per sub-band (uint16 path)
   int32_t sw2_i32 = 0;            // stage-2 staged elements per sub-band (int32 path)
@@ -129,6 +140,12 @@ struct tx_plan {
   // its residue mod 16 (every block when T is a multiple of 16)
   std::vector<int32_t> tab1;
   int32_t tab1_phase = 0;
+  // pipelined stage 2, per (coarse group k, sub-band chunk): rows g < group of
+  // SCq = (nsub_chunk2 + 3) & ~3 words, word ss = the element offset of fine
+  // DM kG + g's pairs in sub-band s = chunk * nsub_chunk2 + ss from the start
+  // of that sub-band's staged row, then one row of those starts relative to
+  // the tile start (multiples of 8: the 16-byte alignment of bulk copies)
+  std::vector<int32_t> tab2;
 
   // ---- workspace carve-up (bytes) -------------------------------------------
   int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_hoff = 0, ws_bytes = 0;

@@ -123,9 +123,15 @@ def test_too_many_channels_per_subband_unsupported(tx):
 def test_tile_knobs_reported(tx):
     wl = synth.tiny_workload(nchan=64, nsub=4, ndm=40)
     auto = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 4, wl.widths, wl.nsamp, group=4)
-    assert auto.tile_q1 == 256 and auto.tile_split2 == 8          # groups of <= 4 DMs: 8 warps each
+    # groups of up to 16 DMs run the pipelined stage 2: 4, 2 or 1 consumer warps per DM, at most 28 in all
+    assert auto.tile_q1 == 256 and auto.tile_split2 == 4
     p = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 4, wl.widths, wl.nsamp, group=4, tile_q1=64, tile_split2=1)
-    assert p.tile_q1 == 64 and p.tile_split2 == 1
+    assert p.tile_q1 == 64 and p.tile_split2 == 4
+    for g, sp in ((7, 4), (8, 2), (14, 2), (16, 1)):
+        assert tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 4, wl.widths, wl.nsamp, group=g).tile_split2 == sp
+    # larger groups: the other kernel, whose warps per DM the description sets
+    big = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, 4, wl.widths, wl.nsamp, group=32, tile_split2=1)
+    assert big.tile_split2 == 1
     # the tile shapes change neither the tables nor the overlap
     assert p.overlap == auto.overlap
     for k in ("d1", "d2", "coarse_of_fine", "coarse_dm"):

@@ -354,12 +354,16 @@ def test_boxcar_width_sets(tx, widths, output):
 
 
 @pytest.mark.parametrize("q1", [32, 64, 128, 256])
-@pytest.mark.parametrize("split", [1, 2, 4, 8])
-def test_tile_shapes_do_not_change_results(tx, q1, split):
-    """Every stage-1 tile length and stage-2 warp split gives the oracle's series."""
-    wl = synth.tiny_workload(nchan=128, nsub=16, ndm=64, nsamp=5000, dm_max=400.0, tsamp=128e-6, group=4)
+@pytest.mark.parametrize("group,split,want", [
+    (4, 0, 4), (8, 0, 2), (16, 0, 1),          # the pipelined stage 2: 4, 2, 1 consumer warps per DM
+    (17, 1, 1), (32, 1, 1),                    # larger groups: the other kernel, split as asked
+])
+def test_tile_shapes_do_not_change_results(tx, q1, group, split, want):
+    """Every stage-1 tile length, both stage-2 kernels and each of their warp
+    splits give the oracle's series."""
+    wl = synth.tiny_workload(nchan=128, nsub=16, ndm=64, nsamp=5000, dm_max=400.0, tsamp=128e-6, group=group)
     plan = make_plan(tx, wl, output="series", tile_q1=q1, tile_split2=split)
-    assert (plan.tile_q1, plan.tile_split2) == (q1, split)
+    assert (plan.tile_q1, plan.tile_split2) == (q1, want)
     op = oracle_plan(wl)
     X = rand_stream(wl.nchan, plan.overlap + wl.nsamp, seed=77)
     (out, _, _), = run_blocks(tx, plan, X)[0]

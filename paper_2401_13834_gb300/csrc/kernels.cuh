@@ -1187,7 +1187,7 @@ struct PipeCursor {
 };
 
 template <int VW, typename Src, bool HALF = false>
-__global__ void __launch_bounds__(VW == 16 ? 640 : 1024, 1)
+__global__ void __launch_bounds__(VW == 16 ? 704 : 1024, 1)
 k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem,
               int nunits, int slot, int tabw) {
   extern __shared__ __align__(16) uint32_t smp[];
@@ -1268,15 +1268,29 @@ k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __
       // odd copy: od[ss][i] = (P[2i + 1], P[2i + 2]) relative to the staged row start
       const uint32_t* ev = smp + (size_t)bp * stage_words;
       uint32_t* od = smp + (size_t)bp * stage_words + slot;
+      // (four 16-byte groups per lane at a time, their loads issued before their stores)
       for (int ss = pw; ss < pc.ns; ss += kPipeProc) {
         const uint32_t* r = ev + (size_t)ss * a.SWW;
         uint32_t* o = od + (size_t)ss * a.SWW;
-        for (int j = 4 * lane; j < a.SWW - 4; j += 128) {
-          const uint4 x = *reinterpret_cast<const uint4*>(r + j);
-          const uint32_t y = r[j + 4];
-          *reinterpret_cast<uint4*>(o + j) =
-              make_uint4(__funnelshift_r(x.x, x.y, 16), __funnelshift_r(x.y, x.z, 16), __funnelshift_r(x.z, x.w, 16),
-                         __funnelshift_r(x.w, y, 16));
+        for (int j0 = 4 * lane; j0 < a.SWW - 4; j0 += 512) {
+          uint4 x[4];
+          uint32_t y[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int j = j0 + 128 * i;
+            if (j < a.SWW - 4) {
+              x[i] = *reinterpret_cast<const uint4*>(r + j);
+              y[i] = r[j + 4];
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int j = j0 + 128 * i;
+            if (j < a.SWW - 4)
+              *reinterpret_cast<uint4*>(o + j) =
+                  make_uint4(__funnelshift_r(x[i].x, x[i].y, 16), __funnelshift_r(x[i].y, x[i].z, 16),
+                             __funnelshift_r(x[i].z, x[i].w, 16), __funnelshift_r(x[i].w, y[i], 16));
+          }
         }
       }
       mbar_arrive(&ready[bp]);

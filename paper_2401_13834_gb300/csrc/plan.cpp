@@ -210,12 +210,14 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->nw2 = split == 1 ? 256 : 512;
   // 16-bit intermediates with groups of up to 16 fine DMs: the pipelined stage 2,
   // 1024-output tiles, consumer warps per fine DM the largest of 4, 2, 1 that
-  // keeps group x warps <= 28 (the desc's tile_split2 applies to the other kernel)
+  // keeps group x warps + producer warps <= 32 (the desc's tile_split2 applies
+  // to the other kernel)
   const bool is16 = d->interm == TX_INTERM_U16 || d->interm == TX_INTERM_F16;
   const int32_t sww_pipe = (int32_t)round_up(512 + (span2 + 7 + 2) / 2 + 6, 4);
   p->pipe2 = is16 && G <= kPipeMaxGroup2 && stage2_pipe_smem(1, sww_pipe) <= kSmemMax - 1024;
   if (p->pipe2) {
-    p->split2 = G * 4 <= 28 ? 4 : G * 2 <= 28 ? 2 : 1;
+    const int cmax = 32 - kPipeProd2;   // consumer warps beside the producer warps
+    p->split2 = G * 4 <= cmax ? 4 : G * 2 <= cmax ? 2 : 1;
     p->nw2 = 512;
   }
   const int64_t tt2 = 2 * (int64_t)p->nw2;

@@ -16,5 +16,9 @@ Modules:
              plane and candidates (Sec. 2.5), running statistics.
   losses  -- the closed-form and semi-analytic S/N-loss expressions: Eqs. 3-4,
              6-8, 12-15 and Appendix A.
+  normalise -- per-channel normalisation of each block (Sec. 2.1): unit
+             variance or inverse-variance weights, as float32 values.
+  plans   -- de-dispersion plans with downsampling (Sec. 2.3).
+  cluster -- DBSCAN of the candidates (Sec. 2.5).
 """
-from . import dedisp, losses  # noqa: F401
+from . import dedisp, losses, normalise  # noqa: F401

@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--output", choices=["cands", "plane", "cube"], default="cands")
     ap.add_argument("--layout", choices=["tf", "ft"], default="tf")
     ap.add_argument("--interm", choices=["u16", "i32", "f16"], default="u16")
+    ap.add_argument("--norm", choices=["none", "unit", "invvar"], default="none",
+                    help="per-channel normalisation (the float path, FP32 intermediates)")
     ap.add_argument("--gamma", type=float, default=7.0)
     ap.add_argument("--max-cands", type=int, default=1 << 24)
     ap.add_argument("--nsamp", type=int, default=0, help="override T (new samples per block), e.g. for profiling")
@@ -286,7 +288,7 @@ def block_hbm_bytes(plan, ncand_avg):
     d2 = t["d2"]
     G = plan.group
     m = plan.nchan // plan.nsub
-    width = {"u16": 2, "f16": 2, "i32": 4}[plan.interm]
+    width = {"u16": 2, "f16": 2, "i32": 4, "f32": 4}[plan.interm]
     entries = 0
     for k in range(plan.ncoarse):
         blk = d2[k * G:min((k + 1) * G, plan.ndm)]
@@ -449,7 +451,8 @@ def workload_config(wl, group, overlap, args, kind="ours"):
         "tsamp_us": wl.tsamp_s * 1e6, "ndm": wl.ndm, "dm_max": float(wl.dms.max()), "nsub": wl.nsub,
         "group": group, "nsamp_per_block": wl.nsamp, "overlap": overlap,
         "widths": [int(w) for w in wl.widths], "output": args.output, "layout": args.layout,
-        "interm": args.interm, "snr_threshold": args.gamma,
+        "interm": args.interm if getattr(args, "norm", "none") == "none" else "f32",
+        "norm": getattr(args, "norm", "none"), "snr_threshold": args.gamma,
         "l2": "inputs larger than L2: each block is nchan*T bytes (268 MB for 4096x65536), two distinct blocks alternate",
         "beams_per_gpu": 1,
     }
@@ -478,7 +481,8 @@ def run_ours(args):
 
     wl = load_workload(args)
     plan = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, layout=args.layout,
-                   interm=args.interm, output=args.output, snr_threshold=args.gamma, max_cands=args.max_cands)
+                   interm=args.interm if args.norm == "none" else "f32", output=args.output, snr_threshold=args.gamma,
+                   max_cands=args.max_cands, norm=args.norm)
     L, T = plan.overlap, plan.nsamp
     nb = 2
     X = make_stream(wl, L, nb, seed=rank)
@@ -624,7 +628,7 @@ def run_ours(args):
         del out, ncand
         torch.cuda.empty_cache()
         pc = tx.Plan(wl.freqs_mhz, wl.tsamp_s, wl.dms, wl.nsub, wl.widths, wl.nsamp, layout=args.layout,
-                     interm=args.interm, output="cube")
+                     interm=args.interm if args.norm == "none" else "f32", output="cube", norm=args.norm)
         bc = tx.Beam(pc)
         bc.prime(torch.from_numpy(tail_h).to(dev))
         oc, _ = pc.alloc_out(dev)
@@ -705,7 +709,9 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32 sums, f32 S/N", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8->int32 sums, f32 S/N" if args.norm == "none" else "u8->f32 normalised, f32 sums, f32 S/N",
+            "data": "synthetic",
             "config": dict(workload_config(wl, plan.group, L, args), parallelism=f"replicas{world}"),
             "p50_block_ms": latency["p50_ms"], "p99_block_ms": latency["p99_ms"], "latency": latency,
             "real_time_factor": (T * wl.tsamp_s) / (elapsed_ms / args.steps / 1e3),
@@ -969,7 +975,8 @@ def run_batched(args):
             "config": {"workload": f"batched-{len(wls)}-beams", "beams": len(wls), "shapes": shapes,
                        "band_mhz": [856.0, 1712.0], "tsamp_us": 153.12, "dm_max": 3000.0,
                        "widths": [int(w) for w in wls[0].widths], "output": args.output, "layout": args.layout,
-                       "interm": args.interm, "snr_threshold": args.gamma, "autotuned_beams": tuned,
+                       "interm": args.interm if getattr(args, "norm", "none") == "none" else "f32",
+        "norm": getattr(args, "norm", "none"), "snr_threshold": args.gamma, "autotuned_beams": tuned,
                        "nsub_per_beam": [p.nsub for p in plans], "group_per_beam": [p.group for p in plans],
                        "workspace_budget_gib": args.ws_budget_gb, "waves": batch.nwaves,
                        "launches_per_step": batch.nlaunches, "graph": True,

@@ -78,18 +78,33 @@ enum tx_layout { TX_LAYOUT_FT = 0,   /* block is channel-major  uint8 [nchan][T]
 enum tx_interm { TX_INTERM_U16 = 0,  /* stage-1 sums stored as uint16 (exact for
                                         nchan/nsub <= 257)                          */
                  TX_INTERM_I32 = 1,  /* stored as int32                              */
-                 TX_INTERM_F16 = 2 };/* stored as FP16 after subtracting an integer
+                 TX_INTERM_F16 = 2,  /* stored as FP16 after subtracting an integer
                                         offset per sub-band (the sum of its channels'
                                         rounded block means), rounded to nearest even
                                         and saturated at +-65504; stage 2 sums the
                                         halves in FP32 and adds the offsets back.
                                         Exact while |sum - offset| <= 2048.         */
+                 TX_INTERM_F32 = 3 };/* the float path (normalised data, tx_norm):
+                                        FP32 sums stored as FP32                     */
+/* Per-channel normalisation (Sec. 2.1): each block is brought to zero mean and
+   unit variance per channel as it arrives, x' = (x - mu_c) / sigma_c, with mu_c
+   and sigma_c the mean and population standard deviation of channel c over the
+   block's T new samples (exact integer sums); TX_NORM_INVVAR weights by the
+   reciprocal of the variance instead, x' = (x - mu_c) / sigma_c^2, which
+   down-weights noisy channels further. A channel with sigma_c = 0 gets weight
+   0. The carried tail keeps the normalisation of the block it arrived with.
+   x' is computed in FP32 as (float(x) - float(mu_c)) * float(w_c), w_c = 1 /
+   sigma_c or 1 / sigma_c^2 rounded from double, and kept in a float32 buffer. */
+enum tx_norm   { TX_NORM_NONE   = 0,  /* raw uint8, equal weights: the integer path  */
+                 TX_NORM_UNIT   = 1,  /* zero mean, unit variance per channel        */
+                 TX_NORM_INVVAR = 2 };/* zero mean, weight 1 / variance              */
 enum tx_output { TX_OUT_CANDS  = 0,  /* tx_cand records, S/N >= snr_threshold        */
                  TX_OUT_PLANE  = 1,  /* float32 [ndm][T] best S/N, then uint8 [ndm][T]
                                         index of the best width                      */
                  TX_OUT_CUBE   = 2,  /* float32 [ndm][nwidth][T]                     */
                  TX_OUT_SERIES = 3 };/* int32 [ndm][T + W_max - 1] de-dispersed series
-                                        (no matched filter)                          */
+                                        (no matched filter); float32 on the float
+                                        path                                         */
 enum tx_stats  { TX_STATS_BLOCK   = 0,  /* mu, sigma of this block                   */
                  TX_STATS_RUNNING = 1 };/* mu, var <- (1-l) prev + l block; the first
                                           block after create/reset initialises      */
@@ -121,7 +136,14 @@ typedef struct tx_plan_desc {
   int32_t        tile_split2;    /* stage-2 warps per fine DM: 1 (tiles of 512
                                     outputs) or 2, 4, 8 (tiles of 1024), with
                                     min(group, 32) * tile_split2 <= 32; 0 = 8, 4, 2
-                                    or 1 for groups of <= 4, 8, 16 or more        */
+                                    or 1 for groups of <= 4, 8, 16 or more; used by
+                                    groups of more than 16 DMs (smaller groups run
+                                    the pipelined stage 2, which sizes itself)   */
+  int32_t        norm;           /* enum tx_norm; TX_NORM_NONE unless interm is
+                                    TX_INTERM_F32, which needs another mode. The
+                                    float path runs single beams (tx_execute,
+                                    tx_execute_host, pipelines); it is not taken by
+                                    compact beams, batches or tx_dedisperse_noalloc */
 } tx_plan_desc;
 
 typedef struct tx_plan_info {

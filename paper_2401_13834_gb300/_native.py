@@ -10,7 +10,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_lib", "libtransientx_gb300.so")
 
 LAYOUTS = {"ft": 0, "tf": 1}
-INTERMS = {"u16": 0, "i32": 1, "f16": 2}
+INTERMS = {"u16": 0, "i32": 1, "f16": 2, "f32": 3}
+NORMS = {"none": 0, "unit": 1, "invvar": 2}
 OUTPUTS = {"cands": 0, "plane": 1, "cube": 2, "series": 3}
 STATS = {"block": 0, "running": 1}
 
@@ -38,7 +39,7 @@ class _Desc(C.Structure):
         ("nwidth", C.c_int32), ("widths", C.POINTER(C.c_int32)), ("nsamp", C.c_int64),
         ("layout", C.c_int32), ("interm", C.c_int32), ("output", C.c_int32),
         ("snr_threshold", C.c_float), ("max_cands", C.c_int64), ("stats", C.c_int32),
-        ("stats_lambda", C.c_double), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32),
+        ("stats_lambda", C.c_double), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32), ("norm", C.c_int32),
     ]
 
 
@@ -176,7 +177,7 @@ def geometric_widths(ratio: float, wmax: int) -> np.ndarray:
 
 
 def _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output, snr_threshold,
-               max_cands, stats, stats_lambda, tile_q1, tile_split2):
+               max_cands, stats, stats_lambda, tile_q1, tile_split2, norm="none"):
     """A tx_plan_desc over arrays kept alive in `keep` (a dict)."""
     keep["freqs"] = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
     keep["dms"] = np.ascontiguousarray(dms, dtype=np.float64)
@@ -201,6 +202,7 @@ def _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout
     d.stats_lambda = float(stats_lambda)
     d.tile_q1 = int(tile_q1)
     d.tile_split2 = int(tile_split2)
+    d.norm = NORMS[norm]
     return d
 
 
@@ -212,6 +214,7 @@ class Plan:
         """A Plan over a handle that `owner` holds (and frees): a segment of a downsampled plan."""
         self = cls.__new__(cls)
         self._owner = owner
+        self.norm = "none"
         self.freqs = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
         self.dms = np.ascontiguousarray(dms, dtype=np.float64)
         self.widths = np.ascontiguousarray(widths, dtype=np.int32)
@@ -231,10 +234,13 @@ class Plan:
 
     def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group=0, layout="ft", interm="u16",
                  output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25,
-                 tile_q1=0, tile_split2=0):
+                 tile_q1=0, tile_split2=0, norm="none"):
+        if norm != "none" and interm == "u16":
+            interm = "f32"                     # a normalisation runs the float path
         keep = {}
         d = _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output,
-                       snr_threshold, max_cands, stats, stats_lambda, tile_q1, tile_split2)
+                       snr_threshold, max_cands, stats, stats_lambda, tile_q1, tile_split2, norm)
+        self.norm = norm
         self.freqs, self.dms, self.widths = keep["freqs"], keep["dms"], keep["widths"]
         self.layout, self.interm, self.output, self.stats = layout, interm, output, stats
         self.snr_threshold = float(snr_threshold)
@@ -523,7 +529,8 @@ def cube_view(plan: Plan, out):
 
 def series_view(plan: Plan, out):
     import torch
-    return out.view(torch.int32).view(plan.ndm, plan.series_len)
+    dt = torch.float32 if plan.interm == "f32" else torch.int32   # float series on the float path
+    return out.view(dt).view(plan.ndm, plan.series_len)
 
 
 def dedisperse_noalloc(plan: Plan, x, ld: int, series, stream=None):

@@ -503,7 +503,7 @@ int32_t tx_batch_create(int32_t n, const tx_plan* const* plans, tx_beam* const* 
     if (!p || !b) { set_error("null plan or beam at %d", i); return TX_ERR_INVALID_ARG; }
     if (b->plan != p) { set_error("beam %d was created for another plan", i); return TX_ERR_INVALID_ARG; }
     if (b->device != dev) { set_error("beam %d lives on device %d, current device is %d", i, b->device, dev); return TX_ERR_INVALID_ARG; }
-    if (p->interm == TX_INTERM_I32) { set_error("batched execute needs 16-bit intermediates (beam %d)", i); return TX_ERR_UNSUPPORTED; }
+    if (p->interm == TX_INTERM_I32 || p->interm == TX_INTERM_F32) { set_error("batched execute needs 16-bit intermediates (beam %d)", i); return TX_ERR_UNSUPPORTED; }
     for (int j = 0; j < i; ++j)
       if (beams[j] == b) { set_error("beam %d appears twice in the batch", i); return TX_ERR_INVALID_ARG; }
     int rc = tx_upload_plan(p);

@@ -181,15 +181,16 @@ int copy_tail(const tx_plan* p, const tx_beam* b, uint8_t* host, bool to_host) {
   }
   const int64_t a = mod(b->head - L, R);
   const int64_t first = std::min(L, R - a);
+  const size_t e = (size_t)p->esz;   // bytes per sample of the buffer (normalised floats on the float path)
   if (to_host) {
-    TX_CUDA(cudaMemcpy2D(host, (size_t)L, b->ring + a, (size_t)R, (size_t)first, (size_t)p->nchan, cudaMemcpyDeviceToHost));
+    TX_CUDA(cudaMemcpy2D(host, L * e, b->ring + a * e, R * e, first * e, (size_t)p->nchan, cudaMemcpyDeviceToHost));
     if (first < L)
-      TX_CUDA(cudaMemcpy2D(host + first, (size_t)L, b->ring, (size_t)R, (size_t)(L - first), (size_t)p->nchan,
+      TX_CUDA(cudaMemcpy2D(host + first * e, L * e, b->ring, R * e, (L - first) * e, (size_t)p->nchan,
                            cudaMemcpyDeviceToHost));
   } else {
-    TX_CUDA(cudaMemcpy2D(b->ring + a, (size_t)R, host, (size_t)L, (size_t)first, (size_t)p->nchan, cudaMemcpyHostToDevice));
+    TX_CUDA(cudaMemcpy2D(b->ring + a * e, R * e, host, L * e, first * e, (size_t)p->nchan, cudaMemcpyHostToDevice));
     if (first < L)
-      TX_CUDA(cudaMemcpy2D(b->ring, (size_t)R, host + first, (size_t)L, (size_t)(L - first), (size_t)p->nchan,
+      TX_CUDA(cudaMemcpy2D(b->ring, R * e, host + first * e, L * e, (L - first) * e, (size_t)p->nchan,
                            cudaMemcpyHostToDevice));
   }
   return TX_OK;
@@ -236,13 +237,15 @@ int beam_create(const tx_plan* p, tx_beam** out, int compact) {
   *out = nullptr;
   int rc = tx_upload_plan(p);
   if (rc) return rc;
+  if (compact && p->norm != TX_NORM_NONE) { set_error("the float path (a normalisation) runs full beams only"); return TX_ERR_UNSUPPORTED; }
   tx_beam* b = new (std::nothrow) tx_beam();
   if (!b) { set_error("out of host memory"); return TX_ERR_OOM; }
   b->plan = p;
   b->compact = compact;
   cudaGetDevice(&b->device);
   cudaError_t e = compact ? cudaMalloc((void**)&b->tail, std::max<size_t>((size_t)p->nchan * p->tail_pitch, 16))
-                          : cudaMalloc((void**)&b->ring, (size_t)p->nchan * p->R);
+                          : cudaMalloc((void**)&b->ring, (size_t)p->nchan * p->R * p->esz);
+  if (e == cudaSuccess && p->norm != TX_NORM_NONE) e = cudaMalloc((void**)&b->chan, (size_t)p->nchan * 24);
   // the running statistics, then the beam's count of waits its kernels gave up
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->run, (size_t)p->ndm * 2 * sizeof(double) + 16);
   if (e == cudaSuccess) b->fail = reinterpret_cast<int32_t*>(b->run + (size_t)p->ndm * 2);
@@ -276,7 +279,7 @@ int32_t tx_beam_reset(const tx_plan* p, tx_beam* b, void* stream) {
   if (b->compact)
     TX_CUDA(cudaMemsetAsync(b->tail, 0, (size_t)p->nchan * p->tail_pitch, st));
   else
-    TX_CUDA(cudaMemsetAsync(b->ring, 0, (size_t)p->nchan * p->R, st));
+    TX_CUDA(cudaMemsetAsync(b->ring, 0, (size_t)p->nchan * p->R * p->esz, st));
   TX_CUDA(cudaMemsetAsync(b->run, 0, (size_t)p->ndm * 2 * sizeof(double) + 16, st));
   k_fill_run<<<(p->ndm + 255) / 256, 256, 0, st>>>(b->run, p->ndm);
   TX_CUDA(cudaGetLastError());
@@ -304,6 +307,7 @@ int32_t tx_beam_prime(const tx_plan* p, tx_beam* b, const uint8_t* d_tail, void*
     }
     return TX_OK;
   }
+  if (p->norm != TX_NORM_NONE) return float_prime(p, b, d_tail, stream);
   // the tail sits in the L positions before the next block
   return ingest(p, d_tail, p->L, b->ring, b->head - p->L, (cudaStream_t)stream);
 }
@@ -324,7 +328,7 @@ int32_t tx_beam_export(const tx_plan* p, const tx_beam* b, void* h_dst, int64_t 
   std::memcpy(h, hdr, sizeof(hdr));
   TX_CUDA(cudaDeviceSynchronize());
   if ((rc = copy_tail(p, b, h + 64, true))) return rc;
-  TX_CUDA(cudaMemcpy(h + 64 + (size_t)p->nchan * p->L, b->run, (size_t)p->ndm * 16, cudaMemcpyDeviceToHost));
+  TX_CUDA(cudaMemcpy(h + 64 + (size_t)p->nchan * p->L * p->esz, b->run, (size_t)p->ndm * 16, cudaMemcpyDeviceToHost));
   return TX_OK;
 }
 
@@ -338,7 +342,7 @@ int32_t tx_beam_import(const tx_plan* p, tx_beam* b, const void* h_src, int64_t 
   if (hdr[0] != 0x54584245414d32LL || hdr[1] != p->nchan || hdr[2] != p->L) { set_error("export does not match this plan"); return TX_ERR_INVALID_ARG; }
   TX_CUDA(cudaDeviceSynchronize());
   if ((rc = copy_tail(p, b, const_cast<uint8_t*>(h + 64), false))) return rc;
-  TX_CUDA(cudaMemcpy(b->run, h + 64 + (size_t)p->nchan * p->L, (size_t)p->ndm * 16, cudaMemcpyHostToDevice));
+  TX_CUDA(cudaMemcpy(b->run, h + 64 + (size_t)p->nchan * p->L * p->esz, (size_t)p->ndm * 16, cudaMemcpyHostToDevice));
   TX_CUDA(cudaMemset(b->fail, 0, sizeof(int32_t)));   // an imported state is a valid one
   b->nblocks = hdr[3];
   return TX_OK;
@@ -363,6 +367,7 @@ void tx_beam_destroy(tx_beam* b) {
   cudaFree(b->ring);
   cudaFree(b->tail);
   cudaFree(b->run);
+  cudaFree(b->chan);
   cudaSetDevice(prev);
   delete b;
 }
@@ -395,6 +400,11 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
     return TX_ERR_INVALID_ARG;
   }
   if ((rc = tx_upload_plan(p))) return rc;
+  if (p->norm != TX_NORM_NONE) {   // the float path: normalisation, FP32 de-dispersion and boxcar
+    rc = float_execute(p, b, d_block, d_out, d_ncand, d_workspace, stream, reinterpret_cast<void* const*>(ev));
+    if (rc == TX_OK) ++b->nblocks;
+    return rc;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   TX_MARK(0);
 

@@ -101,7 +101,13 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   if (d->nsamp < 1) { set_error("nsamp must be >= 1"); return TX_ERR_INVALID_ARG; }
   if (d->group < 0) { set_error("group must be >= 0"); return TX_ERR_INVALID_ARG; }
   if (d->layout != TX_LAYOUT_FT && d->layout != TX_LAYOUT_TF) { set_error("bad layout"); return TX_ERR_INVALID_ARG; }
-  if (d->interm != TX_INTERM_U16 && d->interm != TX_INTERM_I32 && d->interm != TX_INTERM_F16) { set_error("bad interm"); return TX_ERR_INVALID_ARG; }
+  if (d->interm != TX_INTERM_U16 && d->interm != TX_INTERM_I32 && d->interm != TX_INTERM_F16 && d->interm != TX_INTERM_F32) { set_error("bad interm"); return TX_ERR_INVALID_ARG; }
+  if (d->norm != TX_NORM_NONE && d->norm != TX_NORM_UNIT && d->norm != TX_NORM_INVVAR) { set_error("bad norm"); return TX_ERR_INVALID_ARG; }
+  if ((d->norm != TX_NORM_NONE) != (d->interm == TX_INTERM_F32)) {
+    set_error("the float path pairs a normalisation (norm) with float32 intermediates (TX_INTERM_F32)");
+    return TX_ERR_INVALID_ARG;
+  }
+  if (d->norm != TX_NORM_NONE && d->ndm > 65535) { set_error("the float path takes at most 65535 DM trials"); return TX_ERR_UNSUPPORTED; }
   if (d->output < TX_OUT_CANDS || d->output > TX_OUT_SERIES) { set_error("bad output mode"); return TX_ERR_INVALID_ARG; }
   if (d->stats != TX_STATS_BLOCK && d->stats != TX_STATS_RUNNING) { set_error("bad stats mode"); return TX_ERR_INVALID_ARG; }
   if (d->stats == TX_STATS_RUNNING && !(d->stats_lambda > 0.0 && d->stats_lambda <= 1.0)) { set_error("stats_lambda must be in (0, 1]"); return TX_ERR_INVALID_ARG; }
@@ -111,6 +117,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->nchan = d->nchan; p->nsub = d->nsub; p->m = m; p->ndm = d->ndm; p->nw = d->nwidth;
   p->T = d->nsamp; p->layout = d->layout; p->interm = d->interm; p->output = d->output;
   p->stats = d->stats; p->gamma = d->snr_threshold; p->max_cands = d->max_cands;
+  p->norm = d->norm;
   p->lambda = d->stats == TX_STATS_RUNNING ? d->stats_lambda : 1.0;
   p->tsamp = d->tsamp_s;
   p->freq.assign(d->freq_mhz, d->freq_mhz + d->nchan);
@@ -263,6 +270,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   }
   p->Dp = round_up(p->Td + 8, 8);
   p->ntile3 = (int32_t)((p->T + kBoxTile - 1) / kBoxTile);
+  p->ntile2f = (int32_t)((p->Td + kFloatTile - 1) / kFloatTile);
 
   // ---- stage-1 work list ----------------------------------------------------
   // quarter length q1: the largest of 256/128/64/32 whose staged words, raw
@@ -333,13 +341,17 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->head0 = round_up(p->L, 64) % p->R;
 
   // ---- sizes ---------------------------------------------------------------------
-  const int64_t psz = p->interm == TX_INTERM_I32 ? 4 : 2;
+  const bool fpath = p->interm == TX_INTERM_F32;
+  const int64_t psz = p->interm == TX_INTERM_I32 || fpath ? 4 : 2;
   int64_t off = 0;
   p->ws_P = off; off = round_up(off + (int64_t)nk * nsub * p->Pp * psz, 256);
   p->ws_D = off; off = round_up(off + (p->output == TX_OUT_SERIES ? 0 : (int64_t)ndm * p->Dp * 4), 256);
-  p->ws_part = off; off = round_up(off + (int64_t)ndm * p->ntile2 * (p->pipe2 ? p->split2 : 1) * 16, 256);
-  p->ws_const = off; off = round_up(off + (int64_t)ndm * p->nw * (int64_t)sizeof(SnrConst), 256);
-  p->ws_hoff = off; off = round_up(off + (p->interm == TX_INTERM_F16 ? (int64_t)(nsub + 1) * 4 : 0), 256);
+  const int64_t parts = fpath ? (int64_t)p->ntile2f : (int64_t)p->ntile2 * (p->pipe2 ? p->split2 : 1);
+  p->ws_part = off; off = round_up(off + (int64_t)ndm * parts * 16, 256);
+  // S/N constants per (DM, width); the float path keeps (mu, sigma) per DM in double
+  p->ws_const = off; off = round_up(off + std::max<int64_t>((int64_t)ndm * p->nw * (int64_t)sizeof(SnrConst), fpath ? (int64_t)ndm * 16 : 0), 256);
+  // half intermediates: per-sub-band offsets; float path: per-channel sums (2 x u64), then (mu, w) as float pairs
+  p->ws_hoff = off; off = round_up(off + (p->interm == TX_INTERM_F16 ? (int64_t)(nsub + 1) * 4 : fpath ? (int64_t)nchan * 24 : 0), 256);
   p->ws_bytes = off;
   switch (p->output) {
     case TX_OUT_CANDS: p->out_bytes = p->max_cands * (int64_t)sizeof(tx_cand); break;
@@ -347,13 +359,14 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
     case TX_OUT_CUBE: p->out_bytes = (int64_t)ndm * p->nw * p->T * 4; break;
     default: p->out_bytes = (int64_t)ndm * p->Td * 4; break;
   }
-  p->beam_bytes = (int64_t)nchan * p->R + (int64_t)ndm * 16 + 16;
+  p->esz = fpath ? 4 : 1;   // the beam's buffer holds normalised float32 samples on the float path
+  p->beam_bytes = (int64_t)nchan * p->R * p->esz + (int64_t)ndm * 16 + 16;
   p->tail_pad = (16 - p->L % 16) % 16;
   p->tail_pitch = p->L + p->tail_pad;
   p->ws_ring = p->ws_bytes;
   p->ws_bytes_compact = round_up(p->ws_ring + (int64_t)nchan * p->R, 256);
   p->compact_beam_bytes = (int64_t)nchan * p->tail_pitch + (int64_t)ndm * 16 + 16;
-  p->export_bytes = 64 + (int64_t)nchan * p->L + (int64_t)ndm * 16;
+  p->export_bytes = 64 + (int64_t)nchan * p->L * p->esz + (int64_t)ndm * 16;
   return TX_OK;
 }
 

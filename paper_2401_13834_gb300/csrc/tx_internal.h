@@ -53,6 +53,9 @@ constexpr int kBoxThreads = 256;
 constexpr int kMaxWidths = 32;
 constexpr int kMaxWidth = 4096;
 
+// ---- the float path (normalised data) -------------------------------------------
+constexpr int kFloatTile = 256;        // outputs per block of its stage 2 (one thread each)
+
 // Stage-1 work item: sub-band s, coarse DMs [kb, ke), times [tau0, tau0 + 4 q1),
 // span = max over the sub-band's channels of d1[ke-1][c] - d1[kb][c]; tab =
 // word offset of the item's precomputed offset table in the plan's tab1
@@ -98,6 +101,8 @@ struct tx_plan {
   int32_t box_vec = 0;            // widths 1, 2, then multiples of 4: the boxcar's 4-output test
   int64_t T = 0;
   int32_t layout = 0, interm = 0, output = 0, stats = 0;
+  int32_t norm = 0;               // enum tx_norm: the float path when not TX_NORM_NONE
+  int32_t esz = 1;                // bytes per sample of a beam's buffer (4 on the float path)
   float gamma = 0.f;
   int64_t max_cands = 0;
   double lambda = 1.0;
@@ -132,6 +137,7 @@ struct tx_plan {
   int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
   int32_t e2w2 = 0;               // words of one stage-2 group's delays in shared memory (rounded to 4)
   int32_t ntile3 = 0;             // boxcar tiles over [0, T)
+  int32_t ntile2f = 0;            // float path: stage-2 tiles of kFloatTile outputs over the series
   std::vector<tx::Stage1Item> items1;
   // stage-1 offset tables, per (s, kb, ke): rows kk < ke - kb of (m + 3) & ~3
   // words, word c = c * staged words + ((tab1_phase + d1[kb][c]) & 15) +
@@ -170,10 +176,17 @@ struct tx_beam {
   int64_t head = 0;               // where the next block lands
   double* run = nullptr;          // [ndm][2] running (mu, var); var < 0 = unset
   int32_t* fail = nullptr;        // waits the beam's kernels gave up (device word after run)
+  uint8_t* chan = nullptr;        // float path: channel sums and (mu, w) of a primed tail [nchan] x 24 bytes
   int64_t nblocks = 0;
 };
 
 // Implemented in kernels.cu.
 int tx_upload_plan(const tx_plan* plan);
+// The float path (floatpath.cu): one block of a beam of a plan with a
+// normalisation; arguments as tx_execute (ev: optional phase events as in
+// tx_execute_timed). prime: normalise a tail of L samples into the beam.
+int float_execute(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_out, int64_t* d_ncand,
+                  void* d_workspace, void* stream, void* const* ev);
+int float_prime(const tx_plan* p, tx_beam* b, const uint8_t* d_tail, void* stream);
 // Waits given up by the batched kernels on the current device (batch.cu).
 int batch_wait_timeouts(int64_t* n);

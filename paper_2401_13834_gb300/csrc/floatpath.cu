@@ -11,8 +11,8 @@
 //   k_stage2_f32    D[d][t]    = sum_s P[k(d)][s][t + d2[d][s]]     (FP32, sub-bands in order),
 //                   with per-tile sums of D and D^2 in double
 //   k_stats_f32     mu_d, sigma_d of D over [0, T) in double (block or running)
-//   k_boxcar_f32    prefix sums of D - mu_d in double per tile, held as float (hi, lo) pairs,
-//                   window sums B_W = C[t + W] - C[t], S/N = B_W / (sigma_d sqrt W), outputs
+//   k_boxcar_f32    compensated (TwoSum) prefix sums of D per tile as float (hi, lo) pairs,
+//                   window sums B_W = C[t + W] - C[t], S/N = (B_W - W mu_d) / (sigma_d sqrt W)
 // Every thread of the de-dispersion stages computes one output by reading its
 // operands through the L1/L2 caches; the float path trades the integer path's
 // packed sums for arithmetic on normalised data.
@@ -145,66 +145,114 @@ __global__ void __launch_bounds__(kThreads) k_norm_ingest(const uint8_t* __restr
 }
 
 // ---- de-dispersion ----------------------------------------------------------------
-// P[k][s][j] for row positions j of this block (absolute time abase[k][s] + j):
-// the sum over the sub-band's channels, in order, of x' at buffer position
-// start + abase + j + d1[k][c] (mod R).
-__global__ void __launch_bounds__(kThreads) k_stage1_f32(const float* __restrict__ ring, int64_t R, int64_t start,
-                                                          const int32_t* __restrict__ d1, const int32_t* __restrict__ abase,
-                                                          int nchan, int m, int nsub, int64_t Pp, float* __restrict__ P) {
-  extern __shared__ int64_t rowpos[];   // [m]: the buffer position of this block's first output per channel
-  const int s = blockIdx.y, k = blockIdx.z;
-  const int64_t j0 = (int64_t)blockIdx.x * kThreads;
-  const int64_t ab = abase[(size_t)k * nsub + s];
-  for (int i = threadIdx.x; i < m; i += kThreads)
-    rowpos[i] = (start + ab + j0 + d1[(size_t)k * nchan + s * m + i]) % R;
-  __syncthreads();
-  const int64_t j = j0 + threadIdx.x;
-  if (j >= Pp) return;
-  float acc = 0.f;
-  const float* base = ring + (int64_t)s * m * R;
-  for (int i = 0; i < m; ++i) {
-    int64_t p = rowpos[i] + threadIdx.x;
-    if (p >= R) p -= R;
-    acc = __fadd_rn(acc, __ldg(base + (int64_t)i * R + p));
-  }
-  P[((size_t)k * nsub + s) * Pp + j] = acc;
-}
+// One block per item (sub-band s, coarse DMs [kb, ke), absolute times
+// [tau0, tau0 + tile)): every channel's window of x' (tile + spread samples
+// from buffer position start + tau0 + d1[kb][c], mod R) is staged in shared
+// memory once, then each warp sums coarse DMs of the item over the
+// sub-band's channels in order, P[k][s][tau0 + j - abase[k][s]] = sum_c
+// S[c][j + d1[k][c] - d1[kb][c]], VW = tile / 32 outputs per lane.
+constexpr int kThreads1 = 1024;   // stage 1: a warp per coarse DM of an item (up to 32)
 
-// D[d][t] = sum over sub-bands, in order, of P[k(d)][s][t + e2[d][s]] for
-// t < Td; the block's sums of D and D^2 over t < T in double to part[d][tile].
-__global__ void __launch_bounds__(kThreads) k_stage2_f32(const float* __restrict__ P, int64_t Pp,
-                                                          const int32_t* __restrict__ e2, int nsub, int G,
-                                                          float* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
-                                                          double2* __restrict__ part, int ntile) {
-  extern __shared__ int32_t erow[];     // [nsub]
-  const int d = blockIdx.y, tile = blockIdx.x;
-  const int k = d / G;
-  for (int i = threadIdx.x; i < nsub; i += kThreads) erow[i] = e2[(size_t)d * nsub + i];
-  __syncthreads();
-  const int64_t t = (int64_t)tile * kFloatTile + threadIdx.x;
-  double s1 = 0.0, s2 = 0.0;
-  if (t < Td) {
-    float acc = 0.f;
-    const float* rows = P + (size_t)k * nsub * Pp + t;
-    for (int s = 0; s < nsub; ++s) acc = __fadd_rn(acc, __ldg(rows + (size_t)s * Pp + erow[s]));
-    D[(size_t)d * Dp + t] = acc;
-    if (t < T) {
-      s1 = (double)acc;
-      s2 = __dmul_rn((double)acc, (double)acc);
+template <int VW>
+__global__ void __launch_bounds__(kThreads1) k_stage1_f32(const float* __restrict__ ring, int64_t R, int64_t start,
+                                                          const Stage1Item* __restrict__ items,
+                                                          const int32_t* __restrict__ d1,
+                                                          const int32_t* __restrict__ abase, int nchan, int m, int nsub,
+                                                          int64_t Pp, int sw, float* __restrict__ P) {
+  extern __shared__ float S[];   // [m][sw]
+  const Stage1Item it = items[blockIdx.x];
+  constexpr int tile = 32 * VW;
+  const int n = tile + it.span;
+  const int c0 = it.s * m;
+  const int32_t* d1b = d1 + (size_t)it.kb * nchan + c0;
+  // the windows: channel c from buffer position p0_c = (start + tau0 + d1[kb][c]) mod R on
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < m; c += kThreads1 / 32) {
+    const int64_t p0 = (start + it.tau0 + d1b[c]) % R;
+    const float* src = ring + (int64_t)(c0 + c) * R;
+    for (int j = lane; j < n; j += 32) {
+      int64_t p = p0 + j;
+      if (p >= R) p -= R;
+      S[c * sw + j] = __ldg(src + p);
     }
   }
-  __shared__ double r1[kThreads / 32], r2[kThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-  }
-  if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = s1; r2[threadIdx.x >> 5] = s2; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) { a += r1[w]; b += r2[w]; }
-    part[(size_t)d * ntile + tile] = make_double2(a, b);
+  for (int kk = warp; kk < it.ke - it.kb; kk += kThreads1 / 32) {
+    const int k = it.kb + kk;
+    const int32_t* d1k = d1 + (size_t)k * nchan + c0;
+    float acc[VW];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) acc[v] = 0.f;
+    for (int c = 0; c < m; ++c) {
+      const float* row = S + c * sw + (__ldg(d1k + c) - __ldg(d1b + c)) + lane;
+#pragma unroll
+      for (int v = 0; v < VW; ++v) acc[v] = __fadd_rn(acc[v], row[32 * v]);
+    }
+    const int64_t rel = (int64_t)it.tau0 - abase[(size_t)k * nsub + it.s];
+    float* prow = P + ((size_t)k * nsub + it.s) * Pp;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      const int64_t j = rel + lane + 32 * v;
+      if (j >= 0 && j < Pp) prow[j] = acc[v];
+    }
+  }
+}
+
+// One block per (tile of 2 NW outputs, coarse group k), one warp per fine DM
+// of the group: sub-band chunks of SC rows of P (the tile plus the group's
+// delay spread) are staged in shared memory, and each warp sums its DM's
+// shifted rows in sub-band order, V = 2 NW / 32 outputs per lane; then the
+// tile's sums of D and D^2 over t < T in double to part[d][tile].
+template <int NW>
+__global__ void __launch_bounds__(kStage2MaxGroup * 32) k_stage2_f32(const float* __restrict__ P, int64_t Pp,
+                                                                      const int32_t* __restrict__ e2, int ndm, int nsub,
+                                                                      int G, int SC, int SW, float* __restrict__ D,
+                                                                      int64_t Dp, int64_t Td, int64_t T,
+                                                                      double2* __restrict__ part, int ntile) {
+  extern __shared__ float Sf[];   // [SC][SW]
+  constexpr int V = 2 * NW / 32;
+  const int tile = blockIdx.x, k = blockIdx.y;
+  const int64_t t0 = (int64_t)tile * 2 * NW;
+  const int dfirst = k * G;
+  const int nd = min(G, ndm - dfirst);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0.f;
+  for (int sb = 0; sb < nsub; sb += SC) {
+    const int ns = min(SC, nsub - sb);
+    for (int i = threadIdx.x; i < ns * SW; i += blockDim.x) {
+      const int ss = i / SW, j = i - ss * SW;
+      const int s = sb + ss;
+      Sf[(size_t)ss * SW + j] = __ldg(P + ((size_t)k * nsub + s) * Pp + t0 + e2[(size_t)dfirst * nsub + s] + j);
+    }
+    __syncthreads();
+    if (warp < nd) {
+      for (int ss = 0; ss < ns; ++ss) {
+        const int s = sb + ss;
+        const int o = e2[(size_t)(dfirst + warp) * nsub + s] - e2[(size_t)dfirst * nsub + s];
+        const float* rw = Sf + (size_t)ss * SW + o + lane;
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = __fadd_rn(acc[v], rw[32 * v]);
+      }
+    }
+    __syncthreads();
+  }
+  if (warp < nd) {
+    const int d = dfirst + warp;
+    double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int64_t t = t0 + lane + 32 * v;
+      if (t < Td) D[(size_t)d * Dp + t] = acc[v];
+      if (t < T) { s1 += (double)acc[v]; s2 += (double)acc[v] * (double)acc[v]; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) part[(size_t)d * ntile + tile] = make_double2(s1, s2);
   }
 }
 
@@ -238,24 +286,39 @@ __global__ void k_stats_f32(const double2* __restrict__ part, int ntile, int ndm
 }
 
 // ---- boxcar (Eq. 5) -------------------------------------------------------------
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (s, c) += x, compensated: s + c carries the running sum to about twice the
+// float precision (TwoSum of s and x, the rounding error added into c).
+__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+  float e;
+  two_sum(s, x, s, e);
+  c = __fadd_rn(c, e);
+}
+
 // One block per unit (fine DM d, tile of kBoxTile outputs). The window
-// v_i = D[t0 + i] - mu_d (double), i < N = n + W_max - 1, is scanned in double
-// into C[i] = v_0 + ... + v_{i-1}; each C is kept as a float pair hi + lo
-// (hi = float(C), lo = float(C - hi)), so that a window sum
+// D[t0 + i], i < N = n + W_max - 1, is turned into compensated prefix sums
+// C[i] = (hi_i, lo_i), hi_i + lo_i = D[t0] + ... + D[t0 + i - 1] to about twice
+// float precision (TwoSum at every add, also across threads and warps), so that
 //   B_W[t] = (hi[t+W] - hi[t]) + (lo[t+W] - lo[t])
-// takes FP32 operations only and keeps about double accuracy: each difference
-// of two floats is rounded once, relative to itself. S/N = B_W / (sigma_d sqrt W)
-// (0 when sigma_d = 0); outputs as the integer path's (cube / plane / candidates).
+// takes FP32 operations only and each difference of two floats is rounded
+// once, relative to itself. Eq. 5 then subtracts W mu_d as a float pair (from
+// double) and scales by 1 / (sigma_d sqrt W): S/N = ((dhi - Wmu_hi) + (dlo -
+// Wmu_lo)) * inv (0 when sigma_d = 0). Outputs as the integer path's.
 __global__ void __launch_bounds__(kThreads) k_boxcar_f32(const float* __restrict__ D, int64_t Dp, int64_t T,
                                                           int ntile3, const double2* __restrict__ ms,
                                                           const int32_t* __restrict__ widths, int nw, int wmax,
                                                           int mode, float gamma, float* __restrict__ outf,
                                                           uint8_t* __restrict__ outw, tx_cand* __restrict__ cands,
                                                           unsigned long long* __restrict__ ncand, int64_t max_cands) {
-  extern __shared__ double C[];   // [kBoxTile + wmax]
-  __shared__ double wsum[kThreads / 32];
+  extern __shared__ float2 H[];   // [kBoxTile + wmax]: the window, then its prefix sums (hi, lo)
+  __shared__ float2 wtot[kThreads / 32];
   __shared__ int32_t sW[kMaxWidths];
-  __shared__ float sInv[kMaxWidths];
+  __shared__ float sInv[kMaxWidths], sMh[kMaxWidths], sMl[kMaxWidths];
   const int unit = blockIdx.x;
   const int d = unit / ntile3, tile = unit - d * ntile3;
   const int64_t t0 = (int64_t)tile * kBoxTile;
@@ -265,33 +328,48 @@ __global__ void __launch_bounds__(kThreads) k_boxcar_f32(const float* __restrict
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < nw) {
     const int W = widths[threadIdx.x];
+    const double wmu = (double)W * m.x;
+    const float h = __double2float_rn(wmu);
     sW[threadIdx.x] = W;
+    sMh[threadIdx.x] = h;
+    sMl[threadIdx.x] = __double2float_rn(wmu - (double)h);
     sInv[threadIdx.x] = m.y > 0.0 ? __double2float_rn(1.0 / (m.y * sqrt((double)W))) : 0.f;
   }
   const float* row = D + (size_t)d * Dp + t0;
-  for (int i = threadIdx.x; i < N; i += kThreads) C[i] = (double)row[i] - m.x;
+  for (int i = threadIdx.x; i < N; i += kThreads) H[i].x = row[i];
   __syncthreads();
-  // exclusive scan of C[0..N] in place (C[N] enters no window sum that is used)
+  // exclusive compensated scan of H[0..N] in place (element N enters no used sum)
   const int E = (N + 1 + kThreads - 1) / kThreads;
   const int beg = threadIdx.x * E, end = min(beg + E, N + 1);
-  double local = 0.0;
-  for (int i = beg; i < end && i < N; ++i) local += C[i];
-  double x = local;
+  float ls = 0.f, lc = 0.f;                                 // this thread's elements
+  for (int i = beg; i < end && i < N; ++i) comp_add(ls, lc, H[i].x);
+  float xs = ls, xc = lc;                                   // inclusive scan over the warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+    const float ys = __shfl_up_sync(0xffffffffu, xs, o), yc = __shfl_up_sync(0xffffffffu, xc, o);
+    if (lane >= o) {
+      float e;
+      two_sum(ys, xs, xs, e);
+      xc = __fadd_rn(__fadd_rn(xc, yc), e);
+    }
   }
-  if (lane == 31) wsum[warp] = x;
+  if (lane == 31) wtot[warp] = make_float2(xs, xc);
+  // this thread's exclusive prefix within the warp: the inclusive one less its own part
+  const float ps = __shfl_up_sync(0xffffffffu, xs, 1), pc = __shfl_up_sync(0xffffffffu, xc, 1);
   __syncthreads();
-  double pre = x - local;
-  for (int w = 0; w < warp; ++w) pre += wsum[w];
-  float2* H = reinterpret_cast<float2*>(C);
+  float s = 0.f, c = 0.f;
+  for (int w = 0; w < warp; ++w) {
+    comp_add(s, c, wtot[w].x);
+    c = __fadd_rn(c, wtot[w].y);
+  }
+  if (lane > 0) {
+    comp_add(s, c, ps);
+    c = __fadd_rn(c, pc);
+  }
   for (int i = beg; i < end; ++i) {
-    const double v = i < N ? C[i] : 0.0;
-    const float hi = __double2float_rn(pre);
-    H[i] = make_float2(hi, __double2float_rn(pre - (double)hi));
-    pre += v;
+    const float v = i < N ? H[i].x : 0.f;
+    H[i] = make_float2(s, c);
+    comp_add(s, c, v);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += kThreads) {
@@ -300,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_boxcar_f32(const float* __restrict
     int bw = 0;
     for (int w = 0; w < nw; ++w) {
       const float2 c1 = H[i + sW[w]];
-      const float B = __fadd_rn(__fsub_rn(c1.x, c0.x), __fsub_rn(c1.y, c0.y));
+      const float B = __fadd_rn(__fsub_rn(__fsub_rn(c1.x, c0.x), sMh[w]), __fsub_rn(__fsub_rn(c1.y, c0.y), sMl[w]));
       const float snr = __fmul_rn(B, sInv[w]);
       if (mode == TX_OUT_CUBE) outf[((size_t)d * nw + w) * T + t0 + i] = snr;
       if (snr > best) { best = snr; bw = w; }
@@ -399,17 +477,41 @@ int float_execute(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_
   b->head = mod(b->head + p->T, p->R);
   if ((rc = mark(1))) return rc;
 
-  // stage 1: every row position of every (coarse DM, sub-band)
-  const dim3 g1((unsigned)((p->Pp + kThreads - 1) / kThreads), (unsigned)p->nsub, (unsigned)p->nk);
-  k_stage1_f32<<<g1, kThreads, (size_t)p->m * sizeof(int64_t), st>>>(ring, p->R, start, p->dev.d1, p->dev.abase,
-                                                                      p->nchan, p->m, p->nsub, p->Pp, P);
+  // stage 1: the plan's items (sub-band, coarse DMs, time tile), one block each
+  const int sw = p->tile_f + p->span_f + 4;
+  const int smem1 = p->m * sw * (int)sizeof(float);
+  const int nit = (int)p->items_f.size();
+#define TX_F1(VW)                                                                                                  \
+  do {                                                                                                             \
+    TX_CUDA(cudaFuncSetAttribute((const void*)k_stage1_f32<VW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1)); \
+    k_stage1_f32<VW><<<nit, kThreads1, smem1, st>>>(ring, p->R, start, p->dev.items_f, p->dev.d1, p->dev.abase,     \
+                                                   p->nchan, p->m, p->nsub, p->Pp, sw, P);                          \
+  } while (0)
+  switch (p->tile_f) {
+    case 256: TX_F1(8); break;
+    case 128: TX_F1(4); break;
+    case 64: TX_F1(2); break;
+    default: TX_F1(1); break;
+  }
+#undef TX_F1
   TX_CUDA(cudaGetLastError());
   if ((rc = mark(2))) return rc;
 
   // stage 2 with per-tile sums
-  const dim3 g2((unsigned)p->ntile2f, (unsigned)p->ndm);
-  k_stage2_f32<<<g2, kThreads, (size_t)p->nsub * sizeof(int32_t), st>>>(P, p->Pp, p->dev.e2, p->nsub, p->group, D, Dp,
-                                                                         p->Td, p->T, part, p->ntile2f);
+  const dim3 g2((unsigned)p->ntile2, (unsigned)p->nk);
+  const int threads2 = std::min(p->group, kStage2MaxGroup) * 32;
+  // chunks of about 56 KB of staged rows, so that four blocks share an SM
+  const int sc2 = std::max(1, std::min(p->nsub_chunk2, (56 * 1024) / (p->sw2_i32 * (int)sizeof(float))));
+  const int smem2 = sc2 * p->sw2_i32 * (int)sizeof(float);
+#define TX_F2(NW)                                                                                                 \
+  do {                                                                                                            \
+    TX_CUDA(cudaFuncSetAttribute((const void*)k_stage2_f32<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2)); \
+    k_stage2_f32<NW><<<g2, threads2, smem2, st>>>(P, p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, sc2,            \
+                                                  p->sw2_i32, D, Dp, p->Td, p->T, part, p->ntile2);              \
+  } while (0)
+  if (p->nw2 == 512) TX_F2(512);
+  else TX_F2(256);
+#undef TX_F2
   TX_CUDA(cudaGetLastError());
   if ((rc = mark(3))) return rc;
 
@@ -419,10 +521,10 @@ int float_execute(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_
     TX_CUDA(cudaGetLastError());
     if ((rc = mark(4))) return rc;
     if (p->output == TX_OUT_CANDS) TX_CUDA(cudaMemsetAsync(d_ncand, 0, sizeof(int64_t), st));
-    const int smem = (kBoxTile + p->wmax) * (int)sizeof(double);
+    const int smem = (kBoxTile + p->wmax) * (int)sizeof(float2);
     // the most any plan needs (the attribute belongs to the current device)
     TX_CUDA(cudaFuncSetAttribute((const void*)k_boxcar_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (kBoxTile + kMaxWidth) * (int)sizeof(double)));
+                                 (kBoxTile + kMaxWidth) * (int)sizeof(float2)));
     float* outf = static_cast<float*>(d_out);
     uint8_t* outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(d_out) + (size_t)p->ndm * p->T * 4 : nullptr;
     k_boxcar_f32<<<p->ndm * p->ntile3, kThreads, smem, st>>>(

@@ -80,6 +80,7 @@ int do_upload(tx_plan* p) {
   if ((rc = upload(&p->dev.items1, p->items1))) return rc;
   if ((rc = upload(&p->dev.tab1, p->tab1))) return rc;
   if ((rc = upload(&p->dev.tab2, p->tab2))) return rc;
+  if ((rc = upload(&p->dev.items_f, p->items_f))) return rc;
   const int s1 = (int)stage1_smem_bytes(p->m, p->q1);
   switch (p->q1) {
     case 256: rc = set_stage1_attr_for<256>(p, s1); break;
@@ -223,6 +224,7 @@ void tx_plan_destroy(tx_plan* p) {
     cudaFree(p->dev.items1);
     cudaFree(p->dev.tab1);
     cudaFree(p->dev.tab2);
+    cudaFree(p->dev.items_f);
     cudaSetDevice(prev);
   }
   delete p;

@@ -270,7 +270,7 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   }
   p->Dp = round_up(p->Td + 8, 8);
   p->ntile3 = (int32_t)((p->T + kBoxTile - 1) / kBoxTile);
-  p->ntile2f = (int32_t)((p->Td + kFloatTile - 1) / kFloatTile);
+  p->ntile2f = p->ntile2;   // the float path's stage 2 uses the same tiles (2 nw2 outputs)
 
   // ---- stage-1 work list ----------------------------------------------------
   // quarter length q1: the largest of 256/128/64/32 whose staged words, raw
@@ -329,6 +329,41 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   std::stable_sort(p->items1.begin(), p->items1.end(), [](const Stage1Item& a, const Stage1Item& b) {
     return a.tau0 != b.tau0 ? a.tau0 < b.tau0 : (a.s != b.s ? a.s < b.s : a.kb < b.kb);
   });
+  if (p->interm == TX_INTERM_F32) {
+    // float path stage 1: items of `tile_f` times whose coarse DMs' delay spread in
+    // the sub-band is at most span_f, the largest of four shapes whose staged
+    // float windows (tile + spread + 4 per channel) fit shared memory
+    const int shapes[4][2] = {{256, 240}, {128, 112}, {64, 48}, {32, 16}};
+    int si = 0;
+    while (si < 3 && (int64_t)m * (shapes[si][0] + shapes[si][1] + 4) * 4 > kSmemMax - 2048) ++si;
+    p->tile_f = shapes[si][0];
+    p->span_f = shapes[si][1];
+    for (int s = 0; s < nsub; ++s) {
+      int kb = 0;
+      while (kb < nk) {
+        auto spread = [&](int k0, int k1) {
+          int32_t v = 0;
+          for (int c = s * m; c < (s + 1) * m; ++c)
+            v = std::max(v, p->d1[(size_t)(k1 - 1) * nchan + c] - p->d1[(size_t)k0 * nchan + c]);
+          return v;
+        };
+        int ke = kb + 1;
+        while (ke < nk && ke - kb < kStage1MaxCoarse && spread(kb, ke + 1) <= p->span_f) ++ke;
+        int64_t lo = INT64_MAX, hi = 0;
+        for (int k = kb; k < ke; ++k) {
+          lo = std::min<int64_t>(lo, p->abase[(size_t)k * nsub + s]);
+          hi = std::max<int64_t>(hi, (int64_t)p->abase[(size_t)k * nsub + s] + p->Pp);
+        }
+        const int32_t span = spread(kb, ke);
+        for (int64_t t0 = floor_div(lo, p->tile_f) * p->tile_f; t0 < hi; t0 += p->tile_f)
+          p->items_f.push_back(Stage1Item{s, kb, ke, (int32_t)t0, span, 0, 0, 0});
+        kb = ke;
+      }
+    }
+    std::stable_sort(p->items_f.begin(), p->items_f.end(), [](const Stage1Item& a, const Stage1Item& b) {
+      return a.tau0 != b.tau0 ? a.tau0 < b.tau0 : (a.s != b.s ? a.s < b.s : a.kb < b.kb);
+    });
+  }
 
   // ---- ring ----------------------------------------------------------------------
   // Each channel is a circular buffer of R bytes; the next block lands at

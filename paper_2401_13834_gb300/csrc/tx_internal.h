@@ -53,8 +53,7 @@ constexpr int kBoxThreads = 256;
 constexpr int kMaxWidths = 32;
 constexpr int kMaxWidth = 4096;
 
-// ---- the float path (normalised data) -------------------------------------------
-constexpr int kFloatTile = 256;        // outputs per block of its stage 2 (one thread each)
+
 
 // Stage-1 work item: sub-band s, coarse DMs [kb, ke), times [tau0, tau0 + 4 q1),
 // span = max over the sub-band's channels of d1[ke-1][c] - d1[kb][c]; tab =
@@ -85,6 +84,7 @@ struct DevicePlan {
   Stage1Item* items1 = nullptr;  // [n_items1]
   int32_t* tab1 = nullptr;       // stage-1 offset tables of the item groups
   int32_t* tab2 = nullptr;       // pipelined stage 2: offset tables per (coarse group, sub-band chunk)
+  Stage1Item* items_f = nullptr; // float path stage-1 items
 };
 
 void set_error(const char* fmt, ...);
@@ -137,7 +137,9 @@ struct tx_plan {
   int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
   int32_t e2w2 = 0;               // words of one stage-2 group's delays in shared memory (rounded to 4)
   int32_t ntile3 = 0;             // boxcar tiles over [0, T)
-  int32_t ntile2f = 0;            // float path: stage-2 tiles of kFloatTile outputs over the series
+  int32_t ntile2f = 0;            // float path: stage-2 tiles over the series (those of ntile2)
+  int32_t tile_f = 0, span_f = 0;  // float path: stage-1 item length and delay spread limit
+  std::vector<tx::Stage1Item> items_f;  // float path stage-1 items (s, coarse DMs [kb, ke), times)
   std::vector<tx::Stage1Item> items1;
   // stage-1 offset tables, per (s, kb, ke): rows kk < ke - kb of (m + 3) & ~3
   // words, word c = c * staged words + ((tab1_phase + d1[kb][c]) & 15) +

@@ -181,6 +181,7 @@ KERNEL_SECTIONS = {
     "k_ingest_tf": "// ingest (",
     "k_stage1": "// stage 1 (",
     "k_stage2_u16": "// stage 2 (",
+    "k_stage2_pipe": "// stage 2 (",
     "k_boxcar": "// boxcar matched filter",
 }
 
@@ -664,7 +665,8 @@ def run_ours(args):
                 entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": amount})
             phases[name] = entry
         dom = max(phase_ms, key=phase_ms.get)
-        kernel_of = {"ingest": "k_ingest_tf", "stage1": "k_stage1", "stage2": "k_stage2_u16", "stats": "k_stats",
+        kernel_of = {"ingest": "k_ingest_tf", "stage1": "k_stage1", "stage2": "k_stage2_pipe" if plan.tile_split2 and
+                     plan.group <= 16 and plan.interm in ("u16", "f16") else "k_stage2_u16", "stats": "k_stats",
                      "boxcar": "k_boxcar"}
         d = phases[dom]
         roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],

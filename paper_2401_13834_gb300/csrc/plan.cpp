@@ -302,8 +302,9 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
       };
       int ke = kb + 1;
       while (ke < nk && ke - kb < kStage1MaxCoarse && spread(kb, ke + 1) <= p->span1_max) ++ke;
-      // 16 or 32 coarse DMs fill the 32 warps exactly (two or one warps per DM)
-      if (ke - kb >= 16) ke = kb + (ke - kb) / 16 * 16;
+      // 16, 32 or 64 coarse DMs keep the 32 warps evenly busy (two, one or half a warp per DM)
+      if (ke - kb >= 32) ke = kb + (ke - kb) / 32 * 32;
+      else if (ke - kb >= 16) ke = kb + 16;
       const int32_t span = spread(kb, ke);
       int64_t lo = INT64_MAX, hi = 0;
       for (int k = kb; k < ke; ++k) {

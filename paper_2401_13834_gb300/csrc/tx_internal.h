@@ -18,15 +18,16 @@ constexpr double kDispersion = 4.148808e3;
 // A stage-1 tile covers 4*q consecutive times: a shared-memory word holds the
 // samples of times j, j+q, j+2q, j+3q of one channel, so one 32-bit load feeds
 // four outputs whatever the per-channel delay.
-constexpr int kStage1MaxCoarse = 32;   // coarse DMs that share one staged tile
+constexpr int kStage1MaxCoarse = 64;   // coarse DMs that share one staged tile (two per warp at most)
 constexpr int kStage1Warps = 32;
 // Staged words per channel for quarter length q: the tile (q words), the
 // chunk's delay spread (<= q - 16), the window's misalignment (< 16) and
-// rounding to 4-word groups: at most 2q + 2. Word j of a channel takes raw
-// bytes j + iq (i = 0..3), so the raw window spans 5q + 2 bytes, rounded to
-// 16-byte chunks plus one.
-constexpr int kStage1StagedWords(int q) { return 2 * q + 16; }
-constexpr int kStage1RawBytes(int q) { return (5 * q + 2 + 15) / 16 * 16 + 16; }
+// rounding to 4-word groups: at most 2q + 2, so 2q + 4 words. Word j of a
+// channel takes raw bytes j + iq (i = 0..3): the transform reads bytes up to
+// 4 (Q + span + 18) / 4 - 1 + 3q <= 5q + 1 of the window, which spans 5q + 2
+// bytes rounded up to 16-byte chunks.
+constexpr int kStage1StagedWords(int q) { return 2 * q + 4; }
+constexpr int kStage1RawBytes(int q) { return (5 * q + 2 + 15) / 16 * 16; }
 constexpr int kSmemMax = 232448;       // opt-in dynamic shared memory per block (227 KB)
 
 // Polls of an mbarrier before a kernel gives up waiting for a bulk copy; each

@@ -144,10 +144,14 @@ typedef struct tx_plan_desc {
                                     float path runs single beams (tx_execute,
                                     tx_execute_host, pipelines); it is not taken by
                                     compact beams, batches or tx_dedisperse_noalloc */
+  int32_t        tile_box;       /* boxcar outputs per work unit: 2048, 4096 or 8192;
+                                    0 = the longest that leaves at least 4864
+                                    (DM, unit) pairs (results do not depend on it) */
 } tx_plan_desc;
 
 typedef struct tx_plan_info {
-  int32_t nchan, nsub, ndm, ncoarse, group, nwidth, wmax, reserved0;
+  int32_t nchan, nsub, ndm, ncoarse, group, nwidth, wmax;
+  int32_t tile_box;         /* the boxcar unit chosen (see tx_plan_desc)            */
   int64_t nsamp;            /* T                                                    */
   int64_t overlap;          /* L: carried samples per channel                       */
   int64_t max_delay;        /* max over (d, c) of d1 + d2                           */

@@ -40,13 +40,14 @@ class _Desc(C.Structure):
         ("layout", C.c_int32), ("interm", C.c_int32), ("output", C.c_int32),
         ("snr_threshold", C.c_float), ("max_cands", C.c_int64), ("stats", C.c_int32),
         ("stats_lambda", C.c_double), ("tile_q1", C.c_int32), ("tile_split2", C.c_int32), ("norm", C.c_int32),
+        ("tile_box", C.c_int32),
     ]
 
 
 class _Info(C.Structure):
     _fields_ = [
         ("nchan", C.c_int32), ("nsub", C.c_int32), ("ndm", C.c_int32), ("ncoarse", C.c_int32),
-        ("group", C.c_int32), ("nwidth", C.c_int32), ("wmax", C.c_int32), ("reserved0", C.c_int32),
+        ("group", C.c_int32), ("nwidth", C.c_int32), ("wmax", C.c_int32), ("tile_box", C.c_int32),
         ("nsamp", C.c_int64), ("overlap", C.c_int64), ("max_delay", C.c_int64), ("series_len", C.c_int64),
         ("workspace_bytes", C.c_int64), ("beam_state_bytes", C.c_int64), ("out_bytes", C.c_int64),
         ("export_bytes", C.c_int64), ("block_bytes", C.c_int64), ("ring_len", C.c_int64),
@@ -177,7 +178,7 @@ def geometric_widths(ratio: float, wmax: int) -> np.ndarray:
 
 
 def _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output, snr_threshold,
-               max_cands, stats, stats_lambda, tile_q1, tile_split2, norm="none"):
+               max_cands, stats, stats_lambda, tile_q1, tile_split2, norm="none", tile_box=0):
     """A tx_plan_desc over arrays kept alive in `keep` (a dict)."""
     keep["freqs"] = np.ascontiguousarray(freqs_mhz, dtype=np.float64)
     keep["dms"] = np.ascontiguousarray(dms, dtype=np.float64)
@@ -203,6 +204,7 @@ def _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout
     d.tile_q1 = int(tile_q1)
     d.tile_split2 = int(tile_split2)
     d.norm = NORMS[norm]
+    d.tile_box = int(tile_box)
     return d
 
 
@@ -228,18 +230,18 @@ class Plan:
     def _read_info(self, h):
         inf = _Info()
         _check(lib.tx_plan_get_info(h, C.byref(inf)))
-        self.info = {k: int(getattr(inf, k)) for k, _ in _Info._fields_ if k != "reserved0"}
+        self.info = {k: int(getattr(inf, k)) for k, _ in _Info._fields_}
         for k, v in self.info.items():
             setattr(self, k, v)
 
     def __init__(self, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group=0, layout="ft", interm="u16",
                  output="cands", snr_threshold=6.0, max_cands=1 << 20, stats="block", stats_lambda=0.25,
-                 tile_q1=0, tile_split2=0, norm="none"):
+                 tile_q1=0, tile_split2=0, norm="none", tile_box=0):
         if norm != "none" and interm == "u16":
             interm = "f32"                     # a normalisation runs the float path
         keep = {}
         d = _make_desc(keep, freqs_mhz, tsamp_s, dms, nsub, widths, nsamp, group, layout, interm, output,
-                       snr_threshold, max_cands, stats, stats_lambda, tile_q1, tile_split2, norm)
+                       snr_threshold, max_cands, stats, stats_lambda, tile_q1, tile_split2, norm, tile_box)
         self.norm = norm
         self.freqs, self.dms, self.widths = keep["freqs"], keep["dms"], keep["widths"]
         self.layout, self.interm, self.output, self.stats = layout, interm, output, stats

@@ -79,7 +79,7 @@ struct BatchLaunch {
   int nmem = 0, nunits = 0;                  // member beams, work units (stage 1: the plans' items)
   int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
   int layout = 0;                            // stage 1 mL, stage 2 slot words, boxcar wmaxL
-  int aux = 0;                               // stage 2 words of a group's delays
+  int aux = 0;                               // stage 2 words of a group's delays (or chunk sub-bands), boxcar tileL
 };
 
 int64_t mod64(int64_t a, int64_t r) { return ((a % r) + r) % r; }
@@ -335,10 +335,14 @@ int build_batch(tx_batch* B, int64_t budget) {
       if ((rc = add_members(L, kv.second, first,
                             [&](int b) -> int64_t { return (int64_t)B->plans[b]->ndm * B->plans[b]->ntile3; })))
         return rc;
-      int wm = 0;
-      for (int b : kv.second) wm = std::max(wm, B->plans[b]->wmax);
+      int wm = 0, tl = kBoxTile;
+      for (int b : kv.second) {
+        wm = std::max(wm, B->plans[b]->wmax);
+        tl = std::max(tl, B->plans[b]->box_tile);
+      }
       L.layout = wm;
-      L.smem = box_smem_for(wm);
+      L.aux = tl;
+      L.smem = box_smem_for(tl, wm);
       const void* k = launch_kernel(L);
       TX_CUDA(raise_smem_limit(k, L.smem));  // before the occupancy query
       int bps = 1;
@@ -464,7 +468,7 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
         break;
       default:
         box_kernel<SlotArgs>(L.nwc, L.mode)<<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits,
-                                                                               L.layout);
+                                                                               L.aux, L.layout);
         break;
     }
     const cudaError_t e = cudaGetLastError();

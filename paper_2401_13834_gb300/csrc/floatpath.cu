@@ -527,8 +527,9 @@ int float_execute(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_
                                  (kBoxTile + kMaxWidth) * (int)sizeof(float2)));
     float* outf = static_cast<float*>(d_out);
     uint8_t* outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(d_out) + (size_t)p->ndm * p->T * 4 : nullptr;
-    k_boxcar_f32<<<p->ndm * p->ntile3, kThreads, smem, st>>>(
-        D, Dp, p->T, p->ntile3, ms, p->dev.widths, p->nw, p->wmax, p->output, p->gamma, outf, outw,
+    const int nt = (int)((p->T + kBoxTile - 1) / kBoxTile);   // tiles of kBoxTile outputs per DM
+    k_boxcar_f32<<<p->ndm * nt, kThreads, smem, st>>>(
+        D, Dp, p->T, nt, ms, p->dev.widths, p->nw, p->wmax, p->output, p->gamma, outf, outw,
         static_cast<tx_cand*>(d_out), reinterpret_cast<unsigned long long*>(d_ncand), p->max_cands);
     TX_CUDA(cudaGetLastError());
   } else {

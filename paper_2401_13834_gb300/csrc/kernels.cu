@@ -45,7 +45,7 @@ int stage2_smem(const tx_plan* p) {
   return p->nsub_chunk2 * p->sw2_i32 * 4;
 }
 
-int box_smem(const tx_plan* p) { return box_smem_for(p->wmax); }
+int box_smem(const tx_plan* p) { return box_smem_for(p->box_tile, p->wmax); }
 
 template <int Q, typename PT, bool HALF = false>
 int set_stage1_attr(int bytes) {
@@ -500,7 +500,7 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
     const int nunits = p->ndm * p->ntile3;
     const int grid = std::min(nunits, std::max(p->dev.num_sms, 1) * p->dev.box_blocks_per_sm);
     box_kernel<OneBeam>(p->nw, p->output)<<<grid, kBoxThreads, box_smem(p), st>>>(OneBeam{a}, nullptr, nullptr, 1,
-                                                                                   nunits, p->wmax);
+                                                                                   nunits, p->box_tile, p->wmax);
     TX_CUDA(cudaGetLastError());
   } else {
     TX_MARK(4);

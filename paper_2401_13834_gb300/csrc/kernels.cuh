@@ -69,9 +69,13 @@ struct BeamArgs {
   int64_t L, tail_pitch;
   double lam, gamma;
   int32_t nchan, m, nsub, ndm, G, split2, SC, SWW, ntile2, ntile3, nw, wmax;  // split2: part entries per stage-2 tile
-  int32_t layout, ingest_vec, running, output, compact, tail_pad, half, box_vec, tab1_phase;
+  int32_t tail_pad, tab1_phase;
+  int32_t box_tile;              // boxcar outputs per unit (a multiple of kBoxTile)
   uint32_t polls;                // polling limit of the first wait for each bulk copy
+  int8_t layout, ingest_vec, running, output, compact, half, box_vec;
 };
+// Two constant-memory slots of kArgSlotBeams of these fit the 64 KB bank.
+static_assert(sizeof(BeamArgs) <= 352, "BeamArgs grew");
 
 // Where a kernel finds a beam's arguments (the Src template parameter).
 // OneBeam holds them as a kernel parameter (one execute, constant bank); the
@@ -1539,7 +1543,8 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
 // boxcar matched filter (Eq. 5 via prefix sums, Sec. 2.4) and outputs (Sec. 2.5)
 // ---------------------------------------------------------------------------
 // Persistent blocks walk contiguous runs of units (fine DM d, tile of
-// kBoxTile outputs; in a batch, the units of all member beams in turn); each
+// box_tile outputs, a multiple of kBoxTile chosen by the plan; in a batch, the
+// units of all member beams in turn); each
 // unit's series (with its W_max - 1 look-ahead) is copied into shared memory
 // with cp.async while the previous unit is being filtered, then turned in
 // place into the prefix sum P (P[0] = 0), and each output t takes
@@ -1550,11 +1555,12 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
 //   for those points only.
 // NWT > 0: exactly NWT widths, per-width constants in registers.
 // NWT = 0: any count up to kMaxWidths, constants in shared memory.
-// The two shared buffers are sized for wmaxL (the largest W_max of the launch).
+// The two shared buffers are sized for tileL and wmaxL (the largest box_tile and
+// W_max of the launch).
 template <int NWT, int MODE, typename Src>
 __global__ void __launch_bounds__(kBoxThreads, NWT > 12 ? 3 : 4)
 k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
-         int wmaxL) {
+         int tileL, int wmaxL) {
   constexpr int NR = NWT > 0 ? NWT : 1;
   extern __shared__ __align__(16) uint32_t smb[];
   __shared__ uint32_t wsum[kBoxThreads / 32];
@@ -1562,7 +1568,7 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   __shared__ SnrConst sC[kMaxWidths];
   __shared__ __align__(8) uint64_t barb[2];  // completion of the bulk copy into series buffer 0 / 1
   uint32_t bph[2] = {0u, 0u};
-  const int bufw = (kBoxTile + wmaxL + 8 + 3) & ~3;  // words per buffer: 4 pad + series + chunk rounding
+  const int bufw = (tileL + wmaxL + 8 + 3) & ~3;  // words per buffer: 4 pad + series + chunk rounding
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int u_begin = (int)((int64_t)nunits * blockIdx.x / gridDim.x);
   const int u_end = (int)((int64_t)nunits * (blockIdx.x + 1) / gridDim.x);
@@ -1584,8 +1590,8 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     int lu, j;
     const BeamArgs a = locate(cur_i, u, lu, j);
     const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
-    const int64_t t0 = (int64_t)tile * kBoxTile;
-    const int n = (int)min((int64_t)kBoxTile, a.T - t0);
+    const int64_t t0 = (int64_t)tile * a.box_tile;
+    const int n = (int)min((int64_t)a.box_tile, a.T - t0);
     const int nq = (n + a.wmax - 1 + 3) >> 2;  // 16-byte chunks of the series window
     const int32_t* src = a.D + (size_t)d * a.Dp + t0;
     uint32_t* dst = smb + (size_t)buf * bufw + 4;
@@ -1613,8 +1619,8 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const int nw = NWT > 0 ? NWT : a.nw;
     const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
     const int64_t T = a.T;
-    const int64_t t0 = (int64_t)tile * kBoxTile;
-    const int n = (int)min((int64_t)kBoxTile, T - t0);
+    const int64_t t0 = (int64_t)tile * a.box_tile;
+    const int n = (int)min((int64_t)a.box_tile, T - t0);
     const int N = n + a.wmax - 1;
     const SnrConst* cst = a.cst + (size_t)d * nw;
     // series D[j] at C[j] (16-byte aligned); the scan leaves C[k] = D[0] + ... + D[k - 1]
@@ -1669,192 +1675,198 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     }
     __syncthreads();
 
-    if constexpr (NWT > 0 && MODE == TX_OUT_CANDS) {
-      if (n == kBoxTile && a.box_vec) {
-        // full tile, widths 1, 2 and multiples of 4: each thread tests the
-        // four outputs 4q .. 4q + 3 of quads q = tid + 256 r from aligned
-        // 16-byte loads of C (its own quad and the next for widths 1, 2 and
-        // 4, one more per wider width); hits go to a bit mask as below
-        constexpr int QR = kBoxTile / 4 / kBoxThreads;
-        const uint4* C4 = reinterpret_cast<const uint4*>(C);
-        uint32_t mask = 0;
-#pragma unroll
-        for (int r = 0; r < QR; ++r) {
-          const int q = threadIdx.x + r * kBoxThreads;
-          const uint4 cl = C4[q], nx = C4[q + 1];
-          int32_t m0 = (int32_t)(cl.y - cl.x) - thr[0], m1 = (int32_t)(cl.z - cl.y) - thr[0];
-          int32_t m2 = (int32_t)(cl.w - cl.z) - thr[0], m3 = (int32_t)(nx.x - cl.w) - thr[0];
-          m0 = max(m0, (int32_t)(cl.z - cl.x) - thr[1]);
-          m1 = max(m1, (int32_t)(cl.w - cl.y) - thr[1]);
-          m2 = max(m2, (int32_t)(nx.x - cl.z) - thr[1]);
-          m3 = max(m3, (int32_t)(nx.y - cl.w) - thr[1]);
-#pragma unroll
-          for (int w = 2; w < NR; ++w) {
-            const uint4 cw = C4[q + (Wr[w] >> 2)];
-            m0 = max(m0, (int32_t)(cw.x - cl.x) - thr[w]);
-            m1 = max(m1, (int32_t)(cw.y - cl.y) - thr[w]);
-            m2 = max(m2, (int32_t)(cw.z - cl.z) - thr[w]);
-            m3 = max(m3, (int32_t)(cw.w - cl.w) - thr[w]);
+    // the unit in sub-tiles of kBoxTile outputs: full ones take the unrolled tests
+    for (int s0 = 0; s0 < n; s0 += kBoxTile) {
+      const int ns = min(kBoxTile, n - s0);
+      const uint32_t* Cs = C + s0;
+      const int64_t ts = t0 + s0;
+      if constexpr (NWT > 0 && MODE == TX_OUT_CANDS) {
+        if (ns == kBoxTile && a.box_vec) {
+          // full tile, widths 1, 2 and multiples of 4: each thread tests the
+          // four outputs 4q .. 4q + 3 of quads q = tid + 256 r from aligned
+          // 16-byte loads of C (its own quad and the next for widths 1, 2 and
+          // 4, one more per wider width); hits go to a bit mask as below
+          constexpr int QR = kBoxTile / 4 / kBoxThreads;
+          const uint4* C4 = reinterpret_cast<const uint4*>(Cs);
+          uint32_t mask = 0;
+  #pragma unroll
+          for (int r = 0; r < QR; ++r) {
+            const int q = threadIdx.x + r * kBoxThreads;
+            const uint4 cl = C4[q], nx = C4[q + 1];
+            int32_t m0 = (int32_t)(cl.y - cl.x) - thr[0], m1 = (int32_t)(cl.z - cl.y) - thr[0];
+            int32_t m2 = (int32_t)(cl.w - cl.z) - thr[0], m3 = (int32_t)(nx.x - cl.w) - thr[0];
+            m0 = max(m0, (int32_t)(cl.z - cl.x) - thr[1]);
+            m1 = max(m1, (int32_t)(cl.w - cl.y) - thr[1]);
+            m2 = max(m2, (int32_t)(nx.x - cl.z) - thr[1]);
+            m3 = max(m3, (int32_t)(nx.y - cl.w) - thr[1]);
+  #pragma unroll
+            for (int w = 2; w < NR; ++w) {
+              const uint4 cw = C4[q + (Wr[w] >> 2)];
+              m0 = max(m0, (int32_t)(cw.x - cl.x) - thr[w]);
+              m1 = max(m1, (int32_t)(cw.y - cl.y) - thr[w]);
+              m2 = max(m2, (int32_t)(cw.z - cl.z) - thr[w]);
+              m3 = max(m3, (int32_t)(cw.w - cl.w) - thr[w]);
+            }
+            mask |= ((uint32_t)(m0 >= 0) | ((uint32_t)(m1 >= 0) << 1) | ((uint32_t)(m2 >= 0) << 2) |
+                     ((uint32_t)(m3 >= 0) << 3)) << (4 * r);
           }
-          mask |= ((uint32_t)(m0 >= 0) | ((uint32_t)(m1 >= 0) << 1) | ((uint32_t)(m2 >= 0) << 2) |
-                   ((uint32_t)(m3 >= 0) << 3)) << (4 * r);
-        }
-        if (__any_sync(0xffffffffu, mask != 0u)) {
-          for (int r = 0; r < 4 * QR; ++r) {
-            const int i = 4 * (threadIdx.x + (r >> 2) * kBoxThreads) + (r & 3);
-            const bool hit = (mask >> r) & 1u;
-            const unsigned hits = __ballot_sync(0xffffffffu, hit);
-            if (!hits) continue;
-            float best = -INFINITY;
-            int bw = 0;
-            if (hit) {
-              const uint32_t* Ci = C + i;
-              const uint32_t cl = Ci[0];
-              for (int w = 0; w < NR; ++w) {
-                const SnrConst c = cst[w];
-                const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
-                if (sv > best) { best = sv; bw = w; }
+          if (__any_sync(0xffffffffu, mask != 0u)) {
+            for (int r = 0; r < 4 * QR; ++r) {
+              const int i = 4 * (threadIdx.x + (r >> 2) * kBoxThreads) + (r & 3);
+              const bool hit = (mask >> r) & 1u;
+              const unsigned hits = __ballot_sync(0xffffffffu, hit);
+              if (!hits) continue;
+              float best = -INFINITY;
+              int bw = 0;
+              if (hit) {
+                const uint32_t* Ci = Cs + i;
+                const uint32_t cl = Ci[0];
+                for (int w = 0; w < NR; ++w) {
+                  const SnrConst c = cst[w];
+                  const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+                  if (sv > best) { best = sv; bw = w; }
+                }
+              }
+              const int leader = __ffs(hits) - 1;
+              unsigned long long base = 0;
+              if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+              base = __shfl_sync(0xffffffffu, base, leader);
+              if (hit) {
+                const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+                if (idx < (unsigned long long)a.max_cands) {
+                  tx_cand rec;
+                  rec.dm_index = d;
+                  rec.t = (int32_t)(ts + i);
+                  rec.w_index = bw;
+                  rec.snr = best;
+                  a.cands[idx] = rec;
+                }
               }
             }
-            const int leader = __ffs(hits) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (hit) {
-              const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
-              if (idx < (unsigned long long)a.max_cands) {
-                tx_cand rec;
-                rec.dm_index = d;
-                rec.t = (int32_t)(t0 + i);
-                rec.w_index = bw;
-                rec.snr = best;
-                a.cands[idx] = rec;
-              }
-            }
           }
+          continue;
         }
-        continue;
-      }
-      if (n == kBoxTile) {
-        // full tile, candidates: each thread tests outputs tid + 256 r (r < 8)
-        // and keeps its hits in a bit mask; the rare hits are written after,
-        // once per warp that has any
-        constexpr int RR = kBoxTile / kBoxThreads;
-        uint32_t mask = 0;
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          const uint32_t* Ci = C + threadIdx.x + r * kBoxThreads;
-          const uint32_t cl = Ci[0];
-          int32_t mx = INT32_MIN;
-#pragma unroll
-          for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
-          mask |= (uint32_t)(mx >= 0) << r;
-        }
-        if (__any_sync(0xffffffffu, mask != 0u)) {
+        if (ns == kBoxTile) {
+          // full tile, candidates: each thread tests outputs tid + 256 r (r < 8)
+          // and keeps its hits in a bit mask; the rare hits are written after,
+          // once per warp that has any
+          constexpr int RR = kBoxTile / kBoxThreads;
+          uint32_t mask = 0;
+  #pragma unroll
           for (int r = 0; r < RR; ++r) {
-            const int i = threadIdx.x + r * kBoxThreads;
-            const bool hit = (mask >> r) & 1u;
-            const unsigned hits = __ballot_sync(0xffffffffu, hit);
-            if (!hits) continue;
-            float best = -INFINITY;
-            int bw = 0;
-            if (hit) {
-              const uint32_t* Ci = C + i;
-              const uint32_t cl = Ci[0];
+            const uint32_t* Ci = Cs + threadIdx.x + r * kBoxThreads;
+            const uint32_t cl = Ci[0];
+            int32_t mx = INT32_MIN;
+  #pragma unroll
+            for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
+            mask |= (uint32_t)(mx >= 0) << r;
+          }
+          if (__any_sync(0xffffffffu, mask != 0u)) {
+            for (int r = 0; r < RR; ++r) {
+              const int i = threadIdx.x + r * kBoxThreads;
+              const bool hit = (mask >> r) & 1u;
+              const unsigned hits = __ballot_sync(0xffffffffu, hit);
+              if (!hits) continue;
+              float best = -INFINITY;
+              int bw = 0;
+              if (hit) {
+                const uint32_t* Ci = Cs + i;
+                const uint32_t cl = Ci[0];
+                for (int w = 0; w < NR; ++w) {
+                  const SnrConst c = cst[w];
+                  const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+                  if (sv > best) { best = sv; bw = w; }
+                }
+              }
+              const int leader = __ffs(hits) - 1;
+              unsigned long long base = 0;
+              if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+              base = __shfl_sync(0xffffffffu, base, leader);
+              if (hit) {
+                const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+                if (idx < (unsigned long long)a.max_cands) {
+                  tx_cand rec;
+                  rec.dm_index = d;
+                  rec.t = (int32_t)(ts + i);
+                  rec.w_index = bw;
+                  rec.snr = best;
+                  a.cands[idx] = rec;
+                }
+              }
+            }
+          }
+          continue;
+        }
+      }
+
+      for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const uint32_t* Ci = Cs + i;
+        const uint32_t cl = Ci[0];
+        float best = -INFINITY;
+        int bw = 0;
+        bool hit = false;
+        if (NWT > 0) {
+          if (MODE == TX_OUT_CANDS) {
+            int32_t mx = INT32_MIN;
+  #pragma unroll
+            for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
+            hit = mx >= 0;
+            if (hit) {  // rare: float S/N and the best width of a candidate
               for (int w = 0; w < NR; ++w) {
                 const SnrConst c = cst[w];
                 const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
                 if (sv > best) { best = sv; bw = w; }
               }
             }
-            const int leader = __ffs(hits) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (hit) {
-              const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
-              if (idx < (unsigned long long)a.max_cands) {
-                tx_cand rec;
-                rec.dm_index = d;
-                rec.t = (int32_t)(t0 + i);
-                rec.w_index = bw;
-                rec.snr = best;
-                a.cands[idx] = rec;
-              }
-            }
-          }
-        }
-        continue;
-      }
-    }
-
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint32_t* Ci = C + i;
-      const uint32_t cl = Ci[0];
-      float best = -INFINITY;
-      int bw = 0;
-      bool hit = false;
-      if (NWT > 0) {
-        if (MODE == TX_OUT_CANDS) {
-          int32_t mx = INT32_MIN;
-#pragma unroll
-          for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
-          hit = mx >= 0;
-          if (hit) {  // rare: float S/N and the best width of a candidate
+          } else {
+            float sv[NR];
+  #pragma unroll
             for (int w = 0; w < NR; ++w) {
               const SnrConst c = cst[w];
-              const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
-              if (sv > best) { best = sv; bw = w; }
+              sv[w] = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+            }
+            if (MODE == TX_OUT_CUBE) {
+  #pragma unroll
+              for (int w = 0; w < NR; ++w) a.outf[((size_t)d * nw + w) * T + ts + i] = sv[w];
+            } else {
+  #pragma unroll
+              for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
+              bw = NR - 1;
+  #pragma unroll
+              for (int w = NR - 1; w >= 0; --w)
+                if (sv[w] == best) bw = w;
             }
           }
         } else {
-          float sv[NR];
-#pragma unroll
-          for (int w = 0; w < NR; ++w) {
-            const SnrConst c = cst[w];
-            sv[w] = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
-          }
-          if (MODE == TX_OUT_CUBE) {
-#pragma unroll
-            for (int w = 0; w < NR; ++w) a.outf[((size_t)d * nw + w) * T + t0 + i] = sv[w];
-          } else {
-#pragma unroll
-            for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
-            bw = NR - 1;
-#pragma unroll
-            for (int w = NR - 1; w >= 0; --w)
-              if (sv[w] == best) bw = w;
+          for (int w = 0; w < nw; ++w) {
+            const int32_t B = (int32_t)(Ci[sW[w]] - cl);
+            const float snr = ((float)(B - sC[w].hi) - sC[w].lo) * sC[w].inv;
+            if (MODE == TX_OUT_CUBE) a.outf[((size_t)d * nw + w) * T + ts + i] = snr;
+            if (snr > best) { best = snr; bw = w; }
+            hit = hit || B >= sC[w].thr;
           }
         }
-      } else {
-        for (int w = 0; w < nw; ++w) {
-          const int32_t B = (int32_t)(Ci[sW[w]] - cl);
-          const float snr = ((float)(B - sC[w].hi) - sC[w].lo) * sC[w].inv;
-          if (MODE == TX_OUT_CUBE) a.outf[((size_t)d * nw + w) * T + t0 + i] = snr;
-          if (snr > best) { best = snr; bw = w; }
-          hit = hit || B >= sC[w].thr;
-        }
-      }
-      if (MODE == TX_OUT_PLANE) {
-        a.outf[(size_t)d * T + t0 + i] = best;
-        a.outw[(size_t)d * T + t0 + i] = (uint8_t)bw;
-      } else if (MODE == TX_OUT_CANDS) {
-        const unsigned act = __activemask();
-        const unsigned hits = __ballot_sync(act, hit);
-        if (hits) {
-          const int leader = __ffs(hits) - 1;
-          unsigned long long base = 0;
-          if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
-          base = __shfl_sync(act, base, leader);
-          if (hit) {
-            const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
-            if (idx < (unsigned long long)a.max_cands) {
-              tx_cand r;
-              r.dm_index = d;
-              r.t = (int32_t)(t0 + i);
-              r.w_index = bw;
-              r.snr = best;
-              a.cands[idx] = r;
+        if (MODE == TX_OUT_PLANE) {
+          a.outf[(size_t)d * T + ts + i] = best;
+          a.outw[(size_t)d * T + ts + i] = (uint8_t)bw;
+        } else if (MODE == TX_OUT_CANDS) {
+          const unsigned act = __activemask();
+          const unsigned hits = __ballot_sync(act, hit);
+          if (hits) {
+            const int leader = __ffs(hits) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+            base = __shfl_sync(act, base, leader);
+            if (hit) {
+              const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+              if (idx < (unsigned long long)a.max_cands) {
+                tx_cand r;
+                r.dm_index = d;
+                r.t = (int32_t)(ts + i);
+                r.w_index = bw;
+                r.snr = best;
+                a.cands[idx] = r;
+              }
             }
           }
         }
@@ -1864,7 +1876,7 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
 }
 
 template <typename Src>
-using BoxKernel = void (*)(const Src, const int32_t*, const int32_t*, int, int, int);
+using BoxKernel = void (*)(const Src, const int32_t*, const int32_t*, int, int, int, int);
 
 // Exact width counts 1..12 and 16 get their own instantiation; others use
 // the generic one (NWT = 0).
@@ -1917,7 +1929,7 @@ inline cudaError_t raise_smem_limit(const void* k, int bytes) {
 }
 
 // two buffers of (4 pad words + tile + look-ahead, rounded to 16-byte chunks)
-inline int box_smem_for(int wmax) { return 2 * ((kBoxTile + wmax + 8 + 3) & ~3) * 4; }
+inline int box_smem_for(int tile, int wmax) { return 2 * ((tile + wmax + 8 + 3) & ~3) * 4; }
 
 // uint16 stage 2: two even-copy slots, one odd-copy slot, address table
 inline int stage2_u16_smem_for(int slot, int sc, int e2w) {
@@ -1991,7 +2003,8 @@ inline BeamArgs make_args(const tx_plan* p, const tx_beam* b, const uint8_t* blo
   a.cst = reinterpret_cast<SnrConst*>(ws + p->ws_const);
   a.hoff = reinterpret_cast<int32_t*>(ws + p->ws_hoff);
   a.half = p->interm == TX_INTERM_F16;
-  a.box_vec = p->box_vec;
+  a.box_vec = (int8_t)p->box_vec;
+  a.box_tile = p->box_tile;
   a.tab1 = p->dev.tab1;
   a.tab2 = p->dev.tab2;
   a.tab1_phase = p->tab1_phase;

@@ -269,7 +269,22 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
       }
   }
   p->Dp = round_up(p->Td + 8, 8);
-  p->ntile3 = (int32_t)((p->T + kBoxTile - 1) / kBoxTile);
+  // boxcar units: the longest of 4, 2 or 1 kBoxTile sub-tiles that still gives
+  // every resident block of a full GPU several units (longer units spend less
+  // on the scan's barriers, the copy hand-off and the look-ahead)
+  p->box_tile = kBoxTile;
+  if (d->tile_box) {
+    if (d->tile_box != kBoxTile && d->tile_box != 2 * kBoxTile && d->tile_box != 4 * kBoxTile) {
+      set_error("tile_box must be 0, %d, %d or %d", kBoxTile, 2 * kBoxTile, 4 * kBoxTile);
+      return TX_ERR_INVALID_ARG;
+    }
+    p->box_tile = d->tile_box;
+  }
+  for (int f = 4; f > 1 && !d->tile_box; f /= 2) {
+    const int64_t units = (int64_t)p->ndm * ((p->T + (int64_t)f * kBoxTile - 1) / ((int64_t)f * kBoxTile));
+    if (units >= kBoxMinUnits) { p->box_tile = f * kBoxTile; break; }
+  }
+  p->ntile3 = (int32_t)((p->T + p->box_tile - 1) / p->box_tile);
   p->ntile2f = p->ntile2;   // the float path's stage 2 uses the same tiles (2 nw2 outputs)
 
   // ---- stage-1 work list ----------------------------------------------------
@@ -461,6 +476,7 @@ int32_t tx_plan_get_info(const tx_plan* p, tx_plan_info* info) {
   info->ring_head0 = p->head0;
   info->tile_q1 = p->q1;
   info->tile_split2 = p->split2;
+  info->tile_box = p->box_tile;
   info->workspace_bytes_compact = p->ws_bytes_compact;
   info->compact_beam_state_bytes = p->compact_beam_bytes;
   return TX_OK;

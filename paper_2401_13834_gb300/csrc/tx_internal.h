@@ -49,7 +49,8 @@ constexpr int64_t stage2_pipe_smem(int sc, int sww) {
 }
 
 // ---- matched filter ---------------------------------------------------------
-constexpr int kBoxTile = 2048;         // outputs per block of the boxcar kernel
+constexpr int kBoxTile = 2048;         // outputs per boxcar sub-tile (a unit holds 1, 2 or 4)
+constexpr int64_t kBoxMinUnits = 152 * 4 * 8;   // units a plan keeps for a full GPU before lengthening them
 constexpr int kBoxThreads = 256;
 constexpr int kMaxWidths = 32;
 constexpr int kMaxWidth = 4096;
@@ -137,7 +138,8 @@ struct tx_plan {
   int32_t sw2_i32 = 0;            // stage-2 staged elements per sub-band (int32 path)
   int32_t nsub_chunk2 = 0;        // sub-bands staged at once by stage 2
   int32_t e2w2 = 0;               // words of one stage-2 group's delays in shared memory (rounded to 4)
-  int32_t ntile3 = 0;             // boxcar tiles over [0, T)
+  int32_t box_tile = tx::kBoxTile;  // boxcar outputs per unit (a multiple of kBoxTile)
+  int32_t ntile3 = 0;             // boxcar units per DM over [0, T)
   int32_t ntile2f = 0;            // float path: stage-2 tiles over the series (those of ntile2)
   int32_t tile_f = 0, span_f = 0;  // float path: stage-1 item length and delay spread limit
   std::vector<tx::Stage1Item> items_f;  // float path stage-1 items (s, coarse DMs [kb, ke), times)

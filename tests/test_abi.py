@@ -138,6 +138,23 @@ def test_tile_knobs_reported(tx):
         assert np.array_equal(p.tables()[k], auto.tables()[k])
 
 
+def test_boxcar_unit_choice(tx):
+    """The boxcar unit grows to 4 or 2 sub-tiles of 2048 outputs only while at
+    least 4864 (DM, unit) pairs remain; an explicit length is taken as given."""
+    f = synth.channel_centres(1200.0, 1456.0, 32)
+    def plan(ndm, T, **kw):
+        return tx.Plan(f, 256e-6, np.linspace(0.0, 50.0, ndm), 4, (1, 2, 4), T, **kw)
+    assert plan(24, 3000).tile_box == 2048
+    assert plan(2432, 16384).tile_box == 8192        # 2432 DMs x 2 units
+    assert plan(1216, 16384).tile_box == 4096        # 1216 x 4
+    assert plan(1215, 16384).tile_box == 2048        # 1215 x 4 < 4864
+    assert plan(24, 3000, tile_box=8192).tile_box == 8192
+    for bad in (1000, 2047, 16384, -2048):
+        with pytest.raises(tx.TxError) as e:
+            plan(24, 3000, tile_box=bad)
+        assert e.value.code == -1
+
+
 def test_tile_q1_that_does_not_fit_is_unsupported(tx):
     wl = synth.tiny_workload(nchan=257, nsub=1, ndm=8)
     with pytest.raises(tx.TxError) as e:

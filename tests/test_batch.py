@@ -38,9 +38,9 @@ BEAMS = [
     dict(wl=dict(nchan=48, nsub=48, ndm=9, nsamp=777, group=4), output="plane", layout="ft", stats="running"),
     dict(wl=dict(nchan=257, nsub=1, ndm=20, nsamp=4099, group=32), output="cube", layout="ft"),
     dict(wl=dict(nchan=128, nsub=16, ndm=64, nsamp=5000, dm_max=400.0, tsamp=128e-6, widths=FIB),
-         output="cands", layout="tf", stats="running", snr_threshold=3.5),
+         output="cands", layout="tf", stats="running", snr_threshold=3.5, tile_box=4096),
     dict(wl=dict(nchan=96, nsub=8, ndm=24, nsamp=2048, descending=True), output="plane", layout="tf"),
-    dict(wl=None, output="cands", layout="ft", snr_threshold=6.0),   # the 256-channel small workload
+    dict(wl=None, output="cands", layout="ft", snr_threshold=6.0, tile_box=8192),   # the 256-channel small workload
     dict(wl=dict(nchan=257, nsub=1, ndm=20, nsamp=2000, group=32), output="series", layout="tf", interm="f16"),
     dict(wl=dict(nchan=128, nsub=4, ndm=40, nsamp=2500, dm_max=200.0), output="plane", layout="ft", interm="f16"),
 ]

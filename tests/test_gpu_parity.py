@@ -353,6 +353,37 @@ def test_boxcar_width_sets(tx, widths, output):
         _check_cands(got, n, snr, gamma)
 
 
+@pytest.mark.parametrize("tile_box", [4096, 8192])
+@pytest.mark.parametrize("widths", [(1, 2, 4, 8, 16, 32, 64), (1, 2, 3, 5, 8, 13, 21, 34, 55, 89)])
+@pytest.mark.parametrize("output", ["cube", "plane", "cands"])
+def test_boxcar_long_units(tx, tile_box, widths, output):
+    """Boxcar units of 2 or 4 sub-tiles of 2048 outputs: T = 11192 gives full
+    units and a last one of 3000 outputs (one full sub-tile and a ragged one);
+    widths 1, 2 and multiples of 4 take the four-output test, the Fibonacci set
+    the one-output test of full sub-tiles."""
+    wl = synth.tiny_workload(nchan=32, nsub=4, ndm=5, nsamp=11192, widths=widths)
+    gamma = 3.0
+    kw = dict(snr_threshold=gamma, max_cands=1 << 17) if output == "cands" else {}
+    plan = make_plan(tx, wl, output=output, tile_box=tile_box, **kw)
+    assert plan.tile_box == tile_box
+    op = oracle_plan(wl)
+    pulses = [synth.Pulse(dm=30.0, t_arr=float(t), fwhm=12.0, amp=9.0) for t in (1500, 5000, 9000, 10800)]
+    X = synth.make_spectrum(wl, plan.overlap + wl.nsamp, pulses, seed=12)
+    (out, nc, _), = run_blocks(tx, plan, X)[0]
+    snr, _ = _oracle_snr(X, op, wl.nsamp)
+    if output == "cube":
+        check_snr(tx.cube_view(plan, out).cpu().numpy(), snr)
+    elif output == "plane":
+        s, w = tx.plane_view(plan, out)
+        _check_plane(s.cpu().numpy(), w.cpu().numpy(), snr)
+    else:
+        got, n = tx.cands_view(plan, out, nc)
+        assert 0 < n < (1 << 17)
+        t = got["t"][:n]
+        assert (t < 2048).any() and ((t >= 2048) & (t < tile_box)).any() and (t >= 10240).any()
+        _check_cands(got, n, snr, gamma)
+
+
 @pytest.mark.parametrize("q1", [32, 64, 128, 256])
 @pytest.mark.parametrize("group,split,want", [
     (4, 0, 4), (8, 0, 2), (16, 0, 1),          # the pipelined stage 2: 4, 2, 1 consumer warps per DM

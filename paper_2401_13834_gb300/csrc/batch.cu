@@ -78,6 +78,7 @@ struct BatchLaunch {
   int grid = 0, threads = 0, smem = 0;
   int nmem = 0, nunits = 0;                  // member beams, work units (stage 1: the plans' items)
   int64_t off = 0, mem = 0;                  // offsets of the unit-offset / member arrays in the table
+  int64_t ctr = 0;                           // stage 1: offset of the launch's item counter in the table
   int layout = 0;                            // stage 1 mL, stage 2 slot words, boxcar wmaxL
   int aux = 0;                               // stage 2 words of a group's delays (or chunk sub-bands), boxcar tileL
 };
@@ -265,6 +266,8 @@ int build_batch(tx_batch* B, int64_t budget) {
       if (L.smem > kSmemMax) { set_error("stage-1 shared memory for %d channels per sub-band exceeds the limit", mL); return TX_ERR_UNSUPPORTED; }
       L.threads = kStage1Warps * 32;
       L.grid = std::min(L.nunits, nsm);
+      L.ctr = (int64_t)tab.size();
+      tab.push_back(0);
       if (L.nunits > 0) B->launches.push_back(L);
     }
     // ---- stage 2, one launch per (warp split, sub-bands per chunk, block size) -------
@@ -422,14 +425,16 @@ int enqueue(tx_batch* B, const BeamArgs* h_src, cudaStream_t st) {
         k_offsets<SlotArgs><<<L.grid, L.threads, 0, st>>>(src, off, mem, L.nmem, L.nunits);
         break;
       case kStage1: {
+        int32_t* ictr = B->d_tab + L.ctr;
+        TX_CUDA(cudaMemsetAsync(ictr, 0, sizeof(int32_t), st));
 #define TX_B1(Q)                                                                                                \
   do {                                                                                                           \
     if (L.half)                                                                                                  \
       k_stage1<Q, uint16_t, SlotArgs, true><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits,   \
-                                                                               L.layout, 1u);                    \
+                                                                               L.layout, 1u, ictr);              \
     else                                                                                                         \
       k_stage1<Q, uint16_t, SlotArgs><<<L.grid, L.threads, L.smem, st>>>(src, off, mem, L.nmem, L.nunits,         \
-                                                                         L.layout, 1u);                          \
+                                                                         L.layout, 1u, ictr);                    \
   } while (0)
         switch (L.q1) {
           case 256: TX_B1(256); break;

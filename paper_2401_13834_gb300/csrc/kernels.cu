@@ -115,18 +115,21 @@ int do_upload(tx_plan* p) {
 }
 
 template <int Q, typename PT, bool HALF = false>
-void launch_stage1_t(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
+void launch_stage1_t(const tx_plan* p, const BeamArgs& a, int32_t* ictr, cudaStream_t st) {
   const int nitems = (int)p->items1.size();
   const int grid = std::min(nitems, std::max(p->dev.num_sms, 1));
   k_stage1<Q, PT, OneBeam, HALF><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
-      OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u);
+      OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u, ictr);
 }
 
+// stage 1 with its item counter `ictr` (zeroed here first)
 template <int Q>
-void launch_stage1(const tx_plan* p, const BeamArgs& a, cudaStream_t st) {
-  if (p->interm == TX_INTERM_F16) launch_stage1_t<Q, uint16_t, true>(p, a, st);
-  else if (p->interm == TX_INTERM_U16) launch_stage1_t<Q, uint16_t>(p, a, st);
-  else launch_stage1_t<Q, int32_t>(p, a, st);
+int launch_stage1(const tx_plan* p, const BeamArgs& a, int32_t* ictr, cudaStream_t st) {
+  TX_CUDA(cudaMemsetAsync(ictr, 0, sizeof(int32_t), st));
+  if (p->interm == TX_INTERM_F16) launch_stage1_t<Q, uint16_t, true>(p, a, ictr, st);
+  else if (p->interm == TX_INTERM_U16) launch_stage1_t<Q, uint16_t>(p, a, ictr, st);
+  else launch_stage1_t<Q, int32_t>(p, a, ictr, st);
+  return TX_OK;
 }
 
 int check_beam(const tx_plan* p, const tx_beam* b) {
@@ -438,12 +441,14 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   }
 
   // stage 1
+  int32_t* ictr = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(d_workspace) + p->ws_ctr);
   switch (p->q1) {
-    case 256: launch_stage1<256>(p, a, st); break;
-    case 128: launch_stage1<128>(p, a, st); break;
-    case 64: launch_stage1<64>(p, a, st); break;
-    default: launch_stage1<32>(p, a, st); break;
+    case 256: rc = launch_stage1<256>(p, a, ictr, st); break;
+    case 128: rc = launch_stage1<128>(p, a, ictr, st); break;
+    case 64: rc = launch_stage1<64>(p, a, ictr, st); break;
+    default: rc = launch_stage1<32>(p, a, ictr, st); break;
   }
+  if (rc) return rc;
   TX_CUDA(cudaGetLastError());
   TX_MARK(2);
 
@@ -783,7 +788,8 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   const size_t b_P = align256((size_t)p->nk * p->nsub * p->Pp * 2);
   const size_t b_part = align256((size_t)p->ndm * p->ntile2 * (p->pipe2 ? p->split2 : 1) * 16);
   const size_t b_tab2 = align256(p->tab2.size() * 4);
-  const size_t need = b_items + b_d1 + b_abase + b_e2 + b_P + b_part + b_tab2;
+  const size_t b_ctr = 256;   // the stage-1 item counter
+  const size_t need = b_items + b_d1 + b_abase + b_e2 + b_P + b_part + b_tab2 + b_ctr;
   if (need > kNoAllocScratchBytes) {
     set_error("this plan needs %zu bytes of scratch; the static scratch of tx_dedisperse_noalloc holds %zu",
               need, kNoAllocScratchBytes);
@@ -803,6 +809,7 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   uint16_t* P = reinterpret_cast<uint16_t*>(base + b_items + b_d1 + b_abase + b_e2);
   longlong2* part = reinterpret_cast<longlong2*>(base + b_items + b_d1 + b_abase + b_e2 + b_P);
   int32_t* tab2 = reinterpret_cast<int32_t*>(base + b_items + b_d1 + b_abase + b_e2 + b_P + b_part);
+  int32_t* ictr = reinterpret_cast<int32_t*>(base + b_items + b_d1 + b_abase + b_e2 + b_P + b_part + b_tab2);
   cudaStream_t st = (cudaStream_t)stream;
   TX_CUDA(cudaMemcpyAsync(items, p->items1.data(), p->items1.size() * sizeof(Stage1Item), cudaMemcpyHostToDevice, st));
   TX_CUDA(cudaMemcpyAsync(d1, p->d1.data(), p->d1.size() * 4, cudaMemcpyHostToDevice, st));
@@ -845,11 +852,12 @@ int32_t tx_dedisperse_noalloc(const tx_plan* p, const uint8_t* d_x, int64_t ld, 
   const int nitems = (int)p->items1.size();
   const int smem1 = (int)stage1_smem_bytes(p->m, p->q1);
   const int grid1 = std::min(nitems, std::max(nsm, 1));
+  TX_CUDA(cudaMemsetAsync(ictr, 0, sizeof(int32_t), st));
 #define TX_NA_S1(Q)                                                                                               \
   do {                                                                                                            \
     TX_CUDA(raise_smem_limit((const void*)k_stage1<Q, uint16_t, OneBeam>, smem1));                           \
     k_stage1<Q, uint16_t, OneBeam><<<grid1, kStage1Warps * 32, smem1, st>>>(OneBeam{a}, nullptr, nullptr, 1, nitems, \
-                                                                            p->m, 1u);                        \
+                                                                            p->m, 1u, ictr);                  \
   } while (0)
   switch (p->q1) {
     case 256: TX_NA_S1(256); break;

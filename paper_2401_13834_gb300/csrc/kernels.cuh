@@ -611,8 +611,9 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 // or 8 warps. Shared memory is laid out for mL channels (the largest sub-band
 // of the launch), so an item's prefetch never overlaps the previous item's
 // staged words or table. Nothing an item needs is fetched by a dependent
-// global load between barriers: a block's k-th item is blockIdx.x + k *
-// gridDim.x; its descriptor is copied to shared memory two items ahead and
+// global load between barriers: a block's first item is blockIdx.x and it
+// takes each later one from a counter two items ahead (blocks that drew cheap
+// items take more); an item's descriptor is copied to shared memory two items ahead and
 // its channels' delays d1[kb][c] one item ahead (both with cp.async), so that
 // the next item's windows are issued from shared memory; the offset table
 // and the P-row bases of the item's coarse DMs come precomputed with the
@@ -621,7 +622,7 @@ __device__ __forceinline__ void stage1_sum(const uint32_t* __restrict__ S, const
 template <int Q, typename PT, typename Src, bool HALF = false>
 __global__ void __launch_bounds__(kStage1Warps * 32, 1)
 k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nitems,
-         int mL, uint32_t unit) {
+         int mL, uint32_t unit, int32_t* __restrict__ ictr) {
   extern __shared__ __align__(16) uint8_t smem1[];
   constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
@@ -636,6 +637,7 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   int32_t* hsub = wrow + 2 * TSL;  // [2] the sub-band's offset of items k, k+1 (half intermediates)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ __align__(8) uint64_t barr;   // completion of the bulk copies of the raw windows
+  __shared__ int32_t uq[3];                // the item of each descriptor slot
   uint32_t rphase = 0u;
 
   MemberCursor cur_c, cur_n, cur_f;  // items being summed / next (prefetched and announced) / two ahead
@@ -677,13 +679,13 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     const Stage1Item& it = iq[sl];
     const int R = (int)a.R;
     if (lane == 0) {
+      fence_proxy_async();   // the transform's reads of raw (ordered by the barrier) before the copies
       for (int c = warp; c < a.m; c += kStage1Warps) {
         int64_t p = a.start + it.tau0 + wrow[w * TSL + c];
         while (p >= R) p -= R;
         const int pa = (int)p & ~15;
         const uint8_t* row = a.ring + (size_t)(it.s * a.m + c) * R;
         uint8_t* dst = raw + (size_t)c * RB;
-        fence_proxy_async();
         const int first = min(RB, R - pa);
         bulk_g2s(dst, row + pa, (uint32_t)first, &barr);
         if (first < RB) bulk_g2s(dst + first, row, (uint32_t)(RB - first), &barr);
@@ -698,15 +700,29 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     }
   };
 
+  // A block's first item is blockIdx.x; it takes each later one from the
+  // launch's counter (zeroed before the launch) two items ahead, so blocks
+  // that drew cheap items take more of them. Warp 0 asks (lane 0) and copies
+  // the descriptor; the rest of the block reads the index from uq.
   const int G = gridDim.x;
   const int u0 = blockIdx.x;
   if (u0 >= nitems) return;
+  auto take = [&](int sl, bool more) {   // warp 0: the next item into slot sl
+    int v = nitems;
+    if (more) {
+      if (lane == 0) v = G + atomicAdd(ictr, 1);
+      v = __shfl_sync(0xffffffffu, v, 0);
+    }
+    if (lane == 0) uq[sl] = v;
+    fetch_item(v, sl);
+  };
   if (threadIdx.x == 0) {
     mbar_init(&barr, 1);
     fence_mbar_init();
+    uq[0] = u0;
   }
   fetch_item(u0, 0);
-  fetch_item(u0 + G, 1);
+  if (warp == 0) take(1, true);
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
@@ -716,8 +732,9 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   announce(u0);
   __syncthreads();
   issue(u0, 0, 0);
-  for (int k = 0, u = u0; u < nitems; ++k, u += G) {
+  for (int k = 0, u = u0; u < nitems; ++k, u = uq[k % 3]) {
     const int sl = k % 3, sl1 = (k + 1) % 3, sl2 = (k + 2) % 3;
+    const int un = uq[sl1];   // the next item (taken one item earlier)
     int lu;
     const BeamArgs a = locate(cur_c, u, lu);
     cp_async_wait_all();
@@ -747,8 +764,8 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       const int32_t* src_b = src_t + nkk * TS;
       for (int q = threadIdx.x; q < (nkk + 3) / 4; q += blockDim.x) cp_async16(tabase + 4 * q, src_b + 4 * q);
     }
-    fetch_item(u + 2 * G, sl2);
-    fetch_row(u + G, sl1, (k + 1) & 1);
+    if (warp == 0) take(sl2, un < nitems);
+    fetch_row(un, sl1, (k + 1) & 1);
     cp_async_commit();
     // raw -> four-quarter words; lane g builds words 4g .. 4g + 3 of a channel
     const int n4 = (Q + it.span + 15 + 3) >> 2;
@@ -784,9 +801,9 @@ k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       for (int kk = threadIdx.x; kk < nkk; kk += blockDim.x) tabase[kk] = a.abase[(size_t)(it.kb + kk) * a.nsub + it.s];
     }
     cp_async_wait_all();
-    announce(u + G);
+    announce(un);
     __syncthreads();
-    if (u + G < nitems) issue(u + G, sl1, (k + 1) & 1);
+    if (un < nitems) issue(un, sl1, (k + 1) & 1);
 
     const int off = HALF ? hsub[k & 1] : 0;   // the sub-band's offset (half intermediates)
     // tasks: (coarse DM, part of the tile); split the tile when coarse DMs are few

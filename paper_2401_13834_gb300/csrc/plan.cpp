@@ -403,6 +403,8 @@ static int build(tx_plan* p, const tx_plan_desc* d) {
   p->ws_const = off; off = round_up(off + std::max<int64_t>((int64_t)ndm * p->nw * (int64_t)sizeof(SnrConst), fpath ? (int64_t)ndm * 16 : 0), 256);
   // half intermediates: per-sub-band offsets; float path: per-channel sums (2 x u64), then (mu, w) as float pairs
   p->ws_hoff = off; off = round_up(off + (p->interm == TX_INTERM_F16 ? (int64_t)(nsub + 1) * 4 : fpath ? (int64_t)nchan * 24 : 0), 256);
+  // the stage-1 item counter of an execute
+  p->ws_ctr = off; off = round_up(off + 4, 256);
   p->ws_bytes = off;
   switch (p->output) {
     case TX_OUT_CANDS: p->out_bytes = p->max_cands * (int64_t)sizeof(tx_cand); break;

@@ -159,7 +159,7 @@ struct tx_plan {
   std::vector<int32_t> tab2;
 
   // ---- workspace carve-up (bytes) -------------------------------------------
-  int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_hoff = 0, ws_bytes = 0;
+  int64_t ws_P = 0, ws_D = 0, ws_part = 0, ws_const = 0, ws_hoff = 0, ws_ctr = 0, ws_bytes = 0;
   int64_t out_bytes = 0, beam_bytes = 0, export_bytes = 0;
   // compact beams: the tail lives in [nchan][tail_pitch] (samples at
   // tail_pad.. so that they share the ring's 16-byte phase); an execute

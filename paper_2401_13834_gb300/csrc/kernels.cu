@@ -154,7 +154,7 @@ int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64
     const int64_t len = std::min(n - done, R - pos);
     if (p->layout == TX_LAYOUT_TF) {
       const int vec = (p->nchan % 16 == 0) && (pos % 16 == 0) && (((uintptr_t)src & 15) == 0);
-      dim3 grid((unsigned)((len + 63) / 64), (unsigned)((p->nchan + 63) / 64));
+      dim3 grid((unsigned)((len + 64 * kIngestTiles - 1) / (64 * kIngestTiles)), (unsigned)((p->nchan + 63) / 64));
       k_ingest_tf<<<grid, 256, 0, st>>>(src, done, len, p->nchan, ring, R, pos, vec);
     } else {
       const int vec = (n % 16 == 0) && (done % 16 == 0) && (len % 16 == 0) && (pos % 16 == 0) &&
@@ -303,7 +303,7 @@ int32_t tx_beam_prime(const tx_plan* p, tx_beam* b, const uint8_t* d_tail, void*
     uint8_t* t = b->tail + p->tail_pad;
     if (p->layout == TX_LAYOUT_TF) {
       const int vec = (p->tail_pad % 16 == 0) && (p->nchan % 16 == 0) && (((uintptr_t)d_tail & 15) == 0);
-      dim3 grid((unsigned)((p->L + 63) / 64), (unsigned)((p->nchan + 63) / 64));
+      dim3 grid((unsigned)((p->L + 64 * kIngestTiles - 1) / (64 * kIngestTiles)), (unsigned)((p->nchan + 63) / 64));
       k_ingest_tf<<<grid, 256, 0, st>>>(d_tail, 0, p->L, p->nchan, b->tail, p->tail_pitch, p->tail_pad, vec);
       TX_CUDA(cudaGetLastError());
     } else {

@@ -214,6 +214,8 @@ __global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t src_pitch, 
   }
 }
 
+constexpr int kIngestTiles = 4;
+
 // This thread's 16 bytes of the 64-time x 64-channel byte tile (times t0..,
 // channels c0..) of a time-major block [t][nchan]: time t0 + tid / 4,
 // channels c0 + 16 (tid % 4) ..; zero outside the block. 256 threads.
@@ -253,28 +255,38 @@ __device__ __forceinline__ void tf_column(const uint8_t (*tile)[80], int cc, int
 }
 
 // Time-major block rows [t][nchan], t in [t_off, t_off + n) -> ring[c][dst_off + t - t_off],
-// through a 64-time x 64-channel byte tile. vec: 16-byte loads and stores
-// (nchan, dst_off and the source all 16-byte aligned).
+// through 64-time x 64-channel byte tiles, kIngestTiles consecutive ones per
+// block (blockIdx.x: times 64 kIngestTiles blockIdx.x ..; blockIdx.y: channels
+// 64 blockIdx.y ..). vec: 16-byte loads and stores (nchan, dst_off and the
+// source all 16-byte aligned).
 __global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ src, int64_t t_off, int64_t n,
                                                    int nchan, uint8_t* __restrict__ ring, int64_t R,
                                                    int64_t dst_off, int vec) {
-  __shared__ __align__(16) uint8_t tile[64][80];
-  const int64_t t0 = (int64_t)blockIdx.x * 64;
+  __shared__ __align__(16) uint8_t tiles[kIngestTiles][64][80];
   const int c0 = blockIdx.y * 64;
-  tf_load_tile(tile, src + t_off * nchan, t0, n, c0, nchan, vec);
+  uint4 vv[kIngestTiles];   // all of the block's loads in flight at once
+#pragma unroll
+  for (int i = 0; i < kIngestTiles; ++i)
+    vv[i] = tf_tile_chunk(src + t_off * nchan, ((int64_t)blockIdx.x * kIngestTiles + i) * 64, n, c0, nchan, vec);
+#pragma unroll
+  for (int i = 0; i < kIngestTiles; ++i)
+    *reinterpret_cast<uint4*>(&tiles[i][threadIdx.x >> 2][16 * (threadIdx.x & 3)]) = vv[i];
   __syncthreads();
   const int cc = threadIdx.x & 63, pq = threadIdx.x >> 6;
   const int c = c0 + cc;
-  if (c < nchan) {
+  if (c >= nchan) return;
+#pragma unroll 1
+  for (int i = 0; i < kIngestTiles; ++i) {
+    const int64_t t0 = ((int64_t)blockIdx.x * kIngestTiles + i) * 64;
     uint32_t w[4];
-    tf_column(tile, cc, pq, w);
+    tf_column(tiles[i], cc, pq, w);
     const int64_t t = t0 + 16 * pq;
     uint8_t* dp = ring + (int64_t)c * R + dst_off + t;
     if (vec && t + 16 <= n) {
       *reinterpret_cast<uint4*>(dp) = make_uint4(w[0], w[1], w[2], w[3]);
     } else {
-      for (int i = 0; i < 16; ++i)
-        if (t + i < n) dp[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+      for (int j = 0; j < 16; ++j)
+        if (t + j < n) dp[j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
     }
   }
 }

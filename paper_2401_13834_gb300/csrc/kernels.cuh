@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1704,6 +1705,79 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     }
     __syncthreads();
 
+    // candidates of a full run of quads, widths 1, 2 and multiples of 4: each
+    // thread tests the four outputs 4q .. 4q + 3 of quads q = tid + 256 r
+    // (r < QR) from aligned 16-byte loads of Cs (its own quad and the next for
+    // widths 1, 2 and 4, one more per wider width); hits go to a bit mask and
+    // the rare hits are written after, once per warp that has any
+    auto vec_cands = [&](const uint32_t* Cs, int64_t ts, auto qr) {
+      constexpr int QR = decltype(qr)::value;
+      const uint4* C4 = reinterpret_cast<const uint4*>(Cs);
+      uint32_t mask = 0;
+#pragma unroll
+      for (int r = 0; r < QR; ++r) {
+        const int q = threadIdx.x + r * kBoxThreads;
+        const uint4 cl = C4[q], nx = C4[q + 1];
+        int32_t m0 = (int32_t)(cl.y - cl.x) - thr[0], m1 = (int32_t)(cl.z - cl.y) - thr[0];
+        int32_t m2 = (int32_t)(cl.w - cl.z) - thr[0], m3 = (int32_t)(nx.x - cl.w) - thr[0];
+        m0 = max(m0, (int32_t)(cl.z - cl.x) - thr[1]);
+        m1 = max(m1, (int32_t)(cl.w - cl.y) - thr[1]);
+        m2 = max(m2, (int32_t)(nx.x - cl.z) - thr[1]);
+        m3 = max(m3, (int32_t)(nx.y - cl.w) - thr[1]);
+#pragma unroll
+        for (int w = 2; w < NR; ++w) {
+          const uint4 cw = C4[q + (Wr[w] >> 2)];
+          m0 = max(m0, (int32_t)(cw.x - cl.x) - thr[w]);
+          m1 = max(m1, (int32_t)(cw.y - cl.y) - thr[w]);
+          m2 = max(m2, (int32_t)(cw.z - cl.z) - thr[w]);
+          m3 = max(m3, (int32_t)(cw.w - cl.w) - thr[w]);
+        }
+        mask |= ((uint32_t)(m0 >= 0) | ((uint32_t)(m1 >= 0) << 1) | ((uint32_t)(m2 >= 0) << 2) |
+                 ((uint32_t)(m3 >= 0) << 3)) << (4 * r);
+      }
+      if (__any_sync(0xffffffffu, mask != 0u)) {
+        for (int r = 0; r < 4 * QR; ++r) {
+          const int i = 4 * (threadIdx.x + (r >> 2) * kBoxThreads) + (r & 3);
+          const bool hit = (mask >> r) & 1u;
+          const unsigned hits = __ballot_sync(0xffffffffu, hit);
+          if (!hits) continue;
+          float best = -INFINITY;
+          int bw = 0;
+          if (hit) {
+            const uint32_t* Ci = Cs + i;
+            const uint32_t cl = Ci[0];
+            for (int w = 0; w < NR; ++w) {
+              const SnrConst c = cst[w];
+              const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
+              if (sv > best) { best = sv; bw = w; }
+            }
+          }
+          const int leader = __ffs(hits) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (hit) {
+            const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
+            if (idx < (unsigned long long)a.max_cands) {
+              tx_cand rec;
+              rec.dm_index = d;
+              rec.t = (int32_t)(ts + i);
+              rec.w_index = bw;
+              rec.snr = best;
+              a.cands[idx] = rec;
+            }
+          }
+        }
+      }
+    };
+    if constexpr (NWT > 0 && MODE == TX_OUT_CANDS) {
+      if (n == a.box_tile && a.box_vec) {   // a full unit in one pass
+        if (n == 4 * kBoxTile) vec_cands(C, t0, std::integral_constant<int, 4 * kBoxTile / 4 / kBoxThreads>{});
+        else if (n == 2 * kBoxTile) vec_cands(C, t0, std::integral_constant<int, 2 * kBoxTile / 4 / kBoxThreads>{});
+        else vec_cands(C, t0, std::integral_constant<int, kBoxTile / 4 / kBoxThreads>{});
+        continue;
+      }
+    }
     // the unit in sub-tiles of kBoxTile outputs: full ones take the unrolled tests
     for (int s0 = 0; s0 < n; s0 += kBoxTile) {
       const int ns = min(kBoxTile, n - s0);
@@ -1711,68 +1785,7 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
       const int64_t ts = t0 + s0;
       if constexpr (NWT > 0 && MODE == TX_OUT_CANDS) {
         if (ns == kBoxTile && a.box_vec) {
-          // full tile, widths 1, 2 and multiples of 4: each thread tests the
-          // four outputs 4q .. 4q + 3 of quads q = tid + 256 r from aligned
-          // 16-byte loads of C (its own quad and the next for widths 1, 2 and
-          // 4, one more per wider width); hits go to a bit mask as below
-          constexpr int QR = kBoxTile / 4 / kBoxThreads;
-          const uint4* C4 = reinterpret_cast<const uint4*>(Cs);
-          uint32_t mask = 0;
-  #pragma unroll
-          for (int r = 0; r < QR; ++r) {
-            const int q = threadIdx.x + r * kBoxThreads;
-            const uint4 cl = C4[q], nx = C4[q + 1];
-            int32_t m0 = (int32_t)(cl.y - cl.x) - thr[0], m1 = (int32_t)(cl.z - cl.y) - thr[0];
-            int32_t m2 = (int32_t)(cl.w - cl.z) - thr[0], m3 = (int32_t)(nx.x - cl.w) - thr[0];
-            m0 = max(m0, (int32_t)(cl.z - cl.x) - thr[1]);
-            m1 = max(m1, (int32_t)(cl.w - cl.y) - thr[1]);
-            m2 = max(m2, (int32_t)(nx.x - cl.z) - thr[1]);
-            m3 = max(m3, (int32_t)(nx.y - cl.w) - thr[1]);
-  #pragma unroll
-            for (int w = 2; w < NR; ++w) {
-              const uint4 cw = C4[q + (Wr[w] >> 2)];
-              m0 = max(m0, (int32_t)(cw.x - cl.x) - thr[w]);
-              m1 = max(m1, (int32_t)(cw.y - cl.y) - thr[w]);
-              m2 = max(m2, (int32_t)(cw.z - cl.z) - thr[w]);
-              m3 = max(m3, (int32_t)(cw.w - cl.w) - thr[w]);
-            }
-            mask |= ((uint32_t)(m0 >= 0) | ((uint32_t)(m1 >= 0) << 1) | ((uint32_t)(m2 >= 0) << 2) |
-                     ((uint32_t)(m3 >= 0) << 3)) << (4 * r);
-          }
-          if (__any_sync(0xffffffffu, mask != 0u)) {
-            for (int r = 0; r < 4 * QR; ++r) {
-              const int i = 4 * (threadIdx.x + (r >> 2) * kBoxThreads) + (r & 3);
-              const bool hit = (mask >> r) & 1u;
-              const unsigned hits = __ballot_sync(0xffffffffu, hit);
-              if (!hits) continue;
-              float best = -INFINITY;
-              int bw = 0;
-              if (hit) {
-                const uint32_t* Ci = Cs + i;
-                const uint32_t cl = Ci[0];
-                for (int w = 0; w < NR; ++w) {
-                  const SnrConst c = cst[w];
-                  const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
-                  if (sv > best) { best = sv; bw = w; }
-                }
-              }
-              const int leader = __ffs(hits) - 1;
-              unsigned long long base = 0;
-              if (lane == leader) base = atomicAdd(a.ncand, (unsigned long long)__popc(hits));
-              base = __shfl_sync(0xffffffffu, base, leader);
-              if (hit) {
-                const unsigned long long idx = base + __popc(hits & ((1u << lane) - 1u));
-                if (idx < (unsigned long long)a.max_cands) {
-                  tx_cand rec;
-                  rec.dm_index = d;
-                  rec.t = (int32_t)(ts + i);
-                  rec.w_index = bw;
-                  rec.snr = best;
-                  a.cands[idx] = rec;
-                }
-              }
-            }
-          }
+          vec_cands(Cs, ts, std::integral_constant<int, kBoxTile / 4 / kBoxThreads>{});
           continue;
         }
         if (ns == kBoxTile) {

@@ -273,10 +273,21 @@ def onchip_peaks(tx, peaks):
             "sm_max_mhz": mhz, "frac_of_derived": measured / derived}
 
 
-def alu_peak(phase, onchip):
+def bytes_per_add(phase, interm):
+    """Shared-memory bytes a de-dispersion stage reads per sample-add: stage 1
+    one byte (uint8 samples, four per 32-bit word), stage 2 the intermediates'
+    width; the float path holds float32 samples and sums in both stages."""
+    if interm == "f32":
+        return 4.0
+    if phase == "stage2" and interm == "i32":
+        return 4.0
+    return BYTES_PER_ADD[phase]
+
+
+def alu_peak(phase, onchip, interm="u16"):
     """On-chip peak of a de-dispersion stage in sample-adds/s: the measured
     shared-memory read bandwidth over the stage's bytes per sample-add."""
-    return onchip["smem_bytes_per_s_measured"] / BYTES_PER_ADD[phase]
+    return onchip["smem_bytes_per_s_measured"] / bytes_per_add(phase, interm)
 
 
 def block_hbm_bytes(plan, ncand_avg):
@@ -660,21 +671,27 @@ def run_ours(args):
                 entry.update({"achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": ach / peaks["hbm_gbs"], "algorithmic": amount})
             else:
-                pk = alu_peak(name, onchip) / 1e12
+                pk = alu_peak(name, onchip, plan.interm) / 1e12
                 ach = amount / (avg / 1e3) / 1e12 if avg > 0 else 0.0
-                entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": amount})
+                entry.update({"achieved": ach, "peak": pk, "unit": "Tadd/s", "frac": ach / pk, "algorithmic": amount,
+                              "bytes_per_add": bytes_per_add(name, plan.interm)})
             phases[name] = entry
         dom = max(phase_ms, key=phase_ms.get)
-        kernel_of = {"ingest": "k_ingest_tf", "stage1": "k_stage1", "stage2": "k_stage2_pipe" if plan.tile_split2 and
-                     plan.group <= 16 and plan.interm in ("u16", "f16") else "k_stage2_u16", "stats": "k_stats",
-                     "boxcar": "k_boxcar"}
+        if plan.interm == "f32":
+            kernel_of = {"ingest": "k_norm_ingest", "stage1": "k_stage1_f32", "stage2": "k_stage2_f32",
+                         "stats": "k_stats_f32", "boxcar": "k_boxcar_f32"}
+        else:
+            kernel_of = {"ingest": "k_ingest_tf", "stage1": "k_stage1", "stage2": "k_stage2_pipe" if plan.tile_split2
+                         and plan.group <= 16 and plan.interm in ("u16", "f16") else
+                         ("k_stage2_u16" if plan.interm in ("u16", "f16") else "k_stage2_i32"),
+                         "stats": "k_stats", "boxcar": "k_boxcar"}
         d = phases[dom]
         roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": profiled_traffic(kernel_of[dom], wl.name), "kernel": kernel_of[dom],
                 "peak_source": (f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
                                 "measured: shared-memory read bandwidth of this GPU (tx_measure_smem_bandwidth, "
                                 f"{onchip['smem_bytes_per_s_measured'] / 1e12:.2f} TB/s), "
-                                f"{'1' if dom == 'stage1' else '2'} B per sample-add")}
+                                f"{bytes_per_add(dom, plan.interm):g} B per sample-add")}
 
         def block_fraction(p, ms, ncand_avg):
             counted, extra = block_hbm_bytes(p, ncand_avg)
@@ -952,11 +969,12 @@ def run_batched(args):
         dom = max(phase_ms, key=phase_ms.get)
         d = phases[dom]
         roof = {"bound": d["bound"], "achieved": d.get("achieved"), "peak": d.get("peak"), "unit": d.get("unit"),
-                "frac": d.get("frac"), "traffic": None, "kernel": {"stage1": "k_stage1", "stage2": "k_stage2_u16",
+                "frac": d.get("frac"), "traffic": None, "kernel": {"stage1": "k_stage1", "stage2": "k_stage2_pipe / k_stage2_u16",
                                                                       "boxcar": "k_boxcar", "ingest": "k_ingest_batch",
                                                                       "stats": "k_stats"}[dom],
                 "peak_source": (f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
-                                "derived: 152 SMs x shared-memory port 128 B/clk x 2.07 GHz, "
+                                "measured: shared-memory read bandwidth of this GPU (tx_measure_smem_bandwidth, "
+                                f"{onchip['smem_bytes_per_s_measured'] / 1e12:.2f} TB/s), "
                                 f"{'1' if dom == 'stage1' else '2'} B per sample-add"),
                 "phase_times_from": f"{pn} steps of a TX_BATCH_PROFILE batch (direct launches, events per launch)"}
         cpu = None

@@ -122,10 +122,9 @@ void launch_stage1_t(const tx_plan* p, const BeamArgs& a, int32_t* ictr, cudaStr
       OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u, ictr);
 }
 
-// stage 1 with its item counter `ictr` (zeroed here first)
+// stage 1 with its item counter `ictr` (zeroed before, by the ingest)
 template <int Q>
 int launch_stage1(const tx_plan* p, const BeamArgs& a, int32_t* ictr, cudaStream_t st) {
-  TX_CUDA(cudaMemsetAsync(ictr, 0, sizeof(int32_t), st));
   if (p->interm == TX_INTERM_F16) launch_stage1_t<Q, uint16_t, true>(p, a, ictr, st);
   else if (p->interm == TX_INTERM_U16) launch_stage1_t<Q, uint16_t>(p, a, ictr, st);
   else launch_stage1_t<Q, int32_t>(p, a, ictr, st);
@@ -144,8 +143,10 @@ int check_beam(const tx_plan* p, const tx_beam* b) {
 int64_t mod(int64_t a, int64_t r) { return ((a % r) + r) % r; }
 
 // Writes n samples (plan layout, rows of n samples for FT) into the ring at
-// physical positions [pos, pos + n) mod R, splitting at the wrap.
-int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64_t pos, cudaStream_t st) {
+// physical positions [pos, pos + n) mod R, splitting at the wrap; zeroes
+// *zero on the way (when given).
+int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64_t pos, cudaStream_t st,
+           int32_t* zero = nullptr) {
   if (n <= 0) return TX_OK;
   const int64_t R = p->R;
   int64_t done = 0;
@@ -155,12 +156,12 @@ int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64
     if (p->layout == TX_LAYOUT_TF) {
       const int vec = (p->nchan % 16 == 0) && (pos % 16 == 0) && (((uintptr_t)src & 15) == 0);
       dim3 grid((unsigned)((len + 64 * kIngestTiles - 1) / (64 * kIngestTiles)), (unsigned)((p->nchan + 63) / 64));
-      k_ingest_tf<<<grid, 256, 0, st>>>(src, done, len, p->nchan, ring, R, pos, vec);
+      k_ingest_tf<<<grid, 256, 0, st>>>(src, done, len, p->nchan, ring, R, pos, vec, zero);
     } else {
       const int vec = (n % 16 == 0) && (done % 16 == 0) && (len % 16 == 0) && (pos % 16 == 0) &&
                       (((uintptr_t)src & 15) == 0);
       dim3 grid((unsigned)std::min<int64_t>((len + 4095) / 4096, 64), (unsigned)p->nchan);
-      k_ingest_ft<<<grid, 256, 0, st>>>(src, n, done, len, ring, R, pos, vec);
+      k_ingest_ft<<<grid, 256, 0, st>>>(src, n, done, len, ring, R, pos, vec, zero);
     }
     TX_CUDA(cudaGetLastError());
     done += len;
@@ -304,7 +305,8 @@ int32_t tx_beam_prime(const tx_plan* p, tx_beam* b, const uint8_t* d_tail, void*
     if (p->layout == TX_LAYOUT_TF) {
       const int vec = (p->tail_pad % 16 == 0) && (p->nchan % 16 == 0) && (((uintptr_t)d_tail & 15) == 0);
       dim3 grid((unsigned)((p->L + 64 * kIngestTiles - 1) / (64 * kIngestTiles)), (unsigned)((p->nchan + 63) / 64));
-      k_ingest_tf<<<grid, 256, 0, st>>>(d_tail, 0, p->L, p->nchan, b->tail, p->tail_pitch, p->tail_pad, vec);
+      k_ingest_tf<<<grid, 256, 0, st>>>(d_tail, 0, p->L, p->nchan, b->tail, p->tail_pitch, p->tail_pad, vec,
+                                        nullptr);
       TX_CUDA(cudaGetLastError());
     } else {
       TX_CUDA(cudaMemcpy2DAsync(t, (size_t)p->tail_pitch, d_tail, (size_t)p->L, (size_t)p->L, (size_t)p->nchan,
@@ -416,17 +418,19 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   // Sec. 2.3 data flow: the block lands behind the carried tail (steps 1, 2, 4)
   const int64_t start = mod(b->head - p->L, p->R);
   const BeamArgs a = make_args(p, b, d_block, d_out, d_ncand, d_workspace, b->head, start);
+  // the stage-1 item counter, zeroed by the ingest
+  int32_t* ictr = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(d_workspace) + p->ws_ctr);
   if (b->compact) {
     // tail into the borrowed ring, the block behind it, the new tail back out
     const int nunits = p->nchan * (int)((p->tail_pitch + 4095) / 4096);
     const int tgrid = std::min(nunits, std::max(p->dev.num_sms, 1) * 8);
     if (nunits > 0) k_tail<OneBeam><<<tgrid, 256, 0, st>>>(OneBeam{a}, 0, nullptr, nullptr, 1, nunits);
     TX_CUDA(cudaGetLastError());
-    if ((rc = ingest(p, d_block, p->T, a.ring, a.head, st))) return rc;
+    if ((rc = ingest(p, d_block, p->T, a.ring, a.head, st, ictr))) return rc;
     if (nunits > 0) k_tail<OneBeam><<<tgrid, 256, 0, st>>>(OneBeam{a}, 1, nullptr, nullptr, 1, nunits);
     TX_CUDA(cudaGetLastError());
   } else {
-    if ((rc = ingest(p, d_block, p->T, b->ring, b->head, st))) return rc;
+    if ((rc = ingest(p, d_block, p->T, b->ring, b->head, st, ictr))) return rc;
     b->head = mod(b->head + p->T, p->R);
   }
   TX_MARK(1);
@@ -441,7 +445,6 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   }
 
   // stage 1
-  int32_t* ictr = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(d_workspace) + p->ws_ctr);
   switch (p->q1) {
     case 256: rc = launch_stage1<256>(p, a, ictr, st); break;
     case 128: rc = launch_stage1<128>(p, a, ictr, st); break;
@@ -501,8 +504,7 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
     k_stats<OneBeam><<<(p->ndm + 127) / 128, 128, 0, st>>>(OneBeam{a}, nullptr, nullptr, 1, p->ndm);
     TX_CUDA(cudaGetLastError());
     TX_MARK(4);
-    if (p->output == TX_OUT_CANDS) TX_CUDA(cudaMemsetAsync(d_ncand, 0, sizeof(int64_t), st));
-    const int nunits = p->ndm * p->ntile3;
+    const int nunits = p->ndm * p->ntile3;   // k_stats zeroed the candidate counter
     const int grid = std::min(nunits, std::max(p->dev.num_sms, 1) * p->dev.box_blocks_per_sm);
     box_kernel<OneBeam>(p->nw, p->output)<<<grid, kBoxThreads, box_smem(p), st>>>(OneBeam{a}, nullptr, nullptr, 1,
                                                                                    nunits, p->box_tile, p->wmax);

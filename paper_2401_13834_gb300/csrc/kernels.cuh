@@ -199,9 +199,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ---------------------------------------------------------------------------
 // ingest (Sec. 2.3 data flow)
 // ---------------------------------------------------------------------------
+// Both ingest kernels also zero *zero (when given): the stage-1 item counter
+// of the execute, so that no launch of its own is spent on it.
 // Channel-major rows: ring[c][dst_off + i] = src[c][src_off + i], i < n.
 __global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t src_pitch, int64_t src_off, int64_t n,
-                            uint8_t* __restrict__ ring, int64_t R, int64_t dst_off, int vec) {
+                            uint8_t* __restrict__ ring, int64_t R, int64_t dst_off, int vec, int32_t* zero) {
+  if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
   const int c = blockIdx.y;
   const uint8_t* s = src + (int64_t)c * src_pitch + src_off;
   uint8_t* d = ring + (int64_t)c * R + dst_off;
@@ -262,8 +265,9 @@ __device__ __forceinline__ void tf_column(const uint8_t (*tile)[80], int cc, int
 // source all 16-byte aligned).
 __global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ src, int64_t t_off, int64_t n,
                                                    int nchan, uint8_t* __restrict__ ring, int64_t R,
-                                                   int64_t dst_off, int vec) {
+                                                   int64_t dst_off, int vec, int32_t* zero) {
   __shared__ __align__(16) uint8_t tiles[kIngestTiles][64][80];
+  if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
   const int c0 = blockIdx.y * 64;
   uint4 vv[kIngestTiles];   // all of the block's loads in flight at once
 #pragma unroll
@@ -1523,6 +1527,7 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
   } else {
     d = gd;
     a = src.get(0);
+    if (d == 0 && a.output == TX_OUT_CANDS) *a.ncand = 0ull;   // the boxcar launch comes after this one
   }
   const int64_t T = a.T;
   unsigned long long s1 = 0, s2 = 0;

@@ -864,9 +864,14 @@ def run_batched(args):
 
     # ---- per-phase times from a profiling batch (direct launches) -------------
     pbatch = tx.Batch(plans, beams, workspace_budget=budget, graph=False, profile=True)
+    pbatch.execute(blocks, outs, ws)          # one untimed step
+    pbatch.wait()
+    ms0, n0 = pbatch.read_profile()
     for _ in range(3):
         pbatch.execute(blocks, outs, ws)
-    phase_ms, pn = pbatch.read_profile()
+    pbatch.wait()
+    ms1, n1 = pbatch.read_profile()
+    phase_ms, pn = {k: v - ms0[k] for k, v in ms1.items()}, n1 - n0
     del pbatch
 
     # ---- end to end: pinned host blocks in, candidates out --------------------

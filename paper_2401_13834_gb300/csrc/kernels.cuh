@@ -1171,13 +1171,34 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
 }
 
 // The walk of one role over the block's chunks: unit, chunk within the unit,
-// tile, and which member's arguments apply (read from the source when used,
-// so that no copy of them lives in registers).
+// tile, which member's arguments apply, and the few of them every chunk uses
+// (read once per unit: a batched launch finds them in constant memory at a
+// run-time index, which would put a load in every chunk's path); the rest
+// are read from the source when used.
+// The fields of a beam's arguments that the pipelined stage 2 reads for
+// every chunk.
+struct PipeHot {
+  int G, SWW, ndm, SC, nsub;
+  uint32_t polls;
+  int64_t Pp;
+  const void* P;
+  const int32_t* tab2;
+  double* run;   // where a wait that gives up is recorded
+};
+
 template <typename Src>
 struct PipeCursor {
   MemberCursor mc;
   int u, ch, nchunk, k, tile, ns, s0, SC, nsub, beam;
   int64_t t0;
+  struct NoHot {};
+  // batched sources: the member's fields every chunk uses, read once per unit
+  std::conditional_t<Src::kBatch, PipeHot, NoHot> hc;
+  // the fields every chunk uses: the kernel parameters for one beam, the
+  // per-unit copy in a batch
+  __device__ __forceinline__ auto hot(const Src& src) const {
+    if constexpr (Src::kBatch) return hc; else return src.get(0);
+  }
   __device__ __forceinline__ BeamArgs args(const Src& src) const { return src.get(beam); }
   __device__ __forceinline__ void load(const Src& src, const int32_t* __restrict__ uoff,
                                        const int32_t* __restrict__ umem, int nmem) {
@@ -1193,6 +1214,7 @@ struct PipeCursor {
     const BeamArgs a = src.get(beam);
     SC = a.SC;
     nsub = a.nsub;
+    if constexpr (Src::kBatch) hc = PipeHot{a.G, a.SWW, a.ndm, a.SC, a.nsub, a.polls, a.Pp, a.P, a.tab2, a.run};
     nchunk = (nsub + SC - 1) / SC;
     k = lu / a.ntile2;
     tile = lu - k * a.ntile2;
@@ -1248,7 +1270,7 @@ k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __
   __syncthreads();   // barriers initialised: the only block-wide barrier
   volatile int* abort = &abort_flag;
   // a wait that gave up: the first thread to see it raises the flag and records it
-  auto give_up = [&](const BeamArgs& a) {
+  auto give_up = [&](const auto& a) {
     if (atomicExch(&abort_flag, 1) == 0) record_give_up(a);
   };
 
@@ -1258,7 +1280,7 @@ k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __
     bool more = ic.start(src, uoff, umem, nmem, nunits);
     int64_t q = 0;   // chunks issued
     while (more) {
-      const BeamArgs a = ic.args(src);
+      const auto a = ic.hot(src);
       const int bq = (int)(q % kPipeStages);
       // the stage's previous chunk: every consumer has left it
       if (q >= kPipeStages &&
@@ -1297,7 +1319,7 @@ k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __
     PipeCursor<Src> pc;
     bool more = pc.start(src, uoff, umem, nmem, nunits);
     for (int64_t p = 0; more; ++p) {
-      const BeamArgs a = pc.args(src);
+      const auto a = pc.hot(src);
       const int bp = (int)(p % kPipeStages);
       if (!mbar_wait_or_abort(&full[bp], (uint32_t)((p / kPipeStages) & 1), a.polls, abort)) {
         give_up(a);
@@ -1350,7 +1372,7 @@ k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __
   PipeCursor<Src> cc;
   cc.start(src, uoff, umem, nmem, nunits);
   for (int64_t p = 0;; ++p) {
-    const BeamArgs a = cc.args(src);
+    const auto a = cc.hot(src);
     const int bp = (int)(p % kPipeStages);
     if (!mbar_wait_or_abort(&ready[bp], (uint32_t)((p / kPipeStages) & 1), a.polls, abort)) {
       give_up(a);
@@ -1404,38 +1426,43 @@ k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __
     }
     mbar_arrive(&empty[bp]);   // this thread is done with the stage
     if (cc.ch + 1 == cc.nchunk) {
-      // the unit's sums are complete: this warp's slice of the series and its exact sums
-      long long s1 = 0;
-      unsigned long long s2 = 0;
-      if (g < nd) {
-        const int d = dfirst + g;
-        int32_t* drow = a.D + (size_t)d * a.Dp;
-        const int O = HALF ? a.hoff[a.nsub] : 0;   // the offsets taken out in stage 1, added back
+      // the unit's sums are complete: this warp's slice of the series and its
+      // exact sums (a beam's arguments: the chunk's own for one beam, the
+      // member's in a batch)
+      auto finish = [&](const BeamArgs& e) {
+        long long s1 = 0;
+        unsigned long long s2 = 0;
+        if (g < nd) {
+          const int d = dfirst + g;
+          int32_t* drow = e.D + (size_t)d * e.Dp;
+          const int O = HALF ? e.hoff[e.nsub] : 0;   // the offsets taken out in stage 1, added back
 #pragma unroll
-        for (int v = 0; v < VW; ++v) {
-          const int64_t ta = cc.t0 + 2 * (jbase + lane + 32 * v);
-          uint32_t lo, hi;
-          if constexpr (HALF) {
-            // the halves hold integers and their FP32 sums stay below 2^24: exact
-            lo = (uint32_t)((int)fl[v] + O);
-            hi = (uint32_t)((int)fh[v] + O);
-          } else {
-            lo = aw[v] - (ah[v] << 16);
-            hi = ah[v];
+          for (int v = 0; v < VW; ++v) {
+            const int64_t ta = cc.t0 + 2 * (jbase + lane + 32 * v);
+            uint32_t lo, hi;
+            if constexpr (HALF) {
+              // the halves hold integers and their FP32 sums stay below 2^24: exact
+              lo = (uint32_t)((int)fl[v] + O);
+              hi = (uint32_t)((int)fh[v] + O);
+            } else {
+              lo = aw[v] - (ah[v] << 16);
+              hi = ah[v];
+            }
+            if (ta + 1 < e.Td && (e.Dp & 1) == 0) {
+              *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
+            } else {
+              if (ta < e.Td) drow[ta] = (int32_t)lo;
+              if (ta + 1 < e.Td) drow[ta + 1] = (int32_t)hi;
+            }
+            if (ta < e.T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
+            if (ta + 1 < e.T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
           }
-          if (ta + 1 < a.Td && (a.Dp & 1) == 0) {
-            *reinterpret_cast<int2*>(drow + ta) = make_int2((int32_t)lo, (int32_t)hi);
-          } else {
-            if (ta < a.Td) drow[ta] = (int32_t)lo;
-            if (ta + 1 < a.Td) drow[ta + 1] = (int32_t)hi;
-          }
-          if (ta < a.T) { s1 += lo; s2 += (unsigned long long)lo * lo; }
-          if (ta + 1 < a.T) { s1 += hi; s2 += (unsigned long long)hi * hi; }
         }
-      }
-      warp_sum_stats(s1, s2);
-      if (g < nd && lane == 0)
-        a.part[((size_t)(dfirst + g) * a.ntile2 + cc.tile) * SPLIT + part_i] = make_longlong2(s1, (long long)s2);
+        warp_sum_stats(s1, s2);
+        if (g < nd && lane == 0)
+          e.part[((size_t)(dfirst + g) * e.ntile2 + cc.tile) * SPLIT + part_i] = make_longlong2(s1, (long long)s2);
+      };
+      if constexpr (Src::kBatch) finish(cc.args(src)); else finish(a);
 #pragma unroll
       for (int v = 0; v < VW; ++v) {
         aw[v] = ah[v] = 0u;
@@ -1751,6 +1778,7 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
           if (hit) {
             const uint32_t* Ci = Cs + i;
             const uint32_t cl = Ci[0];
+            #pragma unroll   // static indices keep Wr in registers
             for (int w = 0; w < NR; ++w) {
               const SnrConst c = cst[w];
               const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
@@ -1799,12 +1827,12 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
           // once per warp that has any
           constexpr int RR = kBoxTile / kBoxThreads;
           uint32_t mask = 0;
-  #pragma unroll
+#pragma unroll
           for (int r = 0; r < RR; ++r) {
             const uint32_t* Ci = Cs + threadIdx.x + r * kBoxThreads;
             const uint32_t cl = Ci[0];
             int32_t mx = INT32_MIN;
-  #pragma unroll
+#pragma unroll
             for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
             mask |= (uint32_t)(mx >= 0) << r;
           }
@@ -1819,6 +1847,7 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
               if (hit) {
                 const uint32_t* Ci = Cs + i;
                 const uint32_t cl = Ci[0];
+                #pragma unroll   // static indices keep Wr in registers
                 for (int w = 0; w < NR; ++w) {
                   const SnrConst c = cst[w];
                   const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
@@ -1855,10 +1884,11 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         if (NWT > 0) {
           if (MODE == TX_OUT_CANDS) {
             int32_t mx = INT32_MIN;
-  #pragma unroll
+#pragma unroll
             for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
             hit = mx >= 0;
             if (hit) {  // rare: float S/N and the best width of a candidate
+              #pragma unroll   // static indices keep Wr in registers
               for (int w = 0; w < NR; ++w) {
                 const SnrConst c = cst[w];
                 const float sv = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
@@ -1867,19 +1897,19 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
             }
           } else {
             float sv[NR];
-  #pragma unroll
+#pragma unroll
             for (int w = 0; w < NR; ++w) {
               const SnrConst c = cst[w];
               sv[w] = ((float)((int32_t)(Ci[Wr[w]] - cl) - c.hi) - c.lo) * c.inv;
             }
             if (MODE == TX_OUT_CUBE) {
-  #pragma unroll
+#pragma unroll
               for (int w = 0; w < NR; ++w) a.outf[((size_t)d * nw + w) * T + ts + i] = sv[w];
             } else {
-  #pragma unroll
+#pragma unroll
               for (int w = 0; w < NR; ++w) best = fmaxf(best, sv[w]);
               bw = NR - 1;
-  #pragma unroll
+#pragma unroll
               for (int w = NR - 1; w >= 0; --w)
                 if (sv[w] == best) bw = w;
             }

@@ -1767,8 +1767,10 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         mask |= ((uint32_t)(m0 >= 0) | ((uint32_t)(m1 >= 0) << 1) | ((uint32_t)(m2 >= 0) << 2) |
                  ((uint32_t)(m3 >= 0) << 3)) << (4 * r);
       }
-      if (__any_sync(0xffffffffu, mask != 0u)) {
-        for (int r = 0; r < 4 * QR; ++r) {
+      // only the bit positions where some lane of the warp has a hit
+      for (uint32_t rows = __reduce_or_sync(0xffffffffu, mask); rows != 0u; rows &= rows - 1u) {
+        {
+          const int r = __ffs(rows) - 1;
           const int i = 4 * (threadIdx.x + (r >> 2) * kBoxThreads) + (r & 3);
           const bool hit = (mask >> r) & 1u;
           const unsigned hits = __ballot_sync(0xffffffffu, hit);
@@ -1836,8 +1838,9 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
             for (int w = 0; w < NR; ++w) mx = max(mx, (int32_t)(Ci[Wr[w]] - cl) - thr[w]);
             mask |= (uint32_t)(mx >= 0) << r;
           }
-          if (__any_sync(0xffffffffu, mask != 0u)) {
-            for (int r = 0; r < RR; ++r) {
+          for (uint32_t rows = __reduce_or_sync(0xffffffffu, mask); rows != 0u; rows &= rows - 1u) {
+            {
+              const int r = __ffs(rows) - 1;
               const int i = threadIdx.x + r * kBoxThreads;
               const bool hit = (mask >> r) & 1u;
               const unsigned hits = __ballot_sync(0xffffffffu, hit);

@@ -118,8 +118,8 @@ template <int Q, typename PT, bool HALF = false>
 void launch_stage1_t(const tx_plan* p, const BeamArgs& a, int32_t* ictr, cudaStream_t st) {
   const int nitems = (int)p->items1.size();
   const int grid = std::min(nitems, std::max(p->dev.num_sms, 1));
-  k_stage1<Q, PT, OneBeam, HALF><<<grid, kStage1Warps * 32, (int)stage1_smem_bytes(p->m, Q), st>>>(
-      OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u, ictr);
+  launch_pdl(k_stage1<Q, PT, OneBeam, HALF>, grid, kStage1Warps * 32, (size_t)stage1_smem_bytes(p->m, Q), st,
+             OneBeam{a}, nullptr, nullptr, 1, nitems, p->m, 1u, ictr);
 }
 
 // stage 1 with its item counter `ictr` (zeroed before, by the ingest)
@@ -156,12 +156,12 @@ int ingest(const tx_plan* p, const uint8_t* src, int64_t n, uint8_t* ring, int64
     if (p->layout == TX_LAYOUT_TF) {
       const int vec = (p->nchan % 16 == 0) && (pos % 16 == 0) && (((uintptr_t)src & 15) == 0);
       dim3 grid((unsigned)((len + 64 * kIngestTiles - 1) / (64 * kIngestTiles)), (unsigned)((p->nchan + 63) / 64));
-      k_ingest_tf<<<grid, 256, 0, st>>>(src, done, len, p->nchan, ring, R, pos, vec, zero);
+      TX_CUDA(launch_pdl(k_ingest_tf, grid, 256, 0, st, src, done, len, p->nchan, ring, R, pos, vec, zero));
     } else {
       const int vec = (n % 16 == 0) && (done % 16 == 0) && (len % 16 == 0) && (pos % 16 == 0) &&
                       (((uintptr_t)src & 15) == 0);
       dim3 grid((unsigned)std::min<int64_t>((len + 4095) / 4096, 64), (unsigned)p->nchan);
-      k_ingest_ft<<<grid, 256, 0, st>>>(src, n, done, len, ring, R, pos, vec, zero);
+      TX_CUDA(launch_pdl(k_ingest_ft, grid, 256, 0, st, src, n, done, len, ring, R, pos, vec, zero));
     }
     TX_CUDA(cudaGetLastError());
     done += len;
@@ -462,19 +462,16 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
       const int nunits = p->nk * p->ntile2;
       launch_stage2_pipe<OneBeam>(p->split2, half, std::min(nunits, std::max(p->dev.num_sms, 1)), stage2_threads(p),
                                   stage2_smem(p), st, OneBeam{a}, nullptr, nullptr, 1, nunits, p->nsub_chunk2,
-                                  p->nsub_chunk2 * p->sww2);
+                                  p->nsub_chunk2 * p->sww2, true);
     } else if (is16(p)) {
       const int nunits = p->nk * p->ntile2;
       const int grid = std::min(nunits, std::max(p->dev.num_sms, 1));
       const int slot = p->nsub_chunk2 * p->sww2;
 #define TX_S2(NW, SP)                                                                                          \
   do {                                                                                                         \
-    if (half)                                                                                                  \
-      k_stage2_u16<NW, 32, SP, OneBeam, true><<<grid, stage2_threads(p), stage2_smem(p), st>>>(                \
-          OneBeam{a}, nullptr, nullptr, 1, nunits, slot, p->e2w2);                                             \
-    else                                                                                                       \
-      k_stage2_u16<NW, 32, SP, OneBeam, false><<<grid, stage2_threads(p), stage2_smem(p), st>>>(               \
-          OneBeam{a}, nullptr, nullptr, 1, nunits, slot, p->e2w2);                                             \
+    launch_pdl(half ? k_stage2_u16<NW, 32, SP, OneBeam, true> : k_stage2_u16<NW, 32, SP, OneBeam, false>, grid,  \
+               stage2_threads(p), (size_t)stage2_smem(p), st, OneBeam{a}, nullptr, nullptr, 1, nunits, slot,       \
+               p->e2w2);                                                                                       \
   } while (0)
       switch (stage2_split(p)) {
         case 8: TX_S2(512, 8); break;
@@ -487,27 +484,22 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
       const int threads = std::min(p->group, kStage2MaxGroup) * 32;
       dim3 grid((unsigned)p->ntile2, (unsigned)p->nk);
       const int32_t* P = static_cast<const int32_t*>(a.P);
-      if (p->nw2 == 512)
-        k_stage2_i32<512><<<grid, threads, stage2_smem(p), st>>>(P, p->Pp, p->dev.e2, p->ndm, p->nsub, p->group,
-                                                                 p->nsub_chunk2, p->sw2_i32, a.D, a.Dp, p->Td, p->T,
-                                                                 a.part, p->ntile2);
-      else
-        k_stage2_i32<256><<<grid, threads, stage2_smem(p), st>>>(P, p->Pp, p->dev.e2, p->ndm, p->nsub, p->group,
-                                                                 p->nsub_chunk2, p->sw2_i32, a.D, a.Dp, p->Td, p->T,
-                                                                 a.part, p->ntile2);
+      launch_pdl(p->nw2 == 512 ? k_stage2_i32<512> : k_stage2_i32<256>, grid, threads, (size_t)stage2_smem(p), st, P,
+                 p->Pp, p->dev.e2, p->ndm, p->nsub, p->group, p->nsub_chunk2, p->sw2_i32, a.D, a.Dp, p->Td, p->T,
+                 a.part, p->ntile2);
     }
     TX_CUDA(cudaGetLastError());
   }
   TX_MARK(3);
 
   if (!series) {
-    k_stats<OneBeam><<<(p->ndm + 127) / 128, 128, 0, st>>>(OneBeam{a}, nullptr, nullptr, 1, p->ndm);
+    TX_CUDA(launch_pdl(k_stats<OneBeam>, (p->ndm + 127) / 128, 128, 0, st, OneBeam{a}, nullptr, nullptr, 1, p->ndm));
     TX_CUDA(cudaGetLastError());
     TX_MARK(4);
     const int nunits = p->ndm * p->ntile3;   // k_stats zeroed the candidate counter
     const int grid = std::min(nunits, std::max(p->dev.num_sms, 1) * p->dev.box_blocks_per_sm);
-    box_kernel<OneBeam>(p->nw, p->output)<<<grid, kBoxThreads, box_smem(p), st>>>(OneBeam{a}, nullptr, nullptr, 1,
-                                                                                   nunits, p->box_tile, p->wmax);
+    TX_CUDA(launch_pdl(box_kernel<OneBeam>(p->nw, p->output), grid, kBoxThreads, (size_t)box_smem(p), st, OneBeam{a},
+                       nullptr, nullptr, 1, nunits, p->box_tile, p->wmax));
     TX_CUDA(cudaGetLastError());
   } else {
     TX_MARK(4);

@@ -196,6 +196,16 @@ __device__ __forceinline__ void record_give_up(const A& a) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the kernel before it in the stream is still
+// finishing. Each kernel of the path waits (pdl_wait) before it touches
+// memory, so it runs on the completed results of everything before it; and
+// lets the next kernel start launching at once (pdl_trigger), so that the
+// next kernel's launch and block set-up overlap this one's tail. Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // ingest (Sec. 2.3 data flow)
 // ---------------------------------------------------------------------------
@@ -204,6 +214,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Channel-major rows: ring[c][dst_off + i] = src[c][src_off + i], i < n.
 __global__ void k_ingest_ft(const uint8_t* __restrict__ src, int64_t src_pitch, int64_t src_off, int64_t n,
                             uint8_t* __restrict__ ring, int64_t R, int64_t dst_off, int vec, int32_t* zero) {
+  pdl_wait();
+  pdl_trigger();
   if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
   const int c = blockIdx.y;
   const uint8_t* s = src + (int64_t)c * src_pitch + src_off;
@@ -267,6 +279,8 @@ __global__ void __launch_bounds__(256) k_ingest_tf(const uint8_t* __restrict__ s
                                                    int nchan, uint8_t* __restrict__ ring, int64_t R,
                                                    int64_t dst_off, int vec, int32_t* zero) {
   __shared__ __align__(16) uint8_t tiles[kIngestTiles][64][80];
+  pdl_wait();
+  pdl_trigger();
   if (zero && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *zero = 0;
   const int c0 = blockIdx.y * 64;
   uint4 vv[kIngestTiles];   // all of the block's loads in flight at once
@@ -641,6 +655,8 @@ __global__ void __launch_bounds__(kStage1Warps * 32, 1)
 k_stage1(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nitems,
          int mL, uint32_t unit, int32_t* __restrict__ ictr) {
   extern __shared__ __align__(16) uint8_t smem1[];
+  pdl_wait();
+  pdl_trigger();
   constexpr int SW = kStage1StagedWords(Q);      // staged words per channel
   constexpr int RB = kStage1RawBytes(Q);         // raw bytes per channel
   constexpr int V = Q / 32;
@@ -878,6 +894,8 @@ __global__ void __launch_bounds__(MAXWARPS * 32, 1)
 k_stage2_u16(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
              int slot, int e2w) {
   extern __shared__ __align__(16) uint32_t smem2[];
+  pdl_wait();
+  pdl_trigger();
   constexpr int VW = NW / 32 / SPLIT;                    // words per lane
   int32_t* E = reinterpret_cast<int32_t*>(smem2);        // [2][e2w] delays of a unit's group
   uint32_t* Se = smem2 + 2 * (size_t)e2w;                // [2][slot]
@@ -1251,6 +1269,8 @@ __global__ void __launch_bounds__(VW == 16 ? 704 : 1024, 1)
 k_stage2_pipe(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem,
               int nunits, int slot, int tabw) {
   extern __shared__ __align__(16) uint32_t smp[];
+  pdl_wait();
+  pdl_trigger();
   constexpr int SPLIT = 16 / VW;                         // consumer warps per fine DM
   __shared__ __align__(8) uint64_t full[kPipeStages], ready[kPipeStages], empty[kPipeStages];
   __shared__ int abort_flag;
@@ -1481,6 +1501,8 @@ k_stage2_i32(const int32_t* __restrict__ P, int64_t Pp, const int32_t* __restric
              int G, int SC, int SW, int32_t* __restrict__ D, int64_t Dp, int64_t Td, int64_t T,
              longlong2* __restrict__ part, int ntile) {
   extern __shared__ __align__(16) uint32_t smem3[];
+  pdl_wait();
+  pdl_trigger();
   constexpr int V = 2 * NW / 32;
   const int tile = blockIdx.x, k = blockIdx.y;
   const int64_t t0 = (int64_t)tile * 2 * NW;
@@ -1542,6 +1564,8 @@ __device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
 template <typename Src>
 __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem,
                         int nunits) {
+  pdl_wait();
+  pdl_trigger();
   const int gd = blockIdx.x * blockDim.x + threadIdx.x;
   if (gd >= nunits) return;
   int d;
@@ -1625,6 +1649,8 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
          int tileL, int wmaxL) {
   constexpr int NR = NWT > 0 ? NWT : 1;
   extern __shared__ __align__(16) uint32_t smb[];
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t wsum[kBoxThreads / 32];
   __shared__ int32_t sW[kMaxWidths];
   __shared__ SnrConst sC[kMaxWidths];
@@ -1989,6 +2015,23 @@ __global__ void k_fill_run(double* run, int n) {
 // ---------------------------------------------------------------------------
 // host helpers shared by the single-beam and batched launchers
 // ---------------------------------------------------------------------------
+// Launches kernel k with programmatic stream serialization (see pdl_wait):
+// the launch and block set-up overlap the tail of the kernel before it.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 // Raises kernel k's dynamic shared memory limit on the current device to at
 // least `bytes`, never lowering it: plans of different shapes share kernels,
 // and the limit one plan needs must survive another plan's set-up.
@@ -2039,14 +2082,16 @@ const void* stage2_pipe_kernel(int split, bool half) {
 // chunk's staged words (sub-bands x words), smem from stage2_pipe_smem.
 template <typename Src>
 void launch_stage2_pipe(int split, bool half, int grid, int threads, int smem, cudaStream_t st, const Src& src,
-                        const int32_t* uoff, const int32_t* umem, int nmem, int nunits, int sc, int slot) {
+                        const int32_t* uoff, const int32_t* umem, int nmem, int nunits, int sc, int slot,
+                        bool pdl = false) {
   const int tabw = (kPipeMaxGroup2 + 1) * ((sc + 3) & ~3);
 #define TX_P2(VW)                                                                                               \
   do {                                                                                                          \
-    if (half)                                                                                                   \
-      k_stage2_pipe<VW, Src, true><<<grid, threads, smem, st>>>(src, uoff, umem, nmem, nunits, slot, tabw);    \
+    auto k = half ? k_stage2_pipe<VW, Src, true> : k_stage2_pipe<VW, Src, false>;                              \
+    if (pdl)                                                                                                    \
+      launch_pdl(k, grid, threads, smem, st, src, uoff, umem, nmem, nunits, slot, tabw);                        \
     else                                                                                                        \
-      k_stage2_pipe<VW, Src, false><<<grid, threads, smem, st>>>(src, uoff, umem, nmem, nunits, slot, tabw);   \
+      k<<<grid, threads, smem, st>>>(src, uoff, umem, nmem, nunits, slot, tabw);                                \
   } while (0)
   switch (split) {
     case 4: TX_P2(4); break;

@@ -198,9 +198,16 @@ __global__ void __launch_bounds__(kThreads1) k_stage1_f32(const float* __restric
   }
 }
 
+// 4-byte global -> shared copy that completes asynchronously (cp.async)
+__device__ __forceinline__ void cp_async4f(float* smem, const float* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem) : "memory");
+}
+
 // One block per (tile of 2 NW outputs, coarse group k), one warp per fine DM
 // of the group: sub-band chunks of SC rows of P (the tile plus the group's
-// delay spread) are staged in shared memory, and each warp sums its DM's
+// delay spread) are staged in shared memory, two buffers deep (chunk c + 1's
+// copies are in flight while chunk c is summed), and each warp sums its DM's
 // shifted rows in sub-band order, V = 2 NW / 32 outputs per lane; then the
 // tile's sums of D and D^2 over t < T in double to part[d][tile].
 template <int NW>
@@ -209,34 +216,49 @@ __global__ void __launch_bounds__(kStage2MaxGroup * 32) k_stage2_f32(const float
                                                                       int G, int SC, int SW, float* __restrict__ D,
                                                                       int64_t Dp, int64_t Td, int64_t T,
                                                                       double2* __restrict__ part, int ntile) {
-  extern __shared__ float Sf[];   // [SC][SW]
+  extern __shared__ float Sf[];   // [2][SC][SW]
   constexpr int V = 2 * NW / 32;
   const int tile = blockIdx.x, k = blockIdx.y;
   const int64_t t0 = (int64_t)tile * 2 * NW;
   const int dfirst = k * G;
   const int nd = min(G, ndm - dfirst);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nch = (nsub + SC - 1) / SC;
+  // chunk c into buffer c & 1 (the group's first DM's delay is each row's start)
+  auto stage = [&](int c) {
+    const int sb = c * SC, ns = min(SC, nsub - sb);
+    float* dst = Sf + (size_t)(c & 1) * SC * SW;
+    for (int ss = 0; ss < ns; ++ss) {
+      const int s = sb + ss;
+      const float* src = P + ((size_t)k * nsub + s) * Pp + t0 + __ldg(e2 + (size_t)dfirst * nsub + s);
+      for (int j = threadIdx.x; j < SW; j += blockDim.x) cp_async4f(dst + (size_t)ss * SW + j, src + j);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   float acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = 0.f;
-  for (int sb = 0; sb < nsub; sb += SC) {
-    const int ns = min(SC, nsub - sb);
-    for (int i = threadIdx.x; i < ns * SW; i += blockDim.x) {
-      const int ss = i / SW, j = i - ss * SW;
-      const int s = sb + ss;
-      Sf[(size_t)ss * SW + j] = __ldg(P + ((size_t)k * nsub + s) * Pp + t0 + e2[(size_t)dfirst * nsub + s] + j);
+  stage(0);
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) {
+      stage(c + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");   // chunk c has landed
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    const int sb = c * SC, ns = min(SC, nsub - sb);
+    const float* buf = Sf + (size_t)(c & 1) * SC * SW;
     if (warp < nd) {
       for (int ss = 0; ss < ns; ++ss) {
         const int s = sb + ss;
-        const int o = e2[(size_t)(dfirst + warp) * nsub + s] - e2[(size_t)dfirst * nsub + s];
-        const float* rw = Sf + (size_t)ss * SW + o + lane;
+        const int o = __ldg(e2 + (size_t)(dfirst + warp) * nsub + s) - __ldg(e2 + (size_t)dfirst * nsub + s);
+        const float* rw = buf + (size_t)ss * SW + o + lane;
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = __fadd_rn(acc[v], rw[32 * v]);
       }
     }
-    __syncthreads();
+    __syncthreads();   // every warp is done with buffer c & 1 before chunk c + 2 lands there
   }
   if (warp < nd) {
     const int d = dfirst + warp;
@@ -500,9 +522,9 @@ int float_execute(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_
   // stage 2 with per-tile sums
   const dim3 g2((unsigned)p->ntile2, (unsigned)p->nk);
   const int threads2 = std::min(p->group, kStage2MaxGroup) * 32;
-  // chunks of about 56 KB of staged rows, so that four blocks share an SM
-  const int sc2 = std::max(1, std::min(p->nsub_chunk2, (56 * 1024) / (p->sw2_i32 * (int)sizeof(float))));
-  const int smem2 = sc2 * p->sw2_i32 * (int)sizeof(float);
+  // two buffers of chunks, about 56 KB in all, so that four blocks share an SM
+  const int sc2 = std::max(1, std::min(p->nsub_chunk2, (28 * 1024) / (p->sw2_i32 * (int)sizeof(float))));
+  const int smem2 = 2 * sc2 * p->sw2_i32 * (int)sizeof(float);
 #define TX_F2(NW)                                                                                                 \
   do {                                                                                                            \
     TX_CUDA(cudaFuncSetAttribute((const void*)k_stage2_f32<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2)); \

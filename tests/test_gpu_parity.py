@@ -124,6 +124,52 @@ def test_tf_layout_matches_ft(tx):
     assert np.array_equal(res[0], res[1])
 
 
+@pytest.mark.parametrize("output", ["series", "cands"])
+def test_beams_on_two_streams(tx, output):
+    """Two beams of one plan, each with its own workspace and outputs, whose
+    blocks are launched alternately on two CUDA streams: every block's result
+    equals the oracle's (series bit for bit; candidates as in the other
+    tests), so nothing an execute keeps in its workspace (the stage-1 item
+    counter, the sums) or in the plan's tables is shared between concurrent
+    executes."""
+    wl = synth.tiny_workload(nchan=128, nsub=16, ndm=48, nsamp=4096, dm_max=300.0, tsamp=128e-6)
+    gamma = 4.0
+    kw = dict(snr_threshold=gamma, max_cands=1 << 18) if output == "cands" else {}
+    plan = make_plan(tx, wl, output=output, **kw)
+    op = oracle_plan(wl)
+    L, T, nb = plan.overlap, plan.nsamp, 3
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    Xs = [rand_stream(wl.nchan, L + nb * T, seed=40 + i) for i in range(2)]
+    beams, outs = [], [[], []]
+    for i in range(2):
+        b = tx.Beam(plan)
+        b.prime(torch.from_numpy(np.ascontiguousarray(Xs[i][:, :L])).cuda())
+        beams.append(b)
+    torch.cuda.synchronize()
+    ws = [plan.alloc_workspace() for _ in range(2)]
+    blocks = [[torch.from_numpy(np.ascontiguousarray(Xs[i][:, L + b * T:L + (b + 1) * T])).cuda() for b in range(nb)]
+              for i in range(2)]
+    for b in range(nb):
+        for i in range(2):
+            with torch.cuda.stream(streams[i]):
+                o, nc = plan.alloc_out()
+                tx.execute(plan, beams[i], blocks[i][b], out=o, ncand=nc, workspace=ws[i], stream=streams[i])
+                outs[i].append((o, nc))
+    torch.cuda.synchronize()
+    for i in range(2):
+        ref = O.stream_series(Xs[i], op, T, nb)
+        for b in range(nb):
+            o, nc = outs[i][b]
+            if output == "series":
+                assert np.array_equal(tx.series_view(plan, o).cpu().numpy(), ref[b]), (i, b)
+            else:
+                D = ref[b]
+                _, _, mu, sg = O.block_stats(D, T)
+                snr = O.boxcar_snr(D, op.widths, T, mu, sg)
+                got, n = tx.cands_view(plan, o, nc)
+                _check_cands(got, n, snr, gamma)
+
+
 @pytest.mark.parametrize("layout", ["ft", "tf"])
 def test_streaming_blocks_and_checkpoint(tx, layout):
     """Four blocks of one stream and a checkpoint/resume, bit-exact against the oracle.

@@ -183,10 +183,23 @@ __global__ void __launch_bounds__(kThreads1) k_stage1_f32(const float* __restric
     float acc[VW];
 #pragma unroll
     for (int v = 0; v < VW; ++v) acc[v] = 0.f;
-    for (int c = 0; c < m; ++c) {
-      const float* row = S + c * sw + (__ldg(d1k + c) - __ldg(d1b + c)) + lane;
+    if (m <= 64) {
+      // the DM's channel offsets held two per lane and broadcast by shuffles:
+      // no global load between a channel's shared-memory loads
+      const int oa = lane < m ? __ldg(d1k + lane) - __ldg(d1b + lane) : 0;
+      const int ob = lane + 32 < m ? __ldg(d1k + lane + 32) - __ldg(d1b + lane + 32) : 0;
+      for (int c = 0; c < m; ++c) {
+        const int o = __shfl_sync(0xffffffffu, c < 32 ? oa : ob, c & 31);
+        const float* row = S + c * sw + o + lane;
 #pragma unroll
-      for (int v = 0; v < VW; ++v) acc[v] = __fadd_rn(acc[v], row[32 * v]);
+        for (int v = 0; v < VW; ++v) acc[v] = __fadd_rn(acc[v], row[32 * v]);
+      }
+    } else {
+      for (int c = 0; c < m; ++c) {
+        const float* row = S + c * sw + (__ldg(d1k + c) - __ldg(d1b + c)) + lane;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc[v] = __fadd_rn(acc[v], row[32 * v]);
+      }
     }
     const int64_t rel = (int64_t)it.tau0 - abase[(size_t)k * nsub + it.s];
     float* prow = P + ((size_t)k * nsub + it.s) * Pp;

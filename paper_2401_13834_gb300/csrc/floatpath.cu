@@ -345,19 +345,19 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float x) {
 // double) and scales by 1 / (sigma_d sqrt W): S/N = ((dhi - Wmu_hi) + (dlo -
 // Wmu_lo)) * inv (0 when sigma_d = 0). Outputs as the integer path's.
 __global__ void __launch_bounds__(kThreads) k_boxcar_f32(const float* __restrict__ D, int64_t Dp, int64_t T,
-                                                          int ntile3, const double2* __restrict__ ms,
+                                                          int tileL, int ntile3, const double2* __restrict__ ms,
                                                           const int32_t* __restrict__ widths, int nw, int wmax,
                                                           int mode, float gamma, float* __restrict__ outf,
                                                           uint8_t* __restrict__ outw, tx_cand* __restrict__ cands,
                                                           unsigned long long* __restrict__ ncand, int64_t max_cands) {
-  extern __shared__ float2 H[];   // [kBoxTile + wmax]: the window, then its prefix sums (hi, lo)
+  extern __shared__ float2 H[];   // [tileL + wmax]: the window, then its prefix sums (hi, lo)
   __shared__ float2 wtot[kThreads / 32];
   __shared__ int32_t sW[kMaxWidths];
   __shared__ float sInv[kMaxWidths], sMh[kMaxWidths], sMl[kMaxWidths];
   const int unit = blockIdx.x;
   const int d = unit / ntile3, tile = unit - d * ntile3;
-  const int64_t t0 = (int64_t)tile * kBoxTile;
-  const int n = (int)min((int64_t)kBoxTile, T - t0);
+  const int64_t t0 = (int64_t)tile * tileL;
+  const int n = (int)min((int64_t)tileL, T - t0);
   const int N = n + wmax - 1;
   const double2 m = ms[d];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -556,15 +556,18 @@ int float_execute(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_
     TX_CUDA(cudaGetLastError());
     if ((rc = mark(4))) return rc;
     if (p->output == TX_OUT_CANDS) TX_CUDA(cudaMemsetAsync(d_ncand, 0, sizeof(int64_t), st));
-    const int smem = (kBoxTile + p->wmax) * (int)sizeof(float2);
+    // units of the plan's boxcar length (the longest that still leaves a full
+    // GPU several units per resident block)
+    const int tile = p->box_tile;
+    const int smem = (tile + p->wmax) * (int)sizeof(float2);
     // the most any plan needs (the attribute belongs to the current device)
     TX_CUDA(cudaFuncSetAttribute((const void*)k_boxcar_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (kBoxTile + kMaxWidth) * (int)sizeof(float2)));
+                                 (4 * kBoxTile + kMaxWidth) * (int)sizeof(float2)));
     float* outf = static_cast<float*>(d_out);
     uint8_t* outw = p->output == TX_OUT_PLANE ? static_cast<uint8_t*>(d_out) + (size_t)p->ndm * p->T * 4 : nullptr;
-    const int nt = (int)((p->T + kBoxTile - 1) / kBoxTile);   // tiles of kBoxTile outputs per DM
+    const int nt = (int)((p->T + tile - 1) / tile);   // units per DM
     k_boxcar_f32<<<p->ndm * nt, kThreads, smem, st>>>(
-        D, Dp, p->T, nt, ms, p->dev.widths, p->nw, p->wmax, p->output, p->gamma, outf, outw,
+        D, Dp, p->T, tile, nt, ms, p->dev.widths, p->nw, p->wmax, p->output, p->gamma, outf, outw,
         static_cast<tx_cand*>(d_out), reinterpret_cast<unsigned long long*>(d_ncand), p->max_cands);
     TX_CUDA(cudaGetLastError());
   } else {

@@ -122,6 +122,19 @@ def test_float_snr_matches_oracle(tx, norm, output):
             _check_cands(got, n, snr, gamma)
 
 
+@pytest.mark.parametrize("tile_box", [4096, 8192])
+def test_float_boxcar_long_units(tx, tile_box):
+    """Boxcar units of 4096 or 8192 outputs on the float path (a full unit and
+    a ragged one at T = 9000), S/N against the oracle."""
+    wl = _workload(nsamp=9000)
+    plan, X, outs = _run(tx, wl, "unit", "cube", tile_box=tile_box)
+    T = plan.nsamp
+    for b, (out, _) in enumerate(outs):
+        op, D, _ = _oracle(wl, X, plan.overlap, T, "unit", b)
+        _, _, mu, sg = O.block_stats(D, T)
+        check_snr(tx.cube_view(plan, out).cpu().numpy(), O.boxcar_snr(D, op.widths, T, mu, sg))
+
+
 def test_float_running_statistics(tx):
     wl = _workload()
     plan, X, outs = _run(tx, wl, "unit", "cube", stats="running", stats_lambda=0.25)

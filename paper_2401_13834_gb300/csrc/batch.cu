@@ -323,8 +323,8 @@ int build_batch(tx_batch* B, int64_t budget) {
       L.kind = kStats;
       L.wave = wv;
       if ((rc = add_members(L, filt, first, [&](int b) -> int64_t { return B->plans[b]->ndm; }))) return rc;
-      L.threads = 128;
-      L.grid = (L.nunits + 127) / 128;
+      L.threads = 128;                   // one warp per DM
+      L.grid = (L.nunits + 3) / 4;
       B->launches.push_back(L);
     }
     std::map<std::pair<int, int>, std::vector<int>> by_box;

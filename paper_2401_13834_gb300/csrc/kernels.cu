@@ -493,7 +493,7 @@ int execute_impl(const tx_plan* p, tx_beam* b, const uint8_t* d_block, void* d_o
   TX_MARK(3);
 
   if (!series) {
-    TX_CUDA(launch_pdl(k_stats<OneBeam>, (p->ndm + 127) / 128, 128, 0, st, OneBeam{a}, nullptr, nullptr, 1, p->ndm));
+    TX_CUDA(launch_pdl(k_stats<OneBeam>, (p->ndm + 3) / 4, 128, 0, st, OneBeam{a}, nullptr, nullptr, 1, p->ndm));
     TX_CUDA(cudaGetLastError());
     TX_MARK(4);
     const int nunits = p->ndm * p->ntile3;   // k_stats zeroed the candidate counter

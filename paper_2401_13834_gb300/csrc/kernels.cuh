@@ -1556,17 +1556,19 @@ __device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
   return __dadd_rn(__dmul_rn((double)hi, 18446744073709551616.0), (double)lo);
 }
 
-// One thread per fine DM. mu = S1 / T, var = (T S2 - S1^2) / T^2 with an exact
-// 128-bit numerator; the running mode updates (mu, var) <- (1 - l) prev + l new.
-// Then, per width W: hi + lo = W mu (hi integer) and inv = 1 / (sigma sqrt W).
-// In a batch the thread of a candidate-mode beam's first DM also zeroes that
-// beam's candidate counter (the boxcar launch comes after this one).
+// One warp per fine DM (its lanes sum the tiles' exact sums). mu = S1 / T,
+// var = (T S2 - S1^2) / T^2 with an exact 128-bit numerator; the running mode
+// updates (mu, var) <- (1 - l) prev + l new. Then, per width W (one lane
+// each): hi + lo = W mu (hi integer) and inv = 1 / (sigma sqrt W). The warp of
+// a candidate-mode beam's first DM also zeroes the beam's candidate counter
+// (the boxcar launch comes after this one).
 template <typename Src>
 __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem,
                         int nunits) {
   pdl_wait();
   pdl_trigger();
-  const int gd = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gd = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);   // one warp per DM
+  const int lane = threadIdx.x & 31;
   if (gd >= nunits) return;
   int d;
   BeamArgs a;
@@ -1574,39 +1576,47 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
     const int j = find_member(uoff, nmem, gd);
     d = gd - uoff[j];
     a = src.get(umem[j]);
-    if (d == 0 && a.output == TX_OUT_CANDS) *a.ncand = 0ull;
   } else {
     d = gd;
     a = src.get(0);
-    if (d == 0 && a.output == TX_OUT_CANDS) *a.ncand = 0ull;   // the boxcar launch comes after this one
   }
+  if (d == 0 && lane == 0 && a.output == TX_OUT_CANDS) *a.ncand = 0ull;   // the boxcar launch comes after this one
   const int64_t T = a.T;
   unsigned long long s1 = 0, s2 = 0;
   const int np = a.ntile2 * a.split2;   // the stage-2 tiles' exact sums (per warp of a fine DM in a pipeline plan)
-  for (int i = 0; i < np; ++i) {
+  for (int i = lane; i < np; i += 32) {
     const longlong2 v = a.part[(size_t)d * np + i];
     s1 += (unsigned long long)v.x;
     s2 += (unsigned long long)v.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {   // integer sums: exact in any order
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
   double mu = __ddiv_rn((double)s1, (double)T);
   const unsigned __int128 num = (unsigned __int128)(unsigned long long)T * s2 - (unsigned __int128)s1 * s1;
   double var = __ddiv_rn(u128_to_double(num), __dmul_rn((double)T, (double)T));
   if (a.running) {
-    double* r = a.run + (size_t)d * 2;
-    const double lam = a.lam;
-    if (r[1] < 0.0) {  // never initialised (reset writes -1)
-      r[0] = mu;
-      r[1] = var;
-    } else {
-      mu = __dadd_rn(__dmul_rn(1.0 - lam, r[0]), __dmul_rn(lam, mu));
-      var = __dadd_rn(__dmul_rn(1.0 - lam, r[1]), __dmul_rn(lam, var));
-      r[0] = mu;
-      r[1] = var;
+    if (lane == 0) {
+      double* r = a.run + (size_t)d * 2;
+      const double lam = a.lam;
+      if (r[1] < 0.0) {  // never initialised (reset writes -1)
+        r[0] = mu;
+        r[1] = var;
+      } else {
+        mu = __dadd_rn(__dmul_rn(1.0 - lam, r[0]), __dmul_rn(lam, mu));
+        var = __dadd_rn(__dmul_rn(1.0 - lam, r[1]), __dmul_rn(lam, var));
+        r[0] = mu;
+        r[1] = var;
+      }
     }
+    mu = __shfl_sync(0xffffffffu, mu, 0);
+    var = __shfl_sync(0xffffffffu, var, 0);
   }
   const double sigma = sqrt(var);
   const double gamma = a.gamma;
-  for (int w = 0; w < a.nw; ++w) {
+  for (int w = lane; w < a.nw; w += 32) {   // the widths' constants, one lane each
     const double W = (double)a.widths[w];
     const double cw = __dmul_rn(W, mu);
     const double hi = rint(cw);

@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--serve-max-batch", type=int, default=64)
     ap.add_argument("--serve-burst", type=int, default=2, help="serving: blocks per beam in the capacity phase")
     ap.add_argument("--beams", type=int, default=64, help="batched: number of beams")
+    ap.add_argument("--beam-shapes", choices=["uneven", "small"], default="uneven",
+                    help="batched: the uneven draw of channels, DMs and block lengths, or beams of the small "
+                         "workload's shape (each too small to fill the GPU)")
     ap.add_argument("--ws-budget-gb", type=float, default=96.0, help="batched: workspace budget (GiB) for waves")
     ap.add_argument("--plain-steps", type=int, default=3, help="batched: steps of the one-beam-at-a-time loop")
     ap.add_argument("--batch-max-cands", type=int, default=1 << 22)
@@ -791,7 +794,7 @@ def run_batched(args):
     _build.build()
     import paper_2401_13834_gb300 as tx
 
-    wls = synth.batched_workloads(args.beams)
+    wls = synth.batched_workloads(args.beams) if args.beam_shapes == "uneven" else synth.small_beams(args.beams)
     if args.tune and rank == 0:
         autotune.tune_all(wls, args.layout, args.output, args.interm, verbose=True, snr_threshold=args.gamma)
     if world > 1:
@@ -997,7 +1000,8 @@ def run_batched(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8->int32 sums, f32 S/N", "data": "synthetic",
-            "config": {"workload": f"batched-{len(wls)}-beams", "beams": len(wls), "shapes": shapes,
+            "config": {"workload": f"batched-{len(wls)}-beams" + ("" if args.beam_shapes == "uneven" else "-small"),
+                       "beams": len(wls), "shapes": shapes,
                        "band_mhz": [856.0, 1712.0], "tsamp_us": 153.12, "dm_max": 3000.0,
                        "widths": [int(w) for w in wls[0].widths], "output": args.output, "layout": args.layout,
                        "interm": args.interm if getattr(args, "norm", "none") == "none" else "f32",

@@ -22,6 +22,8 @@ Workloads (the paper's benchmark simulates MMGPS-L-like data at 153 us, Sec. 3):
   widths 1..256, a few pulses per beam; drawn with a fixed seed.
 * ``serving``    -- 480 beams, every other one MeerKAT-L-like and the rest
   drawn like the batched beams.
+* ``small_beams`` -- beams of the small workload's shape, for batches whose
+  members are each too small to fill the GPU.
 """
 from __future__ import annotations
 
@@ -167,6 +169,17 @@ def batched_workloads(nbeams: int = 64, seed: int = 3, dm_max: float = 3000.0) -
         nsamp = int(rng.choice([32768, 65536, 131072]))
         ndm = int(rng.choice([1024, 4096, 8192]))
         out.append(batched_beam(nchan, ndm, nsamp, dm_max, name=f"beam{i}"))
+    return out
+
+
+def small_beams(nbeams: int = 64) -> list:
+    """Beams of the small workload's shape (256 channels, 128 DM trials, 16384
+    samples): each too small to fill the GPU alone."""
+    out = []
+    for i in range(nbeams):
+        wl = small_workload()
+        wl.name = f"beam{i}-" + wl.name
+        out.append(wl)
     return out
 
 

@@ -272,7 +272,13 @@ void tx_beam_destroy(tx_beam* beam);
                  value above max_cands means the buffer overflowed
      d_workspace info.workspace_bytes bytes of device scratch (not kept),
                  16-byte aligned; info.workspace_bytes_compact for a compact beam
-   All kernels go on `stream`; the call returns once they are enqueued.
+   All kernels go on `stream`; the call returns once they are enqueued. They
+   are launched with programmatic stream serialization: each one may begin
+   launching while the kernel before it in `stream` is finishing, and waits
+   for that kernel (and so for everything enqueued before it) before it
+   touches memory; ordering against other work on `stream` is unchanged.
+   A workspace must not be shared by executes that can run at the same time
+   (it holds their sums and a work counter).
    Errors: INVALID_ARG (null or misaligned buffer, beam of another plan or
    device) before anything is enqueued, CUDA. */
 int32_t tx_execute(const tx_plan* plan, tx_beam* beam, const uint8_t* d_block, void* d_out,

@@ -1642,7 +1642,7 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
 // box_tile outputs, a multiple of kBoxTile chosen by the plan; in a batch, the
 // units of all member beams in turn); each
 // unit's series (with its W_max - 1 look-ahead) is copied into shared memory
-// with cp.async while the previous unit is being filtered, then turned in
+// by one bulk (TMA) copy while the previous unit is being filtered, then turned in
 // place into the prefix sum P (P[0] = 0), and each output t takes
 // B_W = P[t + W] - P[t] for every width.
 //   CUBE / PLANE: S/N for every width (float), best width for the plane.
@@ -1652,9 +1652,12 @@ __global__ void k_stats(const Src src, const int32_t* __restrict__ uoff, const i
 // NWT > 0: exactly NWT widths, per-width constants in registers.
 // NWT = 0: any count up to kMaxWidths, constants in shared memory.
 // The two shared buffers are sized for tileL and wmaxL (the largest box_tile and
-// W_max of the launch).
+// W_max of the launch). A batched launch keeps three blocks per SM (up to 80
+// registers a thread; its arguments are loaded from constant memory at a run-
+// time index): measured faster there, while the single-beam kernel at 64
+// registers was faster on blocks with many candidates.
 template <int NWT, int MODE, typename Src>
-__global__ void __launch_bounds__(kBoxThreads, NWT > 12 ? 3 : 4)
+__global__ void __launch_bounds__(kBoxThreads, Src::kBatch || NWT > 12 ? 3 : 4)
 k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restrict__ umem, int nmem, int nunits,
          int tileL, int wmaxL) {
   constexpr int NR = NWT > 0 ? NWT : 1;
@@ -1665,39 +1668,45 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
   __shared__ int32_t sW[kMaxWidths];
   __shared__ SnrConst sC[kMaxWidths];
   __shared__ __align__(8) uint64_t barb[2];  // completion of the bulk copy into series buffer 0 / 1
-  uint32_t bph[2] = {0u, 0u};
+  uint32_t bph = 0u;   // bit b: the phase to wait for on barb[b]
   const int bufw = (tileL + wmaxL + 8 + 3) & ~3;  // words per buffer: 4 pad + series + chunk rounding
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int u_begin = (int)((int64_t)nunits * blockIdx.x / gridDim.x);
   const int u_end = (int)((int64_t)nunits * (blockIdx.x + 1) / gridDim.x);
 
-  MemberCursor cur_c, cur_i;  // units being filtered / being prefetched
-  auto locate = [&](MemberCursor& c, int u, int& lu, int& j) -> BeamArgs {
-    if constexpr (Src::kBatch) {
-      c.seek(uoff, umem, nmem, u);
-      j = c.j;
-      lu = u - c.lo;
-      return src.get(c.beam);
-    } else {
-      j = 0;
-      lu = u;
-      return src.get(0);
-    }
-  };
+  // In a batch, the unit in buffer b belongs to the member whose arguments
+  // sit at index ubx[b] and whose first unit is ubx[2 + b]; thread 0 finds it
+  // when it issues the unit's copy, walking a cursor (ubx[4..6]: member, its
+  // first and end unit) forward. No member state stays in registers.
+  __shared__ int32_t ubx[Src::kBatch ? 7 : 1];
+  // thread 0: one bulk copy of unit u's series window into buffer buf (16-byte aligned both sides)
   auto issue = [&](int u, int buf) {
-    int lu, j;
-    const BeamArgs a = locate(cur_i, u, lu, j);
+    if (threadIdx.x != 0) return;
+    int b = 0, lu = u;
+    if constexpr (Src::kBatch) {
+      int j = ubx[4], lo = ubx[5], hi = ubx[6];
+      if (j < 0 || u >= hi) {
+        j = j < 0 ? find_member(uoff, nmem, u) : j;
+        while (u >= __ldg(uoff + j + 1)) ++j;
+        lo = __ldg(uoff + j);
+        hi = __ldg(uoff + j + 1);
+        ubx[4] = j;
+        ubx[5] = lo;
+        ubx[6] = hi;
+      }
+      b = __ldg(umem + j);
+      lu = u - lo;
+      ubx[buf] = b;
+      ubx[2 + buf] = lo;
+    }
+    const BeamArgs a = src.get(b);
     const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
     const int64_t t0 = (int64_t)tile * a.box_tile;
     const int n = (int)min((int64_t)a.box_tile, a.T - t0);
     const int nq = (n + a.wmax - 1 + 3) >> 2;  // 16-byte chunks of the series window
-    const int32_t* src = a.D + (size_t)d * a.Dp + t0;
-    uint32_t* dst = smb + (size_t)buf * bufw + 4;
-    if (threadIdx.x == 0) {  // one bulk copy of the window (16-byte aligned both sides)
-      fence_proxy_async();
-      mbar_expect_tx(&barb[buf], (uint32_t)nq * 16u);
-      bulk_g2s(dst, src, (uint32_t)nq * 16u, &barb[buf]);
-    }
+    fence_proxy_async();
+    mbar_expect_tx(&barb[buf], (uint32_t)nq * 16u);
+    bulk_g2s(smb + (size_t)buf * bufw + 4, a.D + (size_t)d * a.Dp + t0, (uint32_t)nq * 16u, &barb[buf]);
   };
 
   int32_t Wr[NR], thr[NR];
@@ -1707,13 +1716,24 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
     mbar_init(&barb[0], 1);
     mbar_init(&barb[1], 1);
     fence_mbar_init();
+    if constexpr (Src::kBatch) ubx[4] = -1;
   }
   __syncthreads();
   issue(u_begin, 0);
+  if constexpr (Src::kBatch) __syncthreads();   // the first unit's member
   for (int u = u_begin, it = 0; u < u_end; ++u, ++it) {
     const int buf = it & 1;
     int lu, j;
-    const BeamArgs a = locate(cur_c, u, lu, j);
+    BeamArgs a;
+    if constexpr (Src::kBatch) {
+      j = ubx[buf];
+      lu = u - ubx[2 + buf];
+      a = src.get(j);
+    } else {
+      j = 0;
+      lu = u;
+      a = src.get(0);
+    }
     const int nw = NWT > 0 ? NWT : a.nw;
     const int d = lu / a.ntile3, tile = lu - d * a.ntile3;
     const int64_t T = a.T;
@@ -1731,9 +1751,9 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         thr[w] = cst[w].thr;
       }
     }
-    const uint32_t ph = bph[buf];
+    const uint32_t ph = (bph >> buf) & 1u;
     const bool landed = mbar_wait(&barb[buf], ph, a.polls);
-    bph[buf] ^= 1u;
+    bph ^= 1u << buf;
     // this unit's series landed; the previous unit is done with sW/sC and the other buffer
     if (__syncthreads_or(!landed)) {
       // a copy never completed: record it, give the copy in flight a last wait at the full limit, give up
@@ -1794,7 +1814,8 @@ k_boxcar(const Src src, const int32_t* __restrict__ uoff, const int32_t* __restr
         m3 = max(m3, (int32_t)(nx.y - cl.w) - thr[1]);
 #pragma unroll
         for (int w = 2; w < NR; ++w) {
-          const uint4 cw = C4[q + (Wr[w] >> 2)];
+          // width 4 (the usual third) is the next quad, already loaded
+          const uint4 cw = (w == 2 && Wr[2] == 4) ? nx : C4[q + (Wr[w] >> 2)];
           m0 = max(m0, (int32_t)(cw.x - cl.x) - thr[w]);
           m1 = max(m1, (int32_t)(cw.y - cl.y) - thr[w]);
           m2 = max(m2, (int32_t)(cw.z - cl.z) - thr[w]);

@@ -349,6 +349,35 @@ def cpu_baseline(wl, X, gamma, budget_s):
                       f"boxcar S/N, best width and candidates; numpy, single thread, {el:.1f} s"}
 
 
+def cpu_direct(wl, X, budget_s):
+    """The brute-force de-dispersion of Sec. 2.3 (every channel at its own
+    Eq. 1 delay; the oracle's direct_dedisperse) on the same block, one
+    thread: all DM trials when the budget allows, else an evenly spread
+    subset, with the whole block's time extrapolated from the time per trial.
+    De-dispersion only (no boxcar), the reference the sub-band method
+    approximates."""
+    from oracle import dedisp as O
+    T = wl.nsamp
+    # outputs whose every channel track lies inside the window (the direct
+    # delays can pass the sub-band overlap by a few samples)
+    nout = min(T, X.shape[1] - int(O.direct_delays(wl.freqs_mhz, wl.tsamp_s, wl.dms).max()))
+    order = np.linspace(0, wl.ndm - 1, wl.ndm).astype(int)
+    order = np.concatenate([order[::7], np.setdiff1d(order, order[::7])])   # spread first
+    t0 = time.perf_counter()
+    n = 0
+    for d in order:
+        O.direct_dedisperse(X, wl.freqs_mhz, wl.tsamp_s, wl.dms[d:d + 1], nout)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    whole = n == wl.ndm and nout == T
+    return {"value": n * nout / el, "unit": UNIT, "cores": 1, "kind": "oracle (direct)",
+            "whole_block_s": el / n * wl.ndm * T / nout, "whole_block_extrapolated": not whole,
+            "sample": f"{'all' if n == wl.ndm else n} of {wl.ndm} DM trials x {nout} of {T} samples of one "
+                      f"{wl.nchan}-channel block, brute-force de-dispersion only (numpy, single thread, {el:.1f} s)"}
+
+
 _POOL = {}
 
 
@@ -719,6 +748,10 @@ def run_ours(args):
                                                               cpu["per_group_s"], args.cpu_seconds)
                 except Exception as e:                                    # noqa: BLE001 (reported, not fatal)
                     cpu["all_cores"] = {"value": None, "error": f"{type(e).__name__}: {e}"}
+            try:
+                cpu["direct"] = cpu_direct(wl, np.ascontiguousarray(X[:, :L + T]), min(args.cpu_seconds, 8.0))
+            except Exception as e:                                        # noqa: BLE001 (reported, not fatal)
+                cpu["direct"] = {"value": None, "error": f"{type(e).__name__}: {e}"}
             cpu.pop("per_group_s", None)
         # ingest is one launch, two when the block wraps the ring's end; then
         # stage 1, stage 2, statistics and the boxcar

@@ -205,8 +205,9 @@ int32_t tx_plan_get_info(const tx_plan* plan, tx_plan_info* info);
 int32_t tx_plan_tables(const tx_plan* plan, int32_t* d1, int32_t* d2,
                        int32_t* coarse_of_fine, double* coarse_dm);
 
-/* Geometric boxcar ladder (Sec. 2.4: widths in a geometric sequence with a
-   tunable ratio): w_i = floor(ratio^i + 0.5), duplicates dropped, w_i <= wmax.
+/* Geometric boxcar ladder (Sec. 2.4: each width a fixed multiple of the one
+   before, the multiple set by the caller): w_i = floor(ratio^i + 0.5),
+   duplicates dropped, w_i <= wmax.
    Writes at most `cap` widths to h_widths; returns the count (or an error). */
 int32_t tx_geometric_widths(double ratio, int32_t wmax, int32_t* h_widths, int32_t cap);
 

@@ -1549,7 +1549,7 @@ k_stage2_i32(const int32_t* __restrict__ P, int64_t Pp, const int32_t* __restric
 }
 
 // ---------------------------------------------------------------------------
-// statistics (Eq. 5's sigma: the standard deviation of the noise)
+// statistics (Eq. 5's sigma: the spread of the series' noise, per DM)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
   const unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;

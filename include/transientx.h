@@ -1,7 +1,6 @@
 /*
  * transientx.h -- C ABI of a GB300 (sm_103a) implementation of TransientX's
- * de-dispersion + matched-filter hot path (Men & Barr, "TransientX: A high
- * performance single pulse search package").
+ * de-dispersion + matched-filter hot path (Men & Barr, arXiv 2401.13834).
  *
  * What the library computes, per block of T new samples of a beam:
  *
@@ -16,9 +15,9 @@
  *      [s m, (s+1) m); fine DMs are grouped G at a time in order and a group's
  *      coarse DM is the midpoint of its first and last fine DM.
  *   2. Block statistics of each series over t in [0, T): exact integer sums,
- *      mean and population standard deviation ("sigma is the standard
- *      deviation of the noise", Sec. 2.4), or their running (exponential)
- *      update across blocks.
+ *      mean and population standard deviation (Sec. 2.4 takes sigma as the
+ *      noise's spread; here that of the block's series), or their running
+ *      (exponential) update across blocks.
  *   3. The boxcar matched filter of Eq. 5 computed by prefix sums (Sec. 2.4):
  *        S/N[d][w][t] = (sum_{i=t}^{t+W_w-1} D[d][i] - W_w mu_d) / (sigma_d sqrt(W_w))
  *      (window reported at its start t; sigma = 0 gives S/N = 0).
